@@ -1,0 +1,190 @@
+/*
+ * minplus.h -- C ABI of the GB300 (sm_103a) library for exact integer
+ * (min,+) matrix products and the 2-domination power chain of
+ * arXiv 2409.17688 ("HPC acceleration of large (min,+) matrix products to
+ * compute domination-type parameters in graphs").
+ *
+ * Notation.  The paper writes the cylinder as P_m x C_n with m the path
+ * order.  This library writes P_n x C_m: n is the path order (it fixes the
+ * matrix size N = |C_n|, Table 1) and m is the cycle length (the power).
+ *
+ * Conventions shared by every entry point.
+ *  - Matrices are row-major with a leading dimension counted in elements.
+ *  - "device" pointers are CUDA device memory owned by the caller (for
+ *    example torch tensors); "host" pointers are ordinary host memory.
+ *    The library never frees caller memory.  It owns only the internal
+ *    scratch it allocates (stream-ordered, freed before the call's work
+ *    completes on the stream) and the per-device caches listed below.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued asynchronously on it unless an entry point
+ *    says it is synchronous.  Entry points that must size internal buffers
+ *    from device data synchronize the stream once; each says so.
+ *  - INF encoding: 0x7FFF for int16 (MP_I16) and 255 for uint8 (MP_U8).
+ *    Every input entry must lie in [0, INF].  Products are saturating:
+ *    result = min(INF, min_l X_il + Y_lj), so an INF entry never produces a
+ *    finite value.  Outside [0, INF] the results are unspecified.
+ *  - Every function returns MP_OK (0) or a negative status; the message of
+ *    the last failure on the calling host thread is in mp_last_error().
+ *  - Asynchronous device-side failures (a bounded wait that ran out) are
+ *    latched in a per-device flag read by mp_device_status().
+ */
+#ifndef MINPLUS_H
+#define MINPLUS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MP_OK 0
+#define MP_EINVAL -1   /* bad argument: n, m, k_max, sizes, leading dims, dtype */
+#define MP_EALIAS -2   /* an output buffer overlaps an input buffer            */
+#define MP_ENOMEM -3   /* device or host allocation failed / does not fit HBM  */
+#define MP_ERANGE -4   /* exact result could reach the INF code (m*n >= 32767) */
+#define MP_ECUDA -5    /* a CUDA runtime call failed                           */
+#define MP_ETIMEOUT -6 /* a bounded device-side wait ran out                   */
+#define MP_EBUSY -7    /* a server queue is full                               */
+#define MP_ENOTREADY -8 /* a polled server ticket has not finished yet          */
+
+/* ---- element types ----------------------------------------------------- */
+#define MP_I16 0 /* int16 entries in [0, 0x7FFF], INF = 0x7FFF */
+#define MP_U8 1  /* uint8 entries in [0, 255],    INF = 255    */
+
+#define MP_INF16 0x7FFF
+#define MP_INF8 0xFF
+
+/* Largest path order the library enumerates (words are packed 2 bits per
+ * letter in 32 bits).  The dense A(D_n) fits one GB300 up to n = 13. */
+#define MP_MAX_PATH_ORDER 16
+
+/* ---- a1: correct words --------------------------------------------------
+ * Section 2.2 (correct n-words) and Table 1 (their number).
+ * mp_transfer_size returns N = |C_n|, the number of correct n-words, or a
+ * negative status for n < 1 or n > MP_MAX_PATH_ORDER.  Host only, no CUDA.
+ */
+int64_t mp_transfer_size(int n);
+
+/* Writes the correct n-words into the HOST array words[0..cap) in
+ * lexicographic order (letter 1 most significant, 0 < 1 < 2), each packed
+ * two bits per letter with letter 1 in bits 2(n-1)..2n-1, so the packed
+ * values increase strictly.  Returns N (words beyond cap are not written),
+ * or MP_EINVAL.  Host only. */
+int64_t mp_transfer_words(int n, uint32_t *words, int64_t cap);
+
+/* ---- a2: the transfer matrix A(D_n) -------------------------------------
+ * Algorithm 1 with the arc rule and labels of Section 2.2: A[q][p] = number
+ * of zeros of p when word p can follow word q, else INF16.  Row q is the
+ * source column word, column p the target (Theorem 2).
+ * A: DEVICE int16, N x N, leading dimension lda >= N (N from
+ * mp_transfer_size).  words_opt: DEVICE uint32[N] receiving the packed
+ * words, or NULL.  Asynchronous on stream (the word list is uploaded from a
+ * pageable host buffer).  Errors: MP_EINVAL (n or lda), MP_ENOMEM, MP_ECUDA.
+ */
+int mp_build_transfer_matrix(int n, int16_t *A, int64_t lda, uint32_t *words_opt,
+                             void *stream);
+
+/* ---- a3/a5: one (min,+) product ------------------------------------------
+ * Section 1: Z = X (x) Y, Z_ij = min(INF, min_l X_il + Y_lj), exact.
+ * X: DEVICE M x K (ldx >= K), Y: DEVICE K x N (ldy >= N), Z: DEVICE M x N
+ * (ldz >= N), all of element type dtype (MP_I16 or MP_U8).  K = 0 gives an
+ * all-INF Z (X and Y may then be NULL).  M = 0 or N = 0 is a no-op.  Blocks of 128 x 128 that are
+ * entirely INF in X or Y are skipped (their terms cannot lower a minimum).
+ * Errors: MP_EINVAL (negative sizes, ld too small, dtype), MP_EALIAS (Z
+ * overlaps X or Y), MP_ENOMEM, MP_ECUDA.  Asynchronous.
+ */
+int mp_minplus_mul(const void *X, const void *Y, void *Z, int64_t M, int64_t N,
+                   int64_t K, int64_t ldx, int64_t ldy, int64_t ldz, int dtype,
+                   void *stream);
+
+/* ---- a3/a4: the power chain with the gamma_2 readout -----------------------
+ * Algorithm 2 and Theorem 2 / Algorithm 5: P_1 = A, P_k = A (x) P_{k-1} for
+ * k = 2..k_max (equal to P_{k-1} (x) A by associativity), and
+ * g[k-1] = min_i (P_k)_ii.
+ * A: DEVICE int16 N x N (leading dimension N), entries in [0, 0x7FFF].
+ * powers_opt: DEVICE int16 [k_max][N][N], slot k-1 receives P_k, or NULL
+ * (then only two internal ping-pong buffers are used).
+ * gdiag_opt: DEVICE int32 [k_max], slot k-1 receives min diag P_k (0x7FFF
+ * when the whole diagonal is INF), or NULL.
+ * A sparse A (at most 1/4 of its entries finite) runs the sparse transfer
+ * kernel; a denser A the dense product.  Synchronizes the stream once to
+ * size the sparse plan.  Errors: MP_EINVAL, MP_EALIAS (powers overlap A),
+ * MP_ENOMEM, MP_ECUDA.
+ */
+int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max,
+                              int16_t *powers_opt, int32_t *gdiag_opt, void *stream);
+
+/* The same chain for the transfer matrix A(D_n) itself, built on the device
+ * from n (no dense A is formed).  The plan for n is cached per device after
+ * the first call.  powers_opt / gdiag_opt as above with N = |C_n|.
+ * Synchronizes the stream on the first call for a given n. */
+int mp_transfer_power_sequence(int n, int k_max, int16_t *powers_opt,
+                               int32_t *gdiag_opt, void *stream);
+
+/* ---- a6: gamma_2 of one cylinder --------------------------------------------
+ * Theorem 2: gamma_2(P_n x C_m) = min_i (A^m)_ii, for n >= 1 and m >= 3.
+ * Synchronous; *out is a HOST int64.  Uses the cached transfer plan and
+ * either the chain or repeated squaring S_j = S_{j-1} (x) S_{j-1} followed
+ * by a min-trace of the last two factors.  Errors: MP_EINVAL (n out of
+ * range, m < 3), MP_ERANGE (m * n >= 32767: exact values could reach the
+ * int16 INF code), MP_ENOMEM, MP_ECUDA.
+ */
+int mp_gamma2_cylinder(int n, int64_t m, int64_t *out);
+
+/* The gamma_2 table of one path order: out[m] = gamma_2(P_n x C_m) for
+ * m = 3..k_max (Theorem 2 / Algorithm 5 over the chain), out[0..2] = -1.
+ * out is a HOST int64 array of k_max + 1 entries.  Synchronous; runs on a
+ * library-owned stream.  Errors: MP_EINVAL (n, k_max < 3), MP_ERANGE
+ * (k_max * n >= 32767), MP_ENOMEM, MP_ECUDA. */
+int mp_gamma2_table(int n, int k_max, int64_t *out);
+
+/* ---- K3: reductions -----------------------------------------------------
+ * mp_diag_min: *out = min_i P[i][i] over an N x N DEVICE int16 matrix
+ * (leading dimension ld), written to DEVICE int32 out.  Theorem 2.
+ * mp_min_trace: *out = min_{i,l} X[i][l] + Y[l][i] (= min diag of X (x) Y
+ * without forming it) for N x N DEVICE int16 X, Y; DEVICE int32 out,
+ * saturated at 0x7FFF.  Both asynchronous. */
+int mp_diag_min(const int16_t *P, int64_t N, int64_t ld, int32_t *out, void *stream);
+int mp_min_trace(const int16_t *X, const int16_t *Y, int64_t N, int64_t ldx,
+                 int64_t ldy, int32_t *out, void *stream);
+
+/* ---- a7: many products of uneven sizes ----------------------------------------
+ * One descriptor per product Z = X (x) Y; pointers are DEVICE, sizes and
+ * leading dimensions as for mp_minplus_mul, dtype MP_I16 or MP_U8. */
+typedef struct mp_problem {
+    const void *X;
+    const void *Y;
+    void *Z;
+    int64_t M, N, K;
+    int64_t ldx, ldy, ldz;
+    int32_t dtype;
+    int32_t reserved;
+} mp_problem;
+
+/* Runs every product of probs[0..count) (HOST array).  mode 0: one
+ * persistent launch over a tile work list of all products; mode 1: one
+ * launch per product (the plain form, for comparison).  No output may
+ * overlap any input of any problem.  Asynchronous.  Errors: MP_EINVAL,
+ * MP_EALIAS, MP_ENOMEM, MP_ECUDA. */
+int mp_minplus_mul_batched(const mp_problem *probs, int count, int mode, void *stream);
+
+/* ---- K6: DPX add-min peak ------------------------------------------------
+ * Runs independent __viaddmin_u16x2 chains on every SM for `iters`
+ * iterations and writes the achieved add-min rate (two per instruction) in
+ * operations per second to *ops_per_s (HOST).  variant 0: viaddmin u16x2;
+ * 1: vimin3 u16x2 (counted as two minima per lane pair); 2: plain vmin u16x2.
+ * Synchronous. */
+int mp_dpx_peak(int variant, int64_t iters, double *ops_per_s);
+
+/* ---- device status and errors --------------------------------------------
+ * mp_device_status synchronizes the current device, then returns MP_OK or
+ * the first latched device-side error (MP_ETIMEOUT) and clears it. */
+int mp_device_status(void);
+const char *mp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MINPLUS_H */

@@ -1,0 +1,228 @@
+"""GB300 (sm_103a) exact (min,+) products and the 2-domination power chain.
+
+A thin ctypes binding over ``libminplus.so`` (the C ABI in ``include/minplus.h``).
+Every function here only marshals arguments: tensors become raw device
+pointers, the current torch stream becomes the ``cudaStream_t``, and every step
+of the computation runs in the library's CUDA kernels.  There is no CPU or
+PyTorch fallback: if the library is not built, every call raises.
+
+Names follow the C ABI.  Notation: path order ``n`` (matrix size
+N = |C_n|, Table 1 of arXiv 2409.17688) and cycle length ``m``; the paper
+writes the cylinder as P_m x C_n with the letters swapped.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+INF16 = 0x7FFF
+INF8 = 0xFF
+MP_I16 = 0
+MP_U8 = 1
+
+STATUS = {0: "MP_OK", -1: "MP_EINVAL", -2: "MP_EALIAS", -3: "MP_ENOMEM", -4: "MP_ERANGE",
+          -5: "MP_ECUDA", -6: "MP_ETIMEOUT", -7: "MP_EBUSY", -8: "MP_ENOTREADY"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libminplus.so")
+_lib = None
+
+
+class MinplusError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{STATUS.get(code, code)}: {message}")
+        self.code = code
+
+
+class mp_problem(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("Z", ctypes.c_void_p),
+                ("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int64),
+                ("ldx", ctypes.c_int64), ("ldy", ctypes.c_int64), ("ldz", ctypes.c_int64),
+                ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded C library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    sig = {
+        "mp_transfer_size": (I64, [I]),
+        "mp_transfer_words": (I64, [I, P, I64]),
+        "mp_build_transfer_matrix": (I, [I, P, I64, P, P]),
+        "mp_minplus_mul": (I, [P, P, P, I64, I64, I64, I64, I64, I64, I, P]),
+        "mp_minplus_power_sequence": (I, [P, I64, I, P, P, P]),
+        "mp_transfer_power_sequence": (I, [I, I, P, P, P]),
+        "mp_gamma2_cylinder": (I, [I, I64, P]),
+        "mp_gamma2_table": (I, [I, I, P]),
+        "mp_diag_min": (I, [P, I64, I64, P, P]),
+        "mp_min_trace": (I, [P, P, I64, I64, I64, P, P]),
+        "mp_minplus_mul_batched": (I, [P, I, I, P]),
+        "mp_dpx_peak": (I, [I, I64, P]),
+        "mp_device_status": (I, []),
+        "mp_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int) -> int:
+    if status < 0:
+        msg = lib().mp_last_error()
+        raise MinplusError(int(status), msg.decode() if msg else "")
+    return status
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t):
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda, "expected a CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ words / A
+
+def mp_transfer_size(n: int) -> int:
+    """N = |C_n|, the number of correct n-words."""
+    return _check(lib().mp_transfer_size(int(n)))
+
+
+def mp_transfer_words(n: int) -> np.ndarray:
+    """Correct n-words, packed 2 bits per letter, lexicographic order (host)."""
+    N = mp_transfer_size(n)
+    out = np.zeros(N, dtype=np.uint32)
+    _check(lib().mp_transfer_words(int(n), out.ctypes.data, N))
+    return out
+
+
+def mp_build_transfer_matrix(n: int, A=None, words: bool = False, stream=None):
+    """A(D_n) on the current CUDA device (int16, INF = 0x7FFF)."""
+    import torch
+    N = mp_transfer_size(n)
+    if A is None:
+        A = torch.empty((N, N), dtype=torch.int16, device="cuda")
+    assert A.dtype == torch.int16 and A.dim() == 2 and A.shape[0] >= N and A.stride(1) == 1
+    W = torch.empty(N, dtype=torch.int32, device=A.device) if words else None
+    _check(lib().mp_build_transfer_matrix(int(n), _dev(A), A.stride(0),
+                                          _dev(W) if words else None, _stream(stream)))
+    return (A, W) if words else A
+
+
+# --------------------------------------------------------------- products
+
+def mp_minplus_mul(X, Y, Z=None, stream=None):
+    """Z = X (x) Y, exact and saturating; int16 (INF 0x7FFF) or uint8 (INF 255)."""
+    import torch
+    assert X.dtype == Y.dtype and X.dim() == 2 and Y.dim() == 2 and X.shape[1] == Y.shape[0]
+    assert X.stride(1) == 1 and Y.stride(1) == 1
+    dtype = {torch.int16: MP_I16, torch.uint8: MP_U8}[X.dtype]
+    M, K = X.shape
+    N = Y.shape[1]
+    if Z is None:
+        Z = torch.empty((M, N), dtype=X.dtype, device=X.device)
+    assert Z.dtype == X.dtype and Z.stride(1) == 1
+    _check(lib().mp_minplus_mul(_dev(X), _dev(Y), _dev(Z), M, N, K, max(X.stride(0), 1),
+                                max(Y.stride(0), 1), max(Z.stride(0), 1), dtype, _stream(stream)))
+    return Z
+
+
+def mp_minplus_mul_batched(problems, mode: int = 0, stream=None):
+    """problems: list of (X, Y, Z) CUDA tensors; mode 0 persistent, 1 per-product."""
+    import torch
+    arr = (mp_problem * len(problems))()
+    for i, (X, Y, Z) in enumerate(problems):
+        dtype = {torch.int16: MP_I16, torch.uint8: MP_U8}[X.dtype]
+        arr[i] = mp_problem(X.data_ptr(), Y.data_ptr(), Z.data_ptr(), X.shape[0], Y.shape[1],
+                            X.shape[1], max(X.stride(0), 1), max(Y.stride(0), 1),
+                            max(Z.stride(0), 1), dtype, 0)
+    _check(lib().mp_minplus_mul_batched(ctypes.cast(arr, ctypes.c_void_p), len(problems),
+                                        int(mode), _stream(stream)))
+
+
+# ------------------------------------------------------------ power chains
+
+def mp_minplus_power_sequence(A, k_max: int, keep_powers: bool = True, stream=None):
+    """Powers A^1..A^k_max of a square int16 CUDA matrix and g[k-1] = min diag A^k."""
+    import torch
+    N = A.shape[0]
+    assert A.dtype == torch.int16 and A.shape == (N, N) and A.is_contiguous()
+    P = torch.empty((k_max, N, N), dtype=torch.int16, device=A.device) if keep_powers else None
+    g = torch.empty(k_max, dtype=torch.int32, device=A.device)
+    _check(lib().mp_minplus_power_sequence(_dev(A), N, int(k_max), _dev(P) if keep_powers else None,
+                                           _dev(g), _stream(stream)))
+    return P, g
+
+
+def mp_transfer_power_sequence(n: int, k_max: int, keep_powers: bool = True, stream=None):
+    """Powers of A(D_n) built on the device from n, and their diagonal minima."""
+    import torch
+    N = mp_transfer_size(n)
+    P = torch.empty((k_max, N, N), dtype=torch.int16, device="cuda") if keep_powers else None
+    g = torch.empty(k_max, dtype=torch.int32, device="cuda")
+    _check(lib().mp_transfer_power_sequence(int(n), int(k_max), _dev(P) if keep_powers else None,
+                                            _dev(g), _stream(stream)))
+    return P, g
+
+
+def mp_gamma2_cylinder(n: int, m: int) -> int:
+    """gamma_2(P_n x C_m), synchronous."""
+    out = ctypes.c_int64(0)
+    _check(lib().mp_gamma2_cylinder(int(n), int(m), ctypes.byref(out)))
+    return int(out.value)
+
+
+def mp_gamma2_table(n: int, k_max: int) -> np.ndarray:
+    """gamma_2(P_n x C_m) for m = 0..k_max (entries m < 3 are -1), synchronous."""
+    out = np.zeros(k_max + 1, dtype=np.int64)
+    _check(lib().mp_gamma2_table(int(n), int(k_max), out.ctypes.data))
+    return out
+
+
+# -------------------------------------------------------------- reductions
+
+def mp_diag_min(P, stream=None):
+    import torch
+    out = torch.empty(1, dtype=torch.int32, device=P.device)
+    _check(lib().mp_diag_min(_dev(P), P.shape[0], P.stride(0), _dev(out), _stream(stream)))
+    return out
+
+
+def mp_min_trace(X, Y, stream=None):
+    import torch
+    out = torch.empty(1, dtype=torch.int32, device=X.device)
+    _check(lib().mp_min_trace(_dev(X), _dev(Y), X.shape[0], X.stride(0), Y.stride(0), _dev(out),
+                              _stream(stream)))
+    return out
+
+
+# ----------------------------------------------------------------- misc
+
+def mp_dpx_peak(variant: int = 0, iters: int = 1 << 16) -> float:
+    out = ctypes.c_double(0.0)
+    _check(lib().mp_dpx_peak(int(variant), int(iters), ctypes.byref(out)))
+    return float(out.value)
+
+
+def mp_device_status() -> int:
+    return _check(lib().mp_device_status())
+
+
+def mp_last_error() -> str:
+    m = lib().mp_last_error()
+    return m.decode() if m else ""

@@ -1,0 +1,461 @@
+// The exported C ABI (include/minplus.h): argument checks, per-device state
+// and the drivers that string the kernels together.
+#include <stdarg.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+
+#include "mp_internal.cuh"
+#include "spmm.cuh"
+
+namespace mp {
+
+int dpx_peak(int variant, int64_t iters, double *ops_per_s);
+int batched_run(const mp_problem *probs, int count, int mode, cudaStream_t s);
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[1024] = "";
+
+int set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+const char *last_error() { return g_err; }
+
+// ------------------------------------------------------- per-device state
+static std::mutex g_mu;
+
+struct DeviceState {
+    DeviceInfo info;
+    int *status = nullptr;            // device-side error latch
+    cudaStream_t sync_stream = nullptr;  // for the synchronous entry points
+};
+static std::map<int, DeviceState> g_dev;
+
+static int device_state(DeviceState **out) {
+    int dev = -1;
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_dev.find(dev);
+    if (it == g_dev.end()) {
+        DeviceState st;
+        st.info.device = dev;
+        MP_CUDA_TRY(cudaDeviceGetAttribute(&st.info.sms, cudaDevAttrMultiProcessorCount, dev));
+        int optin = 0;
+        MP_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        st.info.smem_optin = (size_t)optin;
+        MP_CUDA_TRY(cudaMalloc(&st.status, sizeof(int)));
+        MP_CUDA_TRY(cudaMemset(st.status, 0, sizeof(int)));
+        MP_CUDA_TRY(cudaStreamCreateWithFlags(&st.sync_stream, cudaStreamNonBlocking));
+        it = g_dev.emplace(dev, st).first;
+    }
+    *out = &it->second;
+    return MP_OK;
+}
+
+int device_info(DeviceInfo *out) {
+    DeviceState *st;
+    MP_TRY(device_state(&st));
+    *out = st->info;
+    return MP_OK;
+}
+
+int device_status_ptr(int **p) {
+    DeviceState *st;
+    MP_TRY(device_state(&st));
+    *p = st->status;
+    return MP_OK;
+}
+
+// ------------------------------------------------ transfer plans (cached)
+struct TransferEntry {
+    int n = 0;
+    int64_t N = 0;
+    std::vector<uint32_t> words;
+    PlanDev plan;
+    DevCsr csr;                // device CSR of A(D_n), labels as values
+    size_t h2d_bytes = 0, d2h_bytes = 0;
+};
+static std::map<std::pair<int, int>, std::unique_ptr<TransferEntry>> g_transfer;
+
+// Builds (or finds) the sparse plan of A(D_n) on the current device.  The
+// arcs come from the device arc test; the host only groups rows.
+static int transfer_entry(int n, cudaStream_t s, TransferEntry **out) {
+    int dev = -1;
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_transfer.find({dev, n});
+        if (it != g_transfer.end()) {
+            *out = it->second.get();
+            return MP_OK;
+        }
+    }
+    auto e = std::make_unique<TransferEntry>();
+    e->n = n;
+    enumerate_words(n, &e->words);
+    const int64_t N = (int64_t)e->words.size();
+    e->N = N;
+    std::vector<WordMasks> masks;
+    word_masks(n, e->words, &masks);
+    DevBuf dmask;
+    MP_TRY(dmask.alloc(masks.size() * sizeof(WordMasks), s));
+    MP_CUDA_TRY(cudaMemcpyAsync(dmask.p, masks.data(), masks.size() * sizeof(WordMasks),
+                                cudaMemcpyHostToDevice, s));
+    HostCsr csr;
+    csr.N = N;
+    MP_TRY(e->csr.row_ptr.alloc((size_t)(N + 1) * 8, s, true));
+    int64_t *d_rp = e->csr.row_ptr.as<int64_t>();
+    MP_TRY(launch_transfer_csr_count(n, dmask.as<WordMasks>(), N, d_rp, s));
+    std::vector<int64_t> cnt((size_t)N);
+    MP_CUDA_TRY(cudaMemcpyAsync(cnt.data(), d_rp, (size_t)N * 8, cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    csr.row_ptr.assign((size_t)N + 1, 0);
+    for (int64_t q = 0; q < N; ++q) csr.row_ptr[q + 1] = csr.row_ptr[q] + cnt[q];
+    const int64_t nnz = csr.row_ptr[N];
+    MP_CUDA_TRY(cudaMemcpyAsync(d_rp, csr.row_ptr.data(), (size_t)(N + 1) * 8,
+                                cudaMemcpyHostToDevice, s));
+    MP_TRY(e->csr.col.alloc((size_t)std::max<int64_t>(nnz, 1) * 4, s, true));
+    MP_TRY(launch_transfer_csr_fill(n, dmask.as<WordMasks>(), N, d_rp, e->csr.col.as<int32_t>(), s));
+    csr.col.resize((size_t)nnz);
+    if (nnz)
+        MP_CUDA_TRY(cudaMemcpyAsync(csr.col.data(), e->csr.col.p, (size_t)nnz * 4,
+                                    cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    // labels: number of zeros of the target word
+    std::vector<uint16_t> z((size_t)N);
+    for (int64_t p = 0; p < N; ++p) z[p] = (uint16_t)__builtin_popcount(masks[p].zero);
+    csr.val.resize((size_t)nnz);
+    for (int64_t t = 0; t < nnz; ++t) csr.val[t] = (int16_t)z[csr.col[t]];
+    MP_TRY(e->csr.val.alloc((size_t)std::max<int64_t>(nnz, 1) * 2, s, true));
+    if (nnz)
+        MP_CUDA_TRY(cudaMemcpyAsync(e->csr.val.p, csr.val.data(), (size_t)nnz * 2,
+                                    cudaMemcpyHostToDevice, s));
+    int cap = 0, bps = 0;
+    MP_TRY(sparse_cap_rows(&cap, &bps));
+    PlanHost ph;
+    MP_TRY(plan_build_host(csr, true, z, cap, &ph));
+    MP_TRY(plan_upload(ph, &e->plan, s, true));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    e->h2d_bytes = masks.size() * sizeof(WordMasks) + (size_t)(N + 1) * 8 + (size_t)nnz * 2 +
+                   e->plan.h2d_bytes;
+    e->d2h_bytes = (size_t)N * 8 + (size_t)nnz * 4;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto &slot = g_transfer[{dev, n}];
+    if (!slot) slot = std::move(e);
+    *out = slot.get();
+    return MP_OK;
+}
+
+// The chain over a prepared sparse plan; B0 already holds P_1.
+static int run_sparse_chain(const PlanDev &plan, uint16_t *B0, uint16_t *B1, int k_max,
+                            int16_t *powers, int32_t *gdiag, cudaStream_t s) {
+    const size_t slot = (size_t)plan.N * (size_t)plan.N;
+    uint16_t *buf[2] = {B0, B1};
+    for (int k = 2; k <= k_max; ++k) {
+        MP_TRY(sparse_step(plan, buf[(k - 2) & 1], buf[(k - 1) & 1],
+                           powers ? powers + (size_t)(k - 1) * slot : nullptr,
+                           gdiag ? gdiag + (k - 1) : nullptr, s));
+    }
+    return MP_OK;
+}
+
+// Dense chain: P_k = P_{k-1} (x) A with the diagonal fused into the product.
+static int run_dense_chain(const int16_t *A, int64_t N, int k_max, int16_t *powers,
+                           int32_t *gdiag, cudaStream_t s) {
+    const size_t slot = (size_t)N * (size_t)N;
+    DevBuf tmp;
+    if (!powers) MP_TRY(tmp.alloc(2 * slot * 2, s));
+    const int16_t *prev = A;
+    for (int k = 2; k <= k_max; ++k) {
+        int16_t *out = powers ? powers + (size_t)(k - 1) * slot
+                              : tmp.as<int16_t>() + (size_t)((k - 2) & 1) * slot;
+        MP_TRY(dense_minplus(prev, A, out, N, N, N, N, N, N, MP_I16,
+                             gdiag ? gdiag + (k - 1) : nullptr, s));
+        prev = out;
+    }
+    return MP_OK;
+}
+
+static int check_n(int n) {
+    if (n < 1 || n > MP_MAX_PATH_ORDER)
+        return set_error(MP_EINVAL, "path order n = %d outside [1, %d]", n, MP_MAX_PATH_ORDER);
+    return MP_OK;
+}
+
+}  // namespace mp
+
+using namespace mp;
+
+extern "C" {
+
+const char *mp_last_error(void) { return mp::last_error(); }
+
+int64_t mp_transfer_size(int n) {
+    MP_TRY(check_n(n));
+    std::vector<uint32_t> w;
+    enumerate_words(n, &w);
+    return (int64_t)w.size();
+}
+
+int64_t mp_transfer_words(int n, uint32_t *words, int64_t cap) {
+    MP_TRY(check_n(n));
+    std::vector<uint32_t> w;
+    enumerate_words(n, &w);
+    if (words && cap > 0)
+        memcpy(words, w.data(), sizeof(uint32_t) * (size_t)std::min<int64_t>(cap, (int64_t)w.size()));
+    return (int64_t)w.size();
+}
+
+int mp_build_transfer_matrix(int n, int16_t *A, int64_t lda, uint32_t *words_opt, void *stream) {
+    MP_TRY(check_n(n));
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<uint32_t> w;
+    enumerate_words(n, &w);
+    const int64_t N = (int64_t)w.size();
+    if (!A) return set_error(MP_EINVAL, "A is NULL");
+    if (lda < N) return set_error(MP_EINVAL, "lda = %lld < N = %lld", (long long)lda, (long long)N);
+    if (words_opt && ranges_overlap(words_opt, (size_t)N * 4, A, span_bytes(N, N, lda, 2)))
+        return set_error(MP_EALIAS, "words_opt overlaps A");
+    std::vector<WordMasks> masks;
+    word_masks(n, w, &masks);
+    DevBuf dm;
+    MP_TRY(dm.alloc(masks.size() * sizeof(WordMasks), s));
+    MP_CUDA_TRY(cudaMemcpyAsync(dm.p, masks.data(), masks.size() * sizeof(WordMasks),
+                                cudaMemcpyHostToDevice, s));
+    if (words_opt)
+        MP_CUDA_TRY(cudaMemcpyAsync(words_opt, w.data(), (size_t)N * 4, cudaMemcpyHostToDevice, s));
+    MP_TRY(launch_build_transfer(n, dm.as<WordMasks>(), N, A, lda, s));
+    // the host vectors must outlive the pageable copies' staging
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    return MP_OK;
+}
+
+int mp_minplus_mul(const void *X, const void *Y, void *Z, int64_t M, int64_t N, int64_t K,
+                   int64_t ldx, int64_t ldy, int64_t ldz, int dtype, void *stream) {
+    if (dtype != MP_I16 && dtype != MP_U8) return set_error(MP_EINVAL, "dtype %d", dtype);
+    if (M < 0 || N < 0 || K < 0) return set_error(MP_EINVAL, "negative size");
+    if (M == 0 || N == 0) return MP_OK;
+    if (!Z || (K > 0 && (!X || !Y))) return set_error(MP_EINVAL, "NULL matrix pointer");
+    if (ldx < std::max<int64_t>(K, 1) || ldy < N || ldz < N)
+        return set_error(MP_EINVAL, "leading dimension too small");
+    const size_t e = dtype == MP_I16 ? 2 : 1;
+    const size_t zb = span_bytes(M, N, ldz, e);
+    if (ranges_overlap(Z, zb, X, span_bytes(M, K, ldx, e)) ||
+        ranges_overlap(Z, zb, Y, span_bytes(K, N, ldy, e)))
+        return set_error(MP_EALIAS, "Z overlaps X or Y");
+    return dense_minplus(X, Y, Z, M, N, K, ldx, ldy, ldz, dtype, nullptr, (cudaStream_t)stream);
+}
+
+int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max, int16_t *powers_opt,
+                              int32_t *gdiag_opt, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!A || N < 1 || k_max < 1) return set_error(MP_EINVAL, "need A, N >= 1, k_max >= 1");
+    const size_t abytes = (size_t)N * (size_t)N * 2;
+    if (powers_opt && ranges_overlap(powers_opt, abytes * (size_t)k_max, A, abytes))
+        return set_error(MP_EALIAS, "powers overlap A");
+    if (gdiag_opt && (ranges_overlap(gdiag_opt, (size_t)k_max * 4, A, abytes) ||
+                      (powers_opt && ranges_overlap(gdiag_opt, (size_t)k_max * 4, powers_opt,
+                                                    abytes * (size_t)k_max))))
+        return set_error(MP_EALIAS, "gdiag overlaps A or the powers");
+    if (gdiag_opt) MP_TRY(launch_fill_i32(gdiag_opt, k_max, (int32_t)kInf16, s));
+
+    HostCsr csr;
+    DevCsr dcsr;
+    MP_TRY(dense_to_csr(A, N, &csr, &dcsr, s));
+    const int64_t nnz = csr.row_ptr[N];
+    const bool sparse = (double)nnz <= 0.25 * (double)N * (double)N;
+    if (!sparse) {
+        if (powers_opt)
+            MP_CUDA_TRY(cudaMemcpyAsync(powers_opt, A, abytes, cudaMemcpyDeviceToDevice, s));
+        if (gdiag_opt) MP_TRY(launch_diag_min(A, N, N, gdiag_opt, false, s));
+        return run_dense_chain(A, N, k_max, powers_opt, gdiag_opt, s);
+    }
+    // column-constant labels allow the pre-added, min-only gather
+    std::vector<int32_t> zc((size_t)N, -1);
+    bool colconst = true;
+    for (int64_t t = 0; t < nnz && colconst; ++t) {
+        int32_t &zz = zc[csr.col[t]];
+        if (zz < 0) zz = csr.val[t];
+        else if (zz != csr.val[t]) colconst = false;
+    }
+    std::vector<uint16_t> z((size_t)N, 0);
+    if (colconst)
+        for (int64_t p = 0; p < N; ++p) z[p] = (uint16_t)std::max(zc[p], 0);
+    int cap = 0, bps = 0;
+    MP_TRY(sparse_cap_rows(&cap, &bps));
+    PlanHost ph;
+    MP_TRY(plan_build_host(csr, colconst, z, cap, &ph));
+    PlanDev plan;
+    MP_TRY(plan_upload(ph, &plan, s, false));
+    DevBuf B;
+    MP_TRY(B.alloc(2 * (size_t)plan.N * (size_t)plan.ldb * 2, s));
+    uint16_t *B0 = B.as<uint16_t>(), *B1 = B0 + (size_t)plan.N * (size_t)plan.ldb;
+    MP_TRY(sparse_init_from_dense(plan, A, B0, powers_opt, gdiag_opt, s));
+    MP_TRY(run_sparse_chain(plan, B0, B1, k_max, powers_opt, gdiag_opt, s));
+    // the host-side plan vectors were copied from pageable memory: make sure
+    // the copies are done before they go out of scope
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    return MP_OK;
+}
+
+int mp_transfer_power_sequence(int n, int k_max, int16_t *powers_opt, int32_t *gdiag_opt,
+                               void *stream) {
+    MP_TRY(check_n(n));
+    if (k_max < 1) return set_error(MP_EINVAL, "k_max = %d < 1", k_max);
+    cudaStream_t s = (cudaStream_t)stream;
+    TransferEntry *te;
+    MP_TRY(transfer_entry(n, s, &te));
+    const PlanDev &plan = te->plan;
+    const size_t slot = (size_t)te->N * (size_t)te->N * 2;
+    if (powers_opt && gdiag_opt &&
+        ranges_overlap(gdiag_opt, (size_t)k_max * 4, powers_opt, slot * (size_t)k_max))
+        return set_error(MP_EALIAS, "gdiag overlaps the powers");
+    if (gdiag_opt) MP_TRY(launch_fill_i32(gdiag_opt, k_max, (int32_t)kInf16, s));
+    DevBuf B;
+    MP_TRY(B.alloc(2 * (size_t)plan.N * (size_t)plan.ldb * 2, s));
+    uint16_t *B0 = B.as<uint16_t>(), *B1 = B0 + (size_t)plan.N * (size_t)plan.ldb;
+    MP_TRY(sparse_init_from_csr(plan, te->csr.row_ptr.as<int64_t>(), te->csr.col.as<int32_t>(),
+                                te->csr.val.as<int16_t>(), B0, powers_opt, gdiag_opt, s));
+    return run_sparse_chain(plan, B0, B1, k_max, powers_opt, gdiag_opt, s);
+}
+
+int mp_gamma2_table(int n, int k_max, int64_t *out) {
+    MP_TRY(check_n(n));
+    if (k_max < 3 || !out) return set_error(MP_EINVAL, "need k_max >= 3 and an output array");
+    if ((int64_t)k_max * n >= (int64_t)kInf16)
+        return set_error(MP_ERANGE, "k_max * n = %lld reaches the int16 INF code",
+                         (long long)k_max * n);
+    DeviceState *st;
+    MP_TRY(device_state(&st));
+    cudaStream_t s = st->sync_stream;
+    DevBuf g;
+    MP_TRY(g.alloc(sizeof(int32_t) * (size_t)k_max, s));
+    MP_TRY(mp_transfer_power_sequence(n, k_max, nullptr, g.as<int32_t>(), s));
+    std::vector<int32_t> h((size_t)k_max);
+    MP_CUDA_TRY(cudaMemcpyAsync(h.data(), g.p, sizeof(int32_t) * (size_t)k_max,
+                                cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int m = 0; m <= k_max; ++m) out[m] = m < 3 ? -1 : (int64_t)h[(size_t)m - 1];
+    return MP_OK;
+}
+
+int mp_diag_min(const int16_t *P, int64_t N, int64_t ld, int32_t *out, void *stream) {
+    if (!P || !out || N < 0 || ld < N) return set_error(MP_EINVAL, "bad diag_min arguments");
+    return launch_diag_min(P, N, ld, out, true, (cudaStream_t)stream);
+}
+
+int mp_min_trace(const int16_t *X, const int16_t *Y, int64_t N, int64_t ldx, int64_t ldy,
+                 int32_t *out, void *stream) {
+    if (!X || !Y || !out || N < 0 || ldx < N || ldy < N)
+        return set_error(MP_EINVAL, "bad min_trace arguments");
+    return launch_min_trace(X, Y, N, ldx, ldy, out, (cudaStream_t)stream);
+}
+
+int mp_gamma2_cylinder(int n, int64_t m, int64_t *out) {
+    MP_TRY(check_n(n));
+    if (m < 3) return set_error(MP_EINVAL, "cycle length m = %lld < 3", (long long)m);
+    if (!out) return set_error(MP_EINVAL, "out is NULL");
+    if (m * (int64_t)n >= (int64_t)kInf16)
+        return set_error(MP_ERANGE, "m * n = %lld reaches the int16 INF code",
+                         (long long)(m * n));
+    DeviceState *st;
+    MP_TRY(device_state(&st));
+    cudaStream_t s = st->sync_stream;
+    TransferEntry *te;
+    MP_TRY(transfer_entry(n, s, &te));
+    const int64_t N = te->N;
+    // cost model: chain = m steps of N*nnz terms; squaring = ~2 log2(m) dense N^3 products
+    const double chain_cost = (double)m * (double)N * (double)te->plan.nnz;
+    const double lg = std::floor(std::log2((double)m)) + 1.0;
+    const double square_cost = 2.5 * (2.0 * lg) * (double)N * (double)N * (double)N;
+    DevBuf g;
+    MP_TRY(g.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(m, 1), s));
+    int32_t result = 0;
+    if (chain_cost <= square_cost || N * N * 2 * 4 > (int64_t)64 << 30) {
+        MP_TRY(mp_transfer_power_sequence(n, (int)m, nullptr, g.as<int32_t>(), s));
+        MP_CUDA_TRY(cudaMemcpyAsync(&result, g.as<int32_t>() + (m - 1), 4, cudaMemcpyDeviceToHost, s));
+    } else {
+        // repeated squaring: S_0 = A, S_j = S_{j-1} (x) S_{j-1}; A^m is the
+        // product of the S_j over the set bits j of m (Lemma 1's algebra), and
+        // the last factor enters only through the min-trace, which gives
+        // min diag of the product without forming it (Theorem 2).
+        const size_t mat = (size_t)N * (size_t)N;
+        DevBuf buf;
+        MP_TRY(buf.alloc(4 * mat * 2, s));
+        int16_t *S = buf.as<int16_t>(), *S2 = S + mat, *R = S + 2 * mat, *R2 = S + 3 * mat;
+        std::vector<WordMasks> masks;
+        word_masks(n, te->words, &masks);
+        DevBuf dm;
+        MP_TRY(dm.alloc(masks.size() * sizeof(WordMasks), s));
+        MP_CUDA_TRY(cudaMemcpyAsync(dm.p, masks.data(), masks.size() * sizeof(WordMasks),
+                                    cudaMemcpyHostToDevice, s));
+        MP_TRY(launch_build_transfer(n, dm.as<WordMasks>(), N, S, N, s));
+        int top = 0;
+        while ((m >> (top + 1)) != 0) ++top;
+        if ((m & (m - 1)) == 0) {
+            // m = 2^top: A^m = S_{top-1} (x) S_{top-1}
+            for (int j = 0; j + 1 < top; ++j) {
+                MP_TRY(dense_minplus(S, S, S2, N, N, N, N, N, N, MP_I16, nullptr, s));
+                std::swap(S, S2);
+            }
+            MP_TRY(launch_min_trace(S, S, N, N, N, g.as<int32_t>(), s));
+        } else {
+            bool have_r = false;
+            for (int j = 0; j <= top; ++j) {
+                if ((m >> j) & 1) {
+                    if (j == top) {
+                        MP_TRY(launch_min_trace(R, S, N, N, N, g.as<int32_t>(), s));
+                        break;
+                    }
+                    if (!have_r) {
+                        MP_CUDA_TRY(cudaMemcpyAsync(R, S, mat * 2, cudaMemcpyDeviceToDevice, s));
+                        have_r = true;
+                    } else {
+                        MP_TRY(dense_minplus(R, S, R2, N, N, N, N, N, N, MP_I16, nullptr, s));
+                        std::swap(R, R2);
+                    }
+                }
+                MP_TRY(dense_minplus(S, S, S2, N, N, N, N, N, N, MP_I16, nullptr, s));
+                std::swap(S, S2);
+            }
+        }
+        MP_CUDA_TRY(cudaMemcpyAsync(&result, g.as<int32_t>(), 4, cudaMemcpyDeviceToHost, s));
+    }
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = result;
+    return MP_OK;
+}
+
+int mp_minplus_mul_batched(const mp_problem *probs, int count, int mode, void *stream) {
+    if (count < 0 || (count > 0 && !probs)) return set_error(MP_EINVAL, "bad problem list");
+    if (mode != 0 && mode != 1) return set_error(MP_EINVAL, "mode %d", mode);
+    return batched_run(probs, count, mode, (cudaStream_t)stream);
+}
+
+int mp_dpx_peak(int variant, int64_t iters, double *ops_per_s) {
+    if (!ops_per_s) return set_error(MP_EINVAL, "ops_per_s is NULL");
+    return dpx_peak(variant, iters, ops_per_s);
+}
+
+int mp_device_status(void) {
+    DeviceState *st;
+    MP_TRY(device_state(&st));
+    MP_CUDA_TRY(cudaDeviceSynchronize());
+    int v = 0;
+    MP_CUDA_TRY(cudaMemcpy(&v, st->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v != 0) {
+        MP_CUDA_TRY(cudaMemset(st->status, 0, sizeof(int)));
+        return set_error(v, "a device-side bounded wait ran out");
+    }
+    return MP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// Sparse (min,+) power-chain plan and launchers (K2).
+#pragma once
+
+#include <vector>
+
+#include "mp_internal.cuh"
+
+namespace mp {
+
+// CSR of a sparse N x N int16 matrix: the finite entries of each row.
+struct HostCsr {
+    int64_t N = 0;
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col;
+    std::vector<int16_t> val;
+};
+struct DevCsr {
+    DevBuf row_ptr, col, val;
+};
+
+// The gather plan of a sparse A, built once on the host (see spmm.cu).
+struct PlanHost {
+    int64_t N = 0, ldb = 0, nnz = 0;
+    int ngroups = 0, nchunks = 0, cap_rows = 0;
+    bool colconst = false;
+    std::vector<int32_t> grp_row0, grp_stage0, stage_u0, stage_ebase, stage_e, urows;
+    std::vector<uint32_t> ent;
+    std::vector<uint16_t> z;
+};
+struct PlanDev {
+    int64_t N = 0, ldb = 0, nnz = 0;
+    int ngroups = 0, nchunks = 0, cap_rows = 0;
+    bool colconst = false;
+    size_t h2d_bytes = 0;
+    DevBuf grp_row0, grp_stage0, stage_u0, stage_ebase, stage_e, urows, ent, z;
+};
+
+struct SpStepArgs {
+    const int32_t *grp_row0, *grp_stage0, *stage_u0, *stage_ebase, *stage_e, *urows;
+    const uint32_t *ent;
+    const uint16_t *z;
+    int ngroups, nchunks, cap_rows;
+    int64_t N, ldb;
+    const uint16_t *Bin;
+    uint16_t *Bout;
+    int16_t *user_out;
+    int32_t *gdiag;
+    int *status;
+};
+
+int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_t> &z,
+                    int cap_rows, PlanHost *out);
+int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent);
+int sparse_cap_rows(int *cap_rows, int *blocks_per_sm);
+int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,
+                int32_t *gdiag, cudaStream_t s);
+int sparse_init_from_dense(const PlanDev &p, const int16_t *A, uint16_t *B0, int16_t *user0,
+                           int32_t *g0, cudaStream_t s);
+int sparse_init_from_csr(const PlanDev &p, const int64_t *row_ptr, const int32_t *col,
+                         const int16_t *val, uint16_t *B0, int16_t *user0, int32_t *g0,
+                         cudaStream_t s);
+int dense_to_csr(const int16_t *A, int64_t N, HostCsr *csr, DevCsr *dcsr, cudaStream_t s);
+
+}  // namespace mp

@@ -1,0 +1,60 @@
+"""CPU-side checks of the C ABI: the library loads, exports every symbol
+include/minplus.h declares, and its host-only word enumeration (Section 2.2,
+Table 1) matches the oracle.  No GPU compute is called here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def mp():
+    import paper_2409_17688_gb300 as mp
+    from paper_2409_17688_gb300 import _build
+    _build.build_library()
+    mp.lib()
+    return mp
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "minplus.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mp_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(mp):
+    names = declared_symbols()
+    assert "mp_minplus_mul" in names and "mp_transfer_power_sequence" in names
+    L = ctypes.CDLL(mp.LIB_PATH)
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_transfer_size_matches_oracle(mp):
+    for n in range(1, 14):
+        assert mp.mp_transfer_size(n) == oracle.transfer_size(n)
+
+
+def test_transfer_words_match_oracle_order(mp):
+    for n in range(1, 10):
+        W = oracle.enumerate_words(n)
+        packed = np.zeros(len(W), dtype=np.uint64)
+        for i in range(n):
+            packed = (packed << np.uint64(2)) | W[:, i].astype(np.uint64)
+        got = mp.mp_transfer_words(n).astype(np.uint64)
+        assert np.array_equal(got, packed), n
+        assert np.all(np.diff(got.astype(np.int64)) > 0)
+
+
+def test_invalid_path_order_rejected(mp):
+    for n in (0, -3, 17):
+        with pytest.raises(mp.MinplusError) as e:
+            mp.mp_transfer_size(n)
+        assert e.value.code == -1
+        assert "path order" in mp.mp_last_error()

@@ -1,0 +1,316 @@
+"""GPU parity: the CUDA path against the CPU oracle, bit-exact.
+
+Every comparison is integer equality: every entry of every power, every
+product and every gamma_2.  Inputs come from paper_2409_17688_gb300.synth
+(seeded) or from the paper's construction; expected values only from oracle/.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_17688_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+INF = oracle.INF16
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def mp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2409_17688_gb300 as mp
+    mp.lib()
+    return mp
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+def to_dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+# ------------------------------------------------------------- a1/a2: A(D_n)
+
+@pytest.mark.parametrize("n", list(range(1, 11)))
+def test_transfer_matrix(mp, torch, n):
+    A, W = mp.mp_build_transfer_matrix(n, words=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(A), oracle.build_transfer(n))
+    assert np.array_equal(host(W).astype(np.uint32), mp.mp_transfer_words(n))
+
+
+def test_transfer_matrix_leading_dimension(mp, torch):
+    N = mp.mp_transfer_size(5)
+    buf = torch.full((N, N + 13), 77, dtype=torch.int16, device="cuda")
+    mp.mp_build_transfer_matrix(5, A=buf)
+    torch.cuda.synchronize()
+    h = host(buf)
+    assert np.array_equal(h[:, :N], oracle.build_transfer(5))
+    assert np.all(h[:, N:] == 77)
+
+
+# ----------------------------------------------------- a5: dense products
+
+SHAPES = [(1, 1, 1), (7, 13, 5), (33, 1, 17), (128, 128, 128), (130, 257, 129),
+          (257, 131, 300), (300, 300, 300), (64, 1000, 40), (5, 3000, 7)]
+
+
+@pytest.mark.parametrize("dtype", [np.int16, np.uint8])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_minplus_mul_random(mp, torch, dtype, shape):
+    M, K, N = shape
+    seed = M * 7919 + K * 31 + N
+    X = synth.block_inf_matrix(M, K, seed, dtype, inf_frac=0.3, block=32)
+    Y = synth.entry_inf_matrix(K, N, seed + 1, dtype, inf_frac=0.2)
+    Z = mp.mp_minplus_mul(to_dev(torch, X), to_dev(torch, Y))
+    torch.cuda.synchronize()
+    assert np.array_equal(host(Z), oracle.minplus_mul(X, Y, threads=THREADS))
+
+
+@pytest.mark.parametrize("dtype", [np.int16, np.uint8])
+def test_minplus_mul_special_values(mp, torch, dtype):
+    inf = INF if dtype == np.int16 else 255
+    rng = np.random.default_rng(2)
+    M, K, N = 150, 260, 140
+    # all INF, no INF, near-INF values (saturation), single INF entries
+    cases = [np.full((M, K), inf, dtype), rng.integers(0, 5, (M, K)).astype(dtype),
+             rng.integers(inf - 3, inf + 1, (M, K)).astype(dtype)]
+    Ys = [rng.integers(0, 30, (K, N)).astype(dtype), np.full((K, N), inf, dtype),
+          rng.integers(inf - 3, inf + 1, (K, N)).astype(dtype)]
+    for X in cases:
+        for Y in Ys:
+            Z = mp.mp_minplus_mul(to_dev(torch, X), to_dev(torch, Y))
+            torch.cuda.synchronize()
+            assert np.array_equal(host(Z), oracle.minplus_mul(X, Y))
+
+
+def test_minplus_mul_whole_inf_blocks(mp, torch):
+    """128-aligned all-INF blocks exercise the block-skip path."""
+    X = synth.block_inf_matrix(384, 512, 5, np.int16, inf_frac=0.5)
+    Y = synth.block_inf_matrix(512, 256, 6, np.int16, inf_frac=0.5)
+    Z = mp.mp_minplus_mul(to_dev(torch, X), to_dev(torch, Y))
+    torch.cuda.synchronize()
+    assert np.array_equal(host(Z), oracle.minplus_mul(X, Y, threads=THREADS))
+
+
+def test_minplus_mul_strided_and_k0(mp, torch):
+    X = synth.entry_inf_matrix(40, 70, 9, np.int16)
+    Y = synth.entry_inf_matrix(70, 50, 10, np.int16)
+    Xb = torch.zeros((40, 77), dtype=torch.int16, device="cuda")
+    Xb[:, :70] = to_dev(torch, X)
+    Zb = torch.full((40, 61), 5, dtype=torch.int16, device="cuda")
+    mp.mp_minplus_mul(Xb[:, :70], to_dev(torch, Y), Zb[:, :50])
+    torch.cuda.synchronize()
+    h = host(Zb)
+    assert np.array_equal(h[:, :50], oracle.minplus_mul(X, Y))
+    assert np.all(h[:, 50:] == 5)
+    Z0 = mp.mp_minplus_mul(torch.zeros((4, 0), dtype=torch.int16, device="cuda"),
+                           torch.zeros((0, 6), dtype=torch.int16, device="cuda"))
+    torch.cuda.synchronize()
+    assert np.all(host(Z0) == INF)
+
+
+def test_minplus_mul_alias_rejected(mp, torch):
+    X = torch.zeros((64, 64), dtype=torch.int16, device="cuda")
+    Y = torch.zeros((64, 64), dtype=torch.int16, device="cuda")
+    with pytest.raises(mp.MinplusError) as e:
+        mp.mp_minplus_mul(X, Y, X)
+    assert e.value.code == -2
+
+
+@pytest.mark.parametrize("dtype", [np.int16, np.uint8])
+def test_minplus_mul_8192_sampled(mp, torch, dtype):
+    """The N = 8192 product with 40% INF 128-blocks, checked on sampled rows
+    and columns (each computed by the oracle on its own)."""
+    N = 8192
+    X = synth.block_inf_matrix(N, N, 1, dtype, inf_frac=0.4)
+    Y = synth.block_inf_matrix(N, N, 2, dtype, inf_frac=0.4)
+    Z = host(mp.mp_minplus_mul(to_dev(torch, X), to_dev(torch, Y)))
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([[0, N - 1], rng.choice(N, 14, replace=False)])
+    cols = np.concatenate([[0, N - 1], rng.choice(N, 6, replace=False)])
+    for i in rows:
+        assert np.array_equal(Z[i:i + 1], oracle.minplus_mul(X[i:i + 1], Y, threads=THREADS)), i
+    for j in cols:
+        assert np.array_equal(Z[:, j:j + 1], oracle.minplus_mul(X, Y[:, j:j + 1], threads=THREADS)), j
+
+
+# ------------------------------------------------- a3/a4: the power chain
+
+@pytest.mark.parametrize("n,kmax", [(1, 40), (2, 60), (3, 30), (4, 50), (5, 80), (6, 200), (7, 200)])
+def test_transfer_chain_every_power(mp, torch, n, kmax):
+    """Every entry of every power and every min-diagonal, bit-exact."""
+    P, g = mp.mp_transfer_power_sequence(n, kmax)
+    torch.cuda.synchronize()
+    A = oracle.build_transfer(n)
+    Po, go = oracle.power_sequence(A, kmax, left_mul=True, threads=THREADS)
+    assert np.array_equal(host(g), go)
+    Ph = host(P)
+    for k in range(kmax):
+        assert np.array_equal(Ph[k], Po[k]), k + 1
+
+
+@pytest.mark.parametrize("n", [8, 9])
+def test_transfer_chain_sampled_rows(mp, torch, n):
+    """n = 8, 9 with k_max = 200: every power on sampled rows (the oracle's own
+    row chain), every min-diagonal, and Table 4's whole-matrix identity
+    A^{n0+a} = b + A^{n0} on the GPU powers."""
+    kmax = 200
+    P, g = mp.mp_transfer_power_sequence(n, kmax)
+    torch.cuda.synchronize()
+    A = oracle.build_transfer(n)
+    N = A.shape[0]
+    rng = np.random.default_rng(n)
+    rows = np.unique(np.concatenate([[0, N - 1], rng.choice(N, 62, replace=False)]))
+    R = oracle.power_rows(A, rows, kmax, threads=THREADS)
+    for t, i in enumerate(rows):
+        got = host(P[:, i, :])
+        assert np.array_equal(got, R[t]), i
+    # min-diagonal from the oracle's K=50 chain (cheap in the A (x) P order)
+    _, go = oracle.power_sequence(A, 50, keep_powers=False, threads=THREADS)
+    assert np.array_equal(host(g)[:50], go)
+    n0, a, b = {8: (25, 3, 10), 9: (22, 3, 11)}[n]
+    lhs = P[n0 + a - 1].to(torch.int32)
+    rhs = P[n0 - 1].to(torch.int32) + b
+    assert bool(torch.equal(lhs, rhs))
+    # Lemma 1: the relation propagates to every later power
+    assert bool(torch.equal(P[kmax - 1].to(torch.int32), P[kmax - 1 - a].to(torch.int32) + b))
+
+
+def test_power_sequence_generic_matches_transfer(mp, torch):
+    """The generic entry point on the dense A(D_n) (it detects the
+    column-constant labels) agrees with the transfer chain and the oracle."""
+    n, kmax = 6, 40
+    A = mp.mp_build_transfer_matrix(n)
+    P, g = mp.mp_minplus_power_sequence(A, kmax)
+    P2, g2 = mp.mp_transfer_power_sequence(n, kmax)
+    torch.cuda.synchronize()
+    Po, go = oracle.power_sequence(oracle.build_transfer(n), kmax, threads=THREADS)
+    assert np.array_equal(host(P), Po) and np.array_equal(host(g), go)
+    assert torch.equal(P, P2) and torch.equal(g, g2)
+
+
+@pytest.mark.parametrize("N,density,seed", [(50, 0.1, 1), (300, 0.05, 2), (700, 0.02, 3),
+                                            (129, 0.2, 4)])
+def test_power_sequence_sparse_general(mp, torch, N, density, seed):
+    """A sparse A with arbitrary labels (per-entry add-min path)."""
+    A = synth.entry_inf_matrix(N, N, seed, np.int16, inf_frac=1 - density, lo=0, hi=9)
+    kmax = 12
+    P, g = mp.mp_minplus_power_sequence(to_dev(torch, A), kmax)
+    torch.cuda.synchronize()
+    Po, go = oracle.power_sequence(A, kmax, threads=THREADS)
+    assert np.array_equal(host(P), Po)
+    assert np.array_equal(host(g), go)
+
+
+def test_power_sequence_dense(mp, torch):
+    A = synth.entry_inf_matrix(200, 200, 8, np.int16, inf_frac=0.3, lo=0, hi=9)
+    P, g = mp.mp_minplus_power_sequence(to_dev(torch, A), 6)
+    torch.cuda.synchronize()
+    Po, go = oracle.power_sequence(A, 6, threads=THREADS)
+    assert np.array_equal(host(P), Po) and np.array_equal(host(g), go)
+
+
+def test_power_sequence_without_powers(mp, torch):
+    _, g = mp.mp_transfer_power_sequence(7, 120, keep_powers=False)
+    torch.cuda.synchronize()
+    _, go = oracle.power_sequence(oracle.build_transfer(7), 120, keep_powers=False, threads=THREADS)
+    assert np.array_equal(host(g), go)
+
+
+# ------------------------------------------------------------ K3, a6
+
+def test_diag_min_and_min_trace(mp, torch):
+    rng = np.random.default_rng(12)
+    for N in (1, 31, 33, 100, 257):
+        X = synth.entry_inf_matrix(N, N, N, np.int16, inf_frac=0.3)
+        Y = synth.entry_inf_matrix(N, N, N + 1, np.int16, inf_frac=0.3)
+        d = mp.mp_diag_min(to_dev(torch, X))
+        t = mp.mp_min_trace(to_dev(torch, X), to_dev(torch, Y))
+        torch.cuda.synchronize()
+        assert int(host(d)[0]) == oracle.diag_min(X)
+        assert int(host(t)[0]) == oracle.diag_min(oracle.minplus_mul(X, Y))
+
+
+@pytest.mark.parametrize("n,m", [(1, 3), (1, 101), (2, 7), (3, 12), (4, 5), (5, 37), (6, 64),
+                                 (7, 100), (7, 257), (8, 49), (9, 40)])
+def test_gamma2_cylinder(mp, n, m):
+    assert mp.mp_gamma2_cylinder(n, m) == oracle.gamma2(n, m, threads=THREADS)
+
+
+def test_gamma2_cylinder_large_m_uses_recurrence_identity(mp):
+    """Large m (repeated-squaring path) against Table 4/5's closed form:
+    gamma_2 = ceil(b m / a) + alpha for m >= n0 (Section 4)."""
+    import math
+    cases = {3: (6, 8, set()), 8: (3, 10, set()), 9: (3, 11, set())}
+    for n, (a, b, ones) in cases.items():
+        for m in (500, 1000, 1024, 2000):
+            want = math.ceil(b * m / a) + (1 if (m % a) in ones else 0)
+            assert mp.mp_gamma2_cylinder(n, m) == want, (n, m)
+
+
+def test_gamma2_cylinder_errors(mp):
+    with pytest.raises(mp.MinplusError) as e:
+        mp.mp_gamma2_cylinder(3, 2)
+    assert e.value.code == -1
+    with pytest.raises(mp.MinplusError) as e:
+        mp.mp_gamma2_cylinder(10, 4000)
+    assert e.value.code == -4
+
+
+# ------------------------------------------------------------------ a7
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batched_matches_single(mp, torch, mode):
+    sizes = [64, 100, 129, 300, 517, 77, 1000]
+    probs, want = [], []
+    for i, N in enumerate(sizes):
+        dt = np.int16 if i % 3 else np.uint8
+        X = synth.block_inf_matrix(N, N, 100 + i, dt, inf_frac=0.3)
+        Y = synth.block_inf_matrix(N, N, 200 + i, dt, inf_frac=0.3)
+        Xd, Yd = to_dev(torch, X), to_dev(torch, Y)
+        Zd = torch.empty_like(Xd)
+        probs.append((Xd, Yd, Zd))
+        want.append(oracle.minplus_mul(X, Y, threads=THREADS))
+    mp.mp_minplus_mul_batched(probs, mode=mode)
+    torch.cuda.synchronize()
+    for (_, _, Zd), w in zip(probs, want):
+        assert np.array_equal(host(Zd), w)
+
+
+def test_batched_alias_rejected(mp, torch):
+    X = torch.zeros((64, 64), dtype=torch.int16, device="cuda")
+    Z = torch.zeros((64, 64), dtype=torch.int16, device="cuda")
+    with pytest.raises(mp.MinplusError) as e:
+        mp.mp_minplus_mul_batched([(X, X, Z), (Z, X, X.clone())])
+    assert e.value.code == -2
+
+
+# --------------------------------------------------------------- misc
+
+def test_dpx_peak_positive(mp):
+    for v in (0, 1, 2):
+        assert mp.mp_dpx_peak(v, 4096) > 1e12
+
+
+def test_device_status_clean(mp):
+    assert mp.mp_device_status() == 0
+
+
+def test_gamma2_table(mp):
+    for n in (2, 5, 8):
+        t = mp.mp_gamma2_table(n, 60)
+        assert np.array_equal(t, oracle.gamma2_range(n, 60, threads=THREADS))
