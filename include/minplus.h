@@ -99,6 +99,25 @@ int mp_minplus_mul(const void *X, const void *Y, void *Z, int64_t M, int64_t N,
                    int64_t K, int64_t ldx, int64_t ldy, int64_t ldz, int dtype,
                    void *stream);
 
+/* The same product for callers that cannot allocate device memory: code
+ * running where cudaMalloc is unavailable or forbidden (inside a memory
+ * budget owned by another allocator, a real-time path that must not call
+ * the allocator, a plugin whose host owns all device memory).  The paper
+ * has no counterpart; it is a deployment variant of mp_minplus_mul.
+ * It allocates nothing: the only scratch of the product, the per-operand
+ * occupancy masks, lives in a fixed 1 MiB device array inside the library
+ * that every GPU which loads the library holds until the process exits.
+ * Arguments, results and errors as mp_minplus_mul, plus MP_EINVAL when
+ * ceil(M/128)*ceil(K/128) + ceil(K/128)*ceil(N/128) exceeds 1048576 (about
+ * N = 90000 for square operands).  The first call on a device looks up the
+ * array's device address with cudaGetSymbolAddress (with that device
+ * current); make that first call before any stream capture.  Every call
+ * shares the array: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race on it and must be serialized by the caller. */
+int mp_minplus_mul_noalloc(const void *X, const void *Y, void *Z, int64_t M, int64_t N,
+                           int64_t K, int64_t ldx, int64_t ldy, int64_t ldz, int dtype,
+                           void *stream);
+
 /* ---- a3/a4: the power chain with the gamma_2 readout -----------------------
  * Algorithm 2 and Theorem 2 / Algorithm 5: P_1 = A, P_k = A (x) P_{k-1} for
  * k = 2..k_max (equal to P_{k-1} (x) A by associativity), and

@@ -15,6 +15,9 @@
 namespace mp {
 
 int dpx_peak(int variant, int64_t iters, double *ops_per_s);
+int dense_minplus_noalloc(const void *X, const void *Y, void *Z, int64_t M, int64_t N,
+                          int64_t K, int64_t ldx, int64_t ldy, int64_t ldz, int dtype,
+                          cudaStream_t s);
 int batched_run(const mp_problem *probs, int count, int mode, cudaStream_t s);
 
 // ------------------------------------------------------------------ errors
@@ -252,6 +255,23 @@ int mp_minplus_mul(const void *X, const void *Y, void *Z, int64_t M, int64_t N, 
         ranges_overlap(Z, zb, Y, span_bytes(K, N, ldy, e)))
         return set_error(MP_EALIAS, "Z overlaps X or Y");
     return dense_minplus(X, Y, Z, M, N, K, ldx, ldy, ldz, dtype, nullptr, (cudaStream_t)stream);
+}
+
+int mp_minplus_mul_noalloc(const void *X, const void *Y, void *Z, int64_t M, int64_t N,
+                           int64_t K, int64_t ldx, int64_t ldy, int64_t ldz, int dtype,
+                           void *stream) {
+    if (dtype != MP_I16 && dtype != MP_U8) return set_error(MP_EINVAL, "dtype %d", dtype);
+    if (M < 0 || N < 0 || K < 0) return set_error(MP_EINVAL, "negative size");
+    if (M == 0 || N == 0) return MP_OK;
+    if (!Z || (K > 0 && (!X || !Y))) return set_error(MP_EINVAL, "NULL matrix pointer");
+    if (ldx < std::max<int64_t>(K, 1) || ldy < N || ldz < N)
+        return set_error(MP_EINVAL, "leading dimension too small");
+    const size_t e = dtype == MP_I16 ? 2 : 1;
+    const size_t zb = span_bytes(M, N, ldz, e);
+    if (ranges_overlap(Z, zb, X, span_bytes(M, K, ldx, e)) ||
+        ranges_overlap(Z, zb, Y, span_bytes(K, N, ldy, e)))
+        return set_error(MP_EALIAS, "Z overlaps X or Y");
+    return dense_minplus_noalloc(X, Y, Z, M, N, K, ldx, ldy, ldz, dtype, (cudaStream_t)stream);
 }
 
 int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max, int16_t *powers_opt,

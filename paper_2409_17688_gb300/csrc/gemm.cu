@@ -16,6 +16,7 @@
 // INF in X or in Y (a precomputed occupancy mask per operand) cannot lower
 // any minimum, so their K-range is skipped for the tile.
 #include <algorithm>
+#include <mutex>
 
 #include "mp_internal.cuh"
 
@@ -498,6 +499,93 @@ int batched_run(const mp_problem *probs, int count, int mode, cudaStream_t s) {
         MP_CUDA_TRY(cudaGetLastError());
     }
     return MP_OK;
+}
+
+// ------------------------------------------------- no-allocation variant
+// mp_minplus_mul_noalloc: the same product for callers that cannot
+// allocate device memory (see include/minplus.h).  The only scratch of the
+// dense product -- the two occupancy masks -- lives in this fixed array,
+// which every GPU that loads the library holds until the process exits.
+
+namespace {
+
+constexpr size_t kNoAllocMaskBytes = (size_t)1 << 20;  // 1 MiB of mask bytes
+static __device__ __align__(256) uint8_t g_noalloc_masks[kNoAllocMaskBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[256] = {};
+
+// Device address of g_noalloc_masks on the current device, looked up once
+// per device with that device current.  In host code the array's name is
+// only a host-side stand-in, never a device address.
+int noalloc_scratch(uint8_t **out) {
+    int dev = -1;
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return set_error(MP_EINVAL, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_masks);
+        if (e != cudaSuccess || !p)
+            return set_error(MP_ECUDA, "cudaGetSymbolAddress(mask scratch) failed: %s",
+                             cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<uint8_t *>(g_noalloc_addr[dev]);
+    return MP_OK;
+}
+
+template <typename T>
+int run_dense_noalloc(const T *X, const T *Y, T *Z, int64_t M, int64_t N, int64_t K,
+                      int64_t ldx, int64_t ldy, int64_t ldz, cudaStream_t s) {
+    const int64_t elems16 = 16 / (int64_t)sizeof(T);
+    int vecx = ((uintptr_t)X % 16 == 0) && (ldx % elems16 == 0);
+    int vecy = ((uintptr_t)Y % 16 == 0) && (ldy % elems16 == 0);
+    int vecz = ((uintptr_t)Z % 16 == 0) && (ldz % 8 == 0);
+    const int64_t mb = (M + BM - 1) / BM, nb = (N + BN - 1) / BN;
+    const int64_t kb = (K + MASK_BLOCK - 1) / MASK_BLOCK;
+    const uint8_t *xm = nullptr, *ym = nullptr;
+    if (K > 0) {
+        uint8_t *base = nullptr;
+        MP_TRY(noalloc_scratch(&base));
+        // every mask byte the product reads is written here first, so stale
+        // contents of an earlier call never matter
+        uint8_t *xmw = base, *ymw = base + mb * kb;
+        block_mask_kernel<T><<<dim3((unsigned)kb, (unsigned)mb), 256, 0, s>>>(X, M, K, ldx, xmw, kb);
+        block_mask_kernel<T><<<dim3((unsigned)nb, (unsigned)kb), 256, 0, s>>>(Y, K, N, ldy, ymw, nb);
+        MP_CUDA_TRY(cudaGetLastError());
+        xm = xmw;
+        ym = ymw;
+    }
+    dim3 grid((unsigned)nb, (unsigned)mb);
+    TileArgs<T> ta{X, Y, Z, M, N, K, ldx, ldy, ldz, xm, ym, kb, nb, vecx, vecy, vecz, nullptr};
+    dense_minplus_kernel<T><<<grid, THREADS, 0, s>>>(ta);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+}  // namespace
+
+int dense_minplus_noalloc(const void *X, const void *Y, void *Z, int64_t M, int64_t N,
+                          int64_t K, int64_t ldx, int64_t ldy, int64_t ldz, int dtype,
+                          cudaStream_t s) {
+    if (M == 0 || N == 0) return MP_OK;
+    const int64_t mb = (M + BM - 1) / BM, nb = (N + BN - 1) / BN;
+    const int64_t kb = (K + MASK_BLOCK - 1) / MASK_BLOCK;
+    if (mb > 65535)
+        return set_error(MP_EINVAL, "M = %lld too large for one launch", (long long)M);
+    if ((double)(mb * kb + kb * nb) > (double)kNoAllocMaskBytes)
+        return set_error(MP_EINVAL,
+                         "problem needs %lld mask bytes; the fixed scratch holds %zu "
+                         "(ceil(M/128)*ceil(K/128) + ceil(K/128)*ceil(N/128) must not exceed it)",
+                         (long long)(mb * kb + kb * nb), kNoAllocMaskBytes);
+    if (dtype == MP_I16)
+        return run_dense_noalloc<uint16_t>((const uint16_t *)X, (const uint16_t *)Y,
+                                           (uint16_t *)Z, M, N, K, ldx, ldy, ldz, s);
+    if (dtype == MP_U8)
+        return run_dense_noalloc<uint8_t>((const uint8_t *)X, (const uint8_t *)Y, (uint8_t *)Z,
+                                          M, N, K, ldx, ldy, ldz, s);
+    return set_error(MP_EINVAL, "unknown dtype %d", dtype);
 }
 
 }  // namespace mp
