@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["chain9", "chain8", "gemm8192", "gemm8192u8"],
+                    help="run one small case for an ncu capture and exit")
     return ap.parse_args()
 
 
@@ -346,8 +348,34 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_profile(what: str):
+    """A short, self-contained case for ncu: a few chains or one product."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2409_17688_gb300 as mp
+    from paper_2409_17688_gb300 import synth
+    if what.startswith("chain"):
+        n = int(what[5:])
+        for _ in range(3):
+            mp.mp_transfer_power_sequence(n, 12, keep_powers=False)
+    else:
+        dt = np.uint8 if what.endswith("u8") else np.int16
+        X = torch.from_numpy(synth.block_inf_matrix(8192, 8192, 1, dt, inf_frac=0.4)).cuda()
+        Y = torch.from_numpy(synth.block_inf_matrix(8192, 8192, 2, dt, inf_frac=0.4)).cuda()
+        for _ in range(2):
+            mp.mp_minplus_mul(X, Y)
+    torch.cuda.synchronize()
+    print(f"profile case {what} done")
+
+
 def main():
     args = parse()
+    if args.profile:
+        run_profile(args.profile)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -141,10 +141,10 @@ static int transfer_entry(int n, cudaStream_t s, TransferEntry **out) {
     if (nnz)
         MP_CUDA_TRY(cudaMemcpyAsync(e->csr.val.p, csr.val.data(), (size_t)nnz * 2,
                                     cudaMemcpyHostToDevice, s));
-    int cap = 0, bps = 0;
-    MP_TRY(sparse_cap_rows(&cap, &bps));
+    int cap = 0, blob_cap = 0, grid = 0;
+    MP_TRY(sparse_cap_rows(&cap, &blob_cap, &grid));
     PlanHost ph;
-    MP_TRY(plan_build_host(csr, true, z, cap, &ph));
+    MP_TRY(plan_build_host(csr, true, z, cap, blob_cap, grid, &ph));
     MP_TRY(plan_upload(ph, &e->plan, s, true));
     MP_CUDA_TRY(cudaStreamSynchronize(s));
     e->h2d_bytes = masks.size() * sizeof(WordMasks) + (size_t)(N + 1) * 8 + (size_t)nnz * 2 +
@@ -309,10 +309,10 @@ int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max, int16_t *p
     std::vector<uint16_t> z((size_t)N, 0);
     if (colconst)
         for (int64_t p = 0; p < N; ++p) z[p] = (uint16_t)std::max(zc[p], 0);
-    int cap = 0, bps = 0;
-    MP_TRY(sparse_cap_rows(&cap, &bps));
+    int cap = 0, blob_cap = 0, grid = 0;
+    MP_TRY(sparse_cap_rows(&cap, &blob_cap, &grid));
     PlanHost ph;
-    MP_TRY(plan_build_host(csr, colconst, z, cap, &ph));
+    MP_TRY(plan_build_host(csr, colconst, z, cap, blob_cap, grid, &ph));
     PlanDev plan;
     MP_TRY(plan_upload(ph, &plan, s, false));
     DevBuf B;

@@ -12,22 +12,29 @@
 //
 // Work decomposition.  Output rows are grouped greedily (consecutive rows,
 // at most 64) so that the union U of the rows they gather stays small; the
-// columns are cut into chunks of 64.  A work item is (group, chunk).  A
-// persistent CTA walks its items; for each it streams the U rows' 64-column
-// segments (128 B each) into shared memory with 1-D TMA bulk copies that
-// complete on an mbarrier, double-buffered so the copies of the next item
-// overlap the arithmetic of the current one.  A U list longer than one
-// buffer is cut into stages, and the per-row minima carry over in
-// registers.  Each warp owns rows of the group; its 32 lanes own the 64
-// columns as 16-bit pairs, so every shared-memory read of a gathered row is
-// one conflict-free 128-byte wavefront and the gather index is uniform
-// across the warp.  Rows of the next power go to a padded internal buffer
-// (and, when asked, to the caller's power array); the diagonal entries are
-// min-reduced per item in shared memory and folded into g[k] with one
-// atomicMin.
+// columns are cut into chunks of 64.  A work item is (group, chunk); a U
+// list longer than one buffer is cut into stages whose per-row minima carry
+// over in registers.  A persistent CTA (one per SM, 16 warps) walks its
+// items through two shared-memory buffers.  While it computes one stage,
+// all its threads stream the next stage into the other buffer with 16-byte
+// cp.async copies: the 128-byte segments (64 columns) of the U rows, and
+// one contiguous "blob" holding the stage's row range and per-row entry
+// lists (32-bit shared-memory byte offsets of the gathered rows).  The plan
+// cuts every stage into tasks -- a row, or a segment of a long row -- and
+// deals them to the 16 warps longest first, so no warp carries much more
+// than its share (row lengths range from 8 to 2^n entries).  A task folds
+// its minimum into the row's accumulator in shared memory with 32-bit
+// shared-memory atomicMin; after the last stage of an item one pass writes
+// the rows out.  The 32 lanes of a warp own the 64 columns as 16-bit
+// pairs, so every read of a gathered row is one conflict-free 128-byte
+// wavefront and every entry read is a broadcast.
+// (1-D TMA bulk copies were tried first for the row segments: at 128 bytes
+// each they issued far too slowly to feed the arithmetic.)
+// Rows of the next power go to a padded internal buffer (and, when asked,
+// to the caller's power array); the diagonal entries are min-reduced in
+// registers and folded into g[k] with one atomicMin per warp.
 #include <algorithm>
 #include <cstring>
-#include <unordered_map>
 
 #include "mp_internal.cuh"
 #include "spmm.cuh"
@@ -36,149 +43,144 @@ namespace mp {
 
 namespace {
 
-constexpr int kThreads = 512;  // 16 warps
+constexpr int kThreads = 512;                    // 16 warps
 constexpr int kWarps = kThreads / 32;
-constexpr int kGroupMax = 64;  // rows per group: at most 4 per warp
+constexpr int kGroupMax = 64;                     // rows per group: at most 4 per warp
 constexpr int kRowsPerWarp = kGroupMax / kWarps;
-constexpr int kChunk = 64;     // columns per work item
+constexpr int kChunk = 64;                        // columns per work item
 constexpr int kRowBytes = kChunk * 2;
-constexpr int kHeader = 128;   // barriers and per-item scratch ahead of the buffers
+constexpr int kBlobHeader = 32;  // words: row0, nrows, flags, ntasks, pad, task table (17)
+constexpr int kAccBytes = kGroupMax * kChunk * 4;  // per-row accumulators, one word per column
+constexpr int kStageRowsMax = 768;                // U rows per stage (register-staged indices)
+constexpr int kRowLoads = kStageRowsMax * (kRowBytes / 16) / kThreads;  // 12 per thread
 
-// ---------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
                  : "memory");
 }
-__device__ __forceinline__ void fence_barrier_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-// Bounded wait: false when kSpinLimit polls pass without the phase flipping.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes,
-                                            uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ uint32_t lds32(const uint8_t *p) {
     return *reinterpret_cast<const uint32_t *>(p);
 }
 
-// Warp 0 streams the U rows of stage s (columns of chunk) into buf.
-__device__ __forceinline__ void issue_stage(const SpStepArgs &a, int64_t chunk, int s,
-                                            uint8_t *buf, uint64_t *bar, int lane) {
-    const int u0 = a.stage_u0[s], u1 = a.stage_u0[s + 1];
-    if (lane == 0) mbar_expect_tx(bar, (uint32_t)(u1 - u0) * kRowBytes);
-    __syncwarp();
-    const uint16_t *base = a.Bin + chunk * kChunk;
-    for (int u = u0 + lane; u < u1; u += 32)
-        tma_load_1d(buf + (size_t)(u - u0) * kRowBytes, base + (int64_t)a.urows[u] * a.ldb,
-                    kRowBytes, bar);
+// Row indices of one unit, one register per 16-byte piece this thread copies.
+struct RowIdx {
+    int32_t r[kRowLoads];
+};
+
+__device__ __forceinline__ void load_row_idx(const SpStepArgs &a, const UnitDesc &u, RowIdx &ri) {
+    const int pieces = (u.u1 - u.u0) * (kRowBytes / 16);
+#pragma unroll
+    for (int j = 0; j < kRowLoads; ++j) {
+        const int idx = threadIdx.x + j * kThreads;
+        ri.r[j] = idx < pieces ? __ldg(a.urows + u.u0 + (idx >> 3)) : -1;
+    }
+}
+
+// All threads stream one unit into buf: its blob, then the 64-column
+// segments of its gathered rows (indices already in registers).
+__device__ __forceinline__ void stage_in(const SpStepArgs &a, const UnitDesc &u,
+                                         const RowIdx &ri, uint8_t *buf, size_t blob_bytes) {
+    const int tid = threadIdx.x;
+    const uint32_t *bsrc = a.blob + u.bo;
+    for (int c = tid; c < (u.bw >> 2); c += kThreads) cp_async16(buf + (size_t)c * 16, bsrc + 4 * c);
+    const uint16_t *base = a.Bin + (int64_t)u.chunk * kChunk;
+    uint8_t *rows = buf + blob_bytes;
+#pragma unroll
+    for (int j = 0; j < kRowLoads; ++j) {
+        const int idx = tid + j * kThreads;
+        if (ri.r[j] >= 0)
+            cp_async16(rows + (size_t)(idx >> 3) * kRowBytes + (idx & 7) * 16,
+                       base + (int64_t)ri.r[j] * a.ldb + (idx & 7) * 8);
+    }
+}
+
+__device__ __forceinline__ UnitDesc load_unit(const SpStepArgs &a, int k, int k_end) {
+    UnitDesc u;
+    if (k < k_end) {
+        u = a.units[k];
+    } else {
+        u.chunk = -1;
+        u.u0 = u.u1 = u.bw = 0;
+        u.bo = 0;
+        u.last = 0;
+        u.pad = 0;
+    }
+    return u;
 }
 
 template <bool kColConst>
 __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    int32_t *dmin = reinterpret_cast<int32_t *>(smem + 16);
-    uint8_t *bufs = smem + kHeader;
-    const size_t buf_bytes = (size_t)a.cap_rows * kRowBytes;
+    const size_t blob_bytes = (size_t)a.blob_cap * 4;
+    const size_t buf_bytes = blob_bytes + (size_t)a.cap_rows * kRowBytes;
+    uint32_t *accs = reinterpret_cast<uint32_t *>(smem + 2 * buf_bytes);  // [64 rows][64 cols]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // the last row of each buffer is the padding row: larger than any value
+    // the last gathered row of each buffer is the padding row: above any value
     if (threadIdx.x < 64) {
-        uint8_t *infrow = bufs + (threadIdx.x >> 5) * buf_bytes + (size_t)(a.cap_rows - 1) * kRowBytes;
+        uint8_t *infrow = smem + (threadIdx.x >> 5) * buf_bytes + blob_bytes +
+                          (size_t)(a.cap_rows - 1) * kRowBytes;
         reinterpret_cast<uint32_t *>(infrow)[lane] = 0xFFFFFFFFu;
     }
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        dmin[0] = dmin[1] = (int32_t)kInf16;
-        fence_barrier_init();
-    }
-    __syncthreads();
+    for (int i = threadIdx.x; i < kGroupMax * kChunk; i += kThreads) accs[i] = kInf16;
 
-    const int64_t total = (int64_t)a.ngroups * a.nchunks;
-    int64_t w = blockIdx.x;
-    if (w >= total) return;
-    int g = (int)(w % a.ngroups);
-    int s = a.grp_stage0[g], s_end = a.grp_stage0[g + 1];
-    if (warp == 0) issue_stage(a, w / a.ngroups, s, bufs, &bar[0], lane);
+    // this CTA's units, in order; descriptors run two units ahead of the
+    // copies and row indices one unit ahead, so no unit waits on a global load
+    const int k0 = a.cta_unit0[blockIdx.x], k_end = a.cta_unit0[blockIdx.x + 1];
+    if (k0 >= k_end) return;
+    UnitDesc cur = load_unit(a, k0, k_end);
+    RowIdx idx;
+    load_row_idx(a, cur, idx);
+    stage_in(a, cur, idx, smem, blob_bytes);
+    cp_async_commit();
+    UnitDesc nxt = load_unit(a, k0 + 1, k_end);
+    if (nxt.chunk >= 0) load_row_idx(a, nxt, idx);
+    UnitDesc nxt2 = load_unit(a, k0 + 2, k_end);
 
-    uint32_t acc[kRowsPerWarp];
-    uint32_t phases = 0;
-    int unit = 0, item = 0;
-    while (true) {
-        const int b = unit & 1;
-        // the next unit: the next stage of this item, or the first of the next item
-        int64_t wn = w;
-        int gn = g, sn = s + 1, sn_end = s_end;
-        if (sn >= s_end) {
-            wn = w + gridDim.x;
-            if (wn < total) {
-                gn = (int)(wn % a.ngroups);
-                sn = a.grp_stage0[gn];
-                sn_end = a.grp_stage0[gn + 1];
-            }
+    int32_t dmin = (int32_t)kInf16;
+    for (int k = k0; k < k_end; ++k) {
+        const int b = (k - k0) & 1;
+        if (nxt.chunk >= 0) {
+            stage_in(a, nxt, idx, smem + (b ^ 1) * buf_bytes, blob_bytes);
+            cp_async_commit();
+            if (nxt2.chunk >= 0) load_row_idx(a, nxt2, idx);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
-        const bool has_next = wn < total;
-        if (has_next && warp == 0)
-            issue_stage(a, wn / a.ngroups, sn, bufs + (b ^ 1) * buf_bytes, &bar[b ^ 1], lane);
+        const UnitDesc nxt3 = load_unit(a, k + 3, k_end);
+        __syncthreads();
 
-        bool ok = mbar_wait_bounded(&bar[b], (phases >> b) & 1u);
-        phases ^= 1u << b;
-        if (__syncthreads_or(!ok)) {
-            // a copy never landed: latch the error, let the other buffer's copy
-            // (if any) finish so nothing writes shared memory after exit, return
-            if (threadIdx.x == 0) atomicExch(a.status, MP_ETIMEOUT);
-            if (has_next) mbar_wait_bounded(&bar[b ^ 1], (phases >> (b ^ 1)) & 1u);
-            return;
-        }
-
-        const int64_t chunk = w / a.ngroups;
-        const int64_t c0 = chunk * kChunk;
-        const int row0 = a.grp_row0[g], nrows = a.grp_row0[g + 1] - row0;
-        const bool first = (s == a.grp_stage0[g]), last = (s + 1 == s_end);
-        const int eb = a.stage_ebase[s];
-        const uint8_t *sb = bufs + b * buf_bytes + lane * 4;
-
-#pragma unroll
-        for (int ri = 0; ri < kRowsPerWarp; ++ri) {
-            const int r = warp + ri * kWarps;
-            if (first) acc[ri] = kInf16x2;
-            if (r >= nrows) continue;
-            const int e0 = a.stage_e[eb + r], e1 = a.stage_e[eb + r + 1];
-            const uint4 *E = reinterpret_cast<const uint4 *>(a.ent + e0);
+        const uint8_t *buf = smem + b * buf_bytes;
+        const uint32_t *blob = reinterpret_cast<const uint32_t *>(buf);
+        const int row0 = (int)blob[0], nrows = (int)blob[1];
+        const int ntasks = (int)blob[3];
+        const uint32_t *tasks = blob + kBlobHeader;
+        const uint16_t *zs = reinterpret_cast<const uint16_t *>(tasks + ((2 * ntasks + 7) & ~7));
+        const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8;
+        const uint8_t *sb = buf + blob_bytes + lane * 4;
+        const int64_t c0 = (int64_t)cur.chunk * kChunk;
+        const int t_end = (int)blob[8 + warp + 1];
+        for (int t = (int)blob[8 + warp]; t < t_end; ++t) {
+            const uint32_t t0 = tasks[2 * t];
+            const int r = (int)(t0 >> 16), e0 = (int)(t0 & 0xFFFFu), e1 = (int)tasks[2 * t + 1];
+            uint32_t m;
             if (kColConst) {
                 uint32_t m0 = 0xFFFFFFFFu, m1 = 0xFFFFFFFFu;
-                for (int t = 0; t < (e1 - e0) >> 3; ++t) {
-                    const uint4 p = __ldg(E + 2 * t), q = __ldg(E + 2 * t + 1);
+#pragma unroll 2
+                for (int e = e0; e < e1; e += 8) {
+                    const uint4 p = *reinterpret_cast<const uint4 *>(ents + e);
+                    const uint4 q = *reinterpret_cast<const uint4 *>(ents + e + 4);
                     const uint32_t v0 = lds32(sb + p.x), v1 = lds32(sb + p.y);
                     const uint32_t v2 = lds32(sb + p.z), v3 = lds32(sb + p.w);
                     const uint32_t v4 = lds32(sb + q.x), v5 = lds32(sb + q.y);
@@ -188,23 +190,34 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
                     m0 = __vimin3_u16x2(m0, v4, v5);
                     m1 = __vimin3_u16x2(m1, v6, v7);
                 }
-                acc[ri] = __vimin3_u16x2(acc[ri], m0, m1);
+                m = __vminu2(m0, m1);
             } else {
-                uint32_t m = acc[ri];
-                // two entries (offset, label pair) per 16-byte load, four per iteration
-                for (int t = 0; t < (e1 - e0) >> 3; ++t) {
-                    const uint4 p = __ldg(E + 2 * t), q = __ldg(E + 2 * t + 1);
+                m = 0xFFFFFFFFu;
+                // two entries (offset, label pair) per 16-byte read, four per iteration
+#pragma unroll 2
+                for (int e = e0; e < e1; e += 8) {
+                    const uint4 p = *reinterpret_cast<const uint4 *>(ents + e);
+                    const uint4 q = *reinterpret_cast<const uint4 *>(ents + e + 4);
                     m = __viaddmin_u16x2(lds32(sb + p.x), p.y, m);
                     m = __viaddmin_u16x2(lds32(sb + p.z), p.w, m);
                     m = __viaddmin_u16x2(lds32(sb + q.x), q.y, m);
                     m = __viaddmin_u16x2(lds32(sb + q.z), q.w, m);
                 }
-                acc[ri] = m;
             }
-            if (last) {
+            uint32_t *acc = accs + r * kChunk + 2 * lane;
+            atomicMin(acc, m & 0xFFFFu);
+            atomicMin(acc + 1, m >> 16);
+        }
+        if (cur.last) {
+            __syncthreads();
+            // write the item's rows: min(INF, .) since the accumulators start at INF
+            for (int r = warp; r < nrows; r += kWarps) {
+                uint32_t *acc = accs + r * kChunk + 2 * lane;
+                const uint32_t v = acc[0] | (acc[1] << 16);
+                acc[0] = kInf16;
+                acc[1] = kInf16;
                 const int64_t q = row0 + r;
-                const uint32_t v = acc[ri];  // = min(INF, .) since acc started at INF
-                const uint32_t keep = kColConst ? v + (uint32_t)a.z[q] * 0x10001u : v;
+                const uint32_t keep = kColConst ? v + (uint32_t)zs[r] * 0x10001u : v;
                 *reinterpret_cast<uint32_t *>(a.Bout + q * a.ldb + c0 + 2 * lane) = keep;
                 const int64_t c = c0 + 2 * lane;
                 if (a.user_out) {
@@ -212,25 +225,19 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
                     if (c < a.N) orow[c] = (int16_t)(v & 0xFFFFu);
                     if (c + 1 < a.N) orow[c + 1] = (int16_t)(v >> 16);
                 }
-                if (a.gdiag && q >= c0 && q < c0 + kChunk && lane == (int)((q - c0) >> 1))
-                    atomicMin(&dmin[item & 1], (int32_t)(((q - c0) & 1) ? (v >> 16) : (v & 0xFFFFu)));
+                if (c == q) dmin = min(dmin, (int32_t)(v & 0xFFFFu));
+                if (c + 1 == q) dmin = min(dmin, (int32_t)(v >> 16));
             }
         }
-        __syncthreads();
-        if (last) {
-            if (threadIdx.x == 0) {
-                const int32_t d = dmin[item & 1];
-                if (a.gdiag && d < (int32_t)kInf16) atomicMin(a.gdiag, d);
-                dmin[item & 1] = (int32_t)kInf16;
-            }
-            ++item;
-        }
-        ++unit;
-        if (!has_next) break;
-        w = wn;
-        g = gn;
-        s = sn;
-        s_end = sn_end;
+        __syncthreads();  // everyone is done with buffer b before it is refilled
+        cur = nxt;
+        nxt = nxt2;
+        nxt2 = nxt3;
+    }
+    if (a.gdiag) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dmin = min(dmin, __shfl_xor_sync(0xFFFFFFFFu, dmin, o));
+        if (lane == 0 && dmin < (int32_t)kInf16) atomicMin(a.gdiag, dmin);
     }
 }
 
@@ -316,7 +323,7 @@ __global__ void dense_csr_fill_kernel(const int16_t *__restrict__ A, int64_t N,
 // ---------------------------------------------------------------- host side
 
 int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_t> &z,
-                    int cap_rows, PlanHost *out) {
+                    int cap_rows, int blob_cap, int grid, PlanHost *out) {
     const int64_t N = csr.N;
     const int umax = cap_rows - 1;  // the last buffer row is the INF padding row
     if (umax < 1) return set_error(MP_EINVAL, "shared-memory buffer too small");
@@ -325,32 +332,44 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
     P.N = N;
     P.colconst = colconst;
     P.cap_rows = cap_rows;
+    P.blob_cap = blob_cap;
     P.z = z;
     if (P.z.size() != (size_t)N) P.z.assign((size_t)N, 0);
     P.ldb = ((N + kChunk - 1) / kChunk) * kChunk;
     P.nchunks = (int)(P.ldb / kChunk);
     P.nnz = csr.row_ptr[N];
 
+    const int per_entry = colconst ? 1 : 2;  // 32-bit words per entry
+    const int pad_to = colconst ? 8 : 4;     // entries per unrolled iteration
+    auto padded = [&](int64_t cnt) { return (cnt + pad_to - 1) / pad_to * pad_to; };
+    auto blob_words = [&](int64_t rows, int64_t entry_words) {
+        return (int64_t)kBlobHeader + ((2 * (rows + kWarps) + 7) & ~7) + ((rows + 15) / 16) * 8 +
+               entry_words;
+    };
+
     std::vector<int32_t> stamp((size_t)N, -1), local((size_t)N, -1);
     P.grp_row0.push_back(0);
     P.grp_stage0.push_back(0);
     P.stage_u0.push_back(0);
+    P.blob_off.push_back(0);
     int32_t gid = 0;
     int64_t q = 0;
-    const int per_entry = colconst ? 1 : 2;  // 32-bit words per entry
-    const int pad_to = colconst ? 8 : 4;     // entries per unrolled iteration
     while (q < N) {
-        // grow the group while the union of gathered rows fits one buffer
+        // grow the group while the union of gathered rows fits one buffer and
+        // the stage's entry blob fits the blob region
         const int64_t g0 = q;
-        int64_t ucount = 0;
+        int64_t ucount = 0, ewords = 0;
         while (q < N && q - g0 < kGroupMax) {
             int64_t add = 0;
             for (int64_t e = csr.row_ptr[q]; e < csr.row_ptr[q + 1]; ++e)
                 if (stamp[csr.col[e]] != gid) ++add;
-            if (q > g0 && ucount + add > umax) break;
-            for (int64_t e = csr.row_ptr[q]; e < csr.row_ptr[q + 1]; ++e)
-                if (stamp[csr.col[e]] != gid) stamp[csr.col[e]] = gid;
+            const int64_t ew = padded(csr.row_ptr[q + 1] - csr.row_ptr[q]) * per_entry;
+            if (q > g0 && (ucount + add > umax ||
+                           blob_words(q - g0 + 1, ewords + ew) > blob_cap))
+                break;
+            for (int64_t e = csr.row_ptr[q]; e < csr.row_ptr[q + 1]; ++e) stamp[csr.col[e]] = gid;
             ucount += add;
+            ewords += ew;
             ++q;
         }
         // the union, sorted, cut into stages of at most umax rows
@@ -363,16 +382,15 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
                     U.push_back(csr.col[e]);
                 }
         std::sort(U.begin(), U.end());
-        std::vector<int32_t> where((size_t)U.size());
         const int nst = U.empty() ? 1 : (int)((U.size() + umax - 1) / umax);
         for (int st = 0; st < nst; ++st) {
             const size_t ub = (size_t)st * umax, ue = std::min(U.size(), ub + (size_t)umax);
             for (size_t u = ub; u < ue; ++u) P.urows.push_back(U[u]);
             P.stage_u0.push_back((int32_t)P.urows.size());
-            P.stage_ebase.push_back((int32_t)P.stage_e.size());
+            // entries of every row of the group that gather from this stage
+            const int64_t rows = q - g0;
+            std::vector<std::vector<uint32_t>> rent((size_t)rows);
             for (int64_t r = g0; r < q; ++r) {
-                P.stage_e.push_back((int32_t)(P.ent.size() / per_entry));
-                // entries of row r whose gathered row falls in this stage, by U order
                 std::vector<std::pair<int32_t, uint32_t>> es;
                 for (int64_t e = csr.row_ptr[r]; e < csr.row_ptr[r + 1]; ++e) {
                     const int32_t p = csr.col[e];
@@ -381,23 +399,129 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
                     es.push_back({(int32_t)(u - ub), (uint32_t)(uint16_t)csr.val[e]});
                 }
                 std::sort(es.begin(), es.end());
-                while (es.size() % pad_to) es.push_back({umax, colconst ? 0u : 0u});
+                while (es.size() % pad_to) es.push_back({umax, 0u});  // padding row
                 for (auto &pr : es) {
-                    // the padding row sits at index cap_rows - 1 = umax
-                    P.ent.push_back((uint32_t)pr.first * kRowBytes);
-                    if (!colconst) P.ent.push_back(pr.second * 0x10001u);
+                    rent[r - g0].push_back((uint32_t)pr.first * kRowBytes);
+                    if (!colconst) rent[r - g0].push_back(pr.second * 0x10001u);
                 }
             }
-            P.stage_e.push_back((int32_t)(P.ent.size() / per_entry));
+            // tasks: rows, long rows cut into segments of about a warp's share
+            // (multiples of one unrolled iteration = 8 words), dealt longest first
+            int64_t words = 0;
+            for (auto &v : rent) words += (int64_t)v.size();
+            const int64_t share = std::max<int64_t>(8, (words / kWarps + 7) / 8 * 8);
+            struct Task { int r; int64_t e0, e1; };
+            std::vector<Task> tasks;
+            std::vector<int64_t> rbase((size_t)rows + 1, 0);
+            for (int64_t r = 0; r < rows; ++r) rbase[r + 1] = rbase[r] + (int64_t)rent[r].size();
+            for (int64_t r = 0; r < rows; ++r) {
+                const int64_t len = (int64_t)rent[r].size();
+                if (len == 0) continue;
+                const int64_t pieces = (len + share - 1) / share;
+                const int64_t step = ((len + pieces - 1) / pieces + 7) / 8 * 8;
+                for (int64_t e = 0; e < len; e += step)
+                    tasks.push_back({(int)r, rbase[r] + e, rbase[r] + std::min(len, e + step)});
+            }
+            std::stable_sort(tasks.begin(), tasks.end(), [](const Task &x, const Task &y) {
+                return (x.e1 - x.e0) > (y.e1 - y.e0);
+            });
+            std::vector<std::vector<Task>> per_warp(kWarps);
+            std::vector<int64_t> load(kWarps, 0);
+            for (auto &t : tasks) {
+                const int wsel = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                per_warp[wsel].push_back(t);
+                load[wsel] += t.e1 - t.e0;
+            }
+            const int ntasks = (int)tasks.size();
+            std::vector<uint32_t> blob((size_t)kBlobHeader + (size_t)((2 * ntasks + 7) & ~7), 0u);
+            blob[0] = (uint32_t)g0;
+            blob[1] = (uint32_t)rows;
+            blob[2] = (st == 0 ? 1u : 0u) | (st == nst - 1 ? 2u : 0u);
+            blob[3] = (uint32_t)ntasks;
+            int tcount = 0;
+            for (int wv = 0; wv < kWarps; ++wv) {
+                blob[8 + wv] = (uint32_t)tcount;
+                for (auto &t : per_warp[wv]) {
+                    blob[kBlobHeader + 2 * tcount] = (uint32_t)t.e0 | ((uint32_t)t.r << 16);
+                    blob[kBlobHeader + 2 * tcount + 1] = (uint32_t)t.e1;
+                    ++tcount;
+                }
+            }
+            blob[8 + kWarps] = (uint32_t)tcount;
+            // labels of the group's rows (16-bit), added when a row is written
+            std::vector<uint32_t> zw((size_t)((rows + 15) / 16) * 8, 0u);
+            for (int64_t r = 0; r < rows; ++r)
+                zw[(size_t)(r >> 1)] |= (uint32_t)P.z[(size_t)(g0 + r)] << (16 * (r & 1));
+            blob.insert(blob.end(), zw.begin(), zw.end());
+            for (auto &v : rent) blob.insert(blob.end(), v.begin(), v.end());
+            while (blob.size() % 8) blob.push_back(0u);  // 32-byte granules for the copy
+            if (words > 0xFFFF)
+                return set_error(MP_EINVAL, "stage entry list of %lld words too long",
+                                 (long long)words);
+            if ((int64_t)blob.size() > blob_cap)
+                return set_error(MP_EINVAL, "stage blob of %zu words exceeds the %d-word region",
+                                 blob.size(), blob_cap);
+            P.blob.insert(P.blob.end(), blob.begin(), blob.end());
+            P.blob_off.push_back((int64_t)P.blob.size());
         }
         P.grp_row0.push_back((int32_t)q);
         P.grp_stage0.push_back((int32_t)(P.stage_u0.size() - 1));
         ++gid;
     }
     P.ngroups = gid;
-    // entry indices are in units of entries; convert to 32-bit word offsets
-    if (!colconst)
-        for (auto &v : P.stage_e) v *= 2;
+
+    // Schedule: work items (group, chunk) dealt to the CTAs longest first,
+    // each CTA's items then ordered by chunk; a unit per stage of an item.
+    P.grid = std::max(1, grid);
+    std::vector<int64_t> gcost((size_t)gid, 0);
+    for (int gg = 0; gg < gid; ++gg)
+        for (int st = P.grp_stage0[gg]; st < P.grp_stage0[gg + 1]; ++st)
+            gcost[gg] += (P.blob_off[st + 1] - P.blob_off[st]) + 256;  // entries + fixed cost
+    struct Item { int64_t cost; int32_t g, chunk; };
+    std::vector<Item> items;
+    items.reserve((size_t)gid * P.nchunks);
+    for (int c = 0; c < P.nchunks; ++c)
+        for (int gg = 0; gg < gid; ++gg) items.push_back({gcost[gg], gg, c});
+    std::stable_sort(items.begin(), items.end(),
+                     [](const Item &x, const Item &y) { return x.cost > y.cost; });
+    std::vector<std::vector<Item>> per_cta((size_t)P.grid);
+    std::vector<int64_t> load((size_t)P.grid, 0);
+    {
+        // least-loaded CTA first (a binary heap of (load, cta))
+        std::vector<std::pair<int64_t, int>> heap;
+        for (int c = 0; c < P.grid; ++c) heap.push_back({0, c});
+        auto cmp = [](const std::pair<int64_t, int> &x, const std::pair<int64_t, int> &y) {
+            return x.first > y.first || (x.first == y.first && x.second > y.second);
+        };
+        std::make_heap(heap.begin(), heap.end(), cmp);
+        for (auto &it : items) {
+            std::pop_heap(heap.begin(), heap.end(), cmp);
+            auto &top = heap.back();
+            per_cta[(size_t)top.second].push_back(it);
+            top.first += it.cost;
+            std::push_heap(heap.begin(), heap.end(), cmp);
+        }
+    }
+    P.cta_unit0.assign((size_t)P.grid + 1, 0);
+    for (int c = 0; c < P.grid; ++c) {
+        auto &L = per_cta[(size_t)c];
+        std::sort(L.begin(), L.end(), [](const Item &x, const Item &y) {
+            return x.chunk != y.chunk ? x.chunk < y.chunk : x.g < y.g;
+        });
+        for (auto &it : L)
+            for (int st = P.grp_stage0[it.g]; st < P.grp_stage0[it.g + 1]; ++st) {
+                UnitDesc u;
+                u.chunk = it.chunk;
+                u.u0 = P.stage_u0[st];
+                u.u1 = P.stage_u0[st + 1];
+                u.bo = P.blob_off[st];
+                u.bw = (int32_t)(P.blob_off[st + 1] - P.blob_off[st]);
+                u.last = (st + 1 == P.grp_stage0[it.g + 1]) ? 1 : 0;
+                u.pad = 0;
+                P.units.push_back(u);
+            }
+        P.cta_unit0[(size_t)c + 1] = (int32_t)P.units.size();
+    }
     return MP_OK;
 }
 
@@ -407,6 +531,7 @@ int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent) 
     d->ngroups = h.ngroups;
     d->nchunks = h.nchunks;
     d->cap_rows = h.cap_rows;
+    d->blob_cap = h.blob_cap;
     d->colconst = h.colconst;
     d->nnz = h.nnz;
     auto up = [&](DevBuf &buf, const void *src, size_t bytes) -> int {
@@ -417,26 +542,32 @@ int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent) 
     MP_TRY(up(d->grp_row0, h.grp_row0.data(), h.grp_row0.size() * 4));
     MP_TRY(up(d->grp_stage0, h.grp_stage0.data(), h.grp_stage0.size() * 4));
     MP_TRY(up(d->stage_u0, h.stage_u0.data(), h.stage_u0.size() * 4));
-    MP_TRY(up(d->stage_ebase, h.stage_ebase.data(), h.stage_ebase.size() * 4));
-    MP_TRY(up(d->stage_e, h.stage_e.data(), h.stage_e.size() * 4));
+    MP_TRY(up(d->blob_off, h.blob_off.data(), h.blob_off.size() * 8));
+    MP_TRY(up(d->blob, h.blob.data(), h.blob.size() * 4));
     MP_TRY(up(d->urows, h.urows.data(), h.urows.size() * 4));
-    MP_TRY(up(d->ent, h.ent.data(), h.ent.size() * 4));
     MP_TRY(up(d->z, h.z.data(), h.z.size() * 2));
-    d->h2d_bytes = (h.grp_row0.size() + h.grp_stage0.size() + h.stage_u0.size() +
-                    h.stage_ebase.size() + h.stage_e.size() + h.urows.size() + h.ent.size()) * 4 +
-                   h.z.size() * 2;
+    MP_TRY(up(d->units, h.units.data(), h.units.size() * sizeof(UnitDesc)));
+    MP_TRY(up(d->cta_unit0, h.cta_unit0.data(), h.cta_unit0.size() * 4));
+    d->grid = h.grid;
+    d->h2d_bytes = (h.grp_row0.size() + h.grp_stage0.size() + h.stage_u0.size() + h.blob.size() +
+                    h.urows.size() + h.cta_unit0.size()) * 4 + h.blob_off.size() * 8 +
+                   h.z.size() * 2 + h.units.size() * sizeof(UnitDesc);
     return MP_OK;
 }
 
-int sparse_cap_rows(int *cap_rows, int *blocks_per_sm) {
+int sparse_cap_rows(int *cap_rows, int *blob_cap, int *grid) {
     DeviceInfo di;
     MP_TRY(device_info(&di));
-    // one CTA per SM, two buffers of cap_rows rows of 128 B
-    size_t budget = di.smem_optin - 1024 - kHeader;
+    // one CTA per SM; two buffers, each a 24 KiB blob region plus cap_rows
+    // gathered row segments of 128 B (at most kStageRowsMax + the padding
+    // row), and the 16 KiB of per-row accumulators
+    const int blob = 6144;
+    const size_t budget = di.smem_optin - 1024 - kAccBytes - 2 * (size_t)blob * 4;
     int cap = (int)(budget / (2 * (size_t)kRowBytes));
-    if (cap > 2048) cap = 2048;
+    if (cap > kStageRowsMax + 1) cap = kStageRowsMax + 1;
     *cap_rows = cap;
-    *blocks_per_sm = 1;
+    *blob_cap = blob;
+    *grid = di.sms;
     return MP_OK;
 }
 
@@ -448,17 +579,12 @@ int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *
     MP_TRY(device_status_ptr(&status));
     SpStepArgs a;
     memset(&a, 0, sizeof(a));
-    a.grp_row0 = p.grp_row0.as<int32_t>();
-    a.grp_stage0 = p.grp_stage0.as<int32_t>();
-    a.stage_u0 = p.stage_u0.as<int32_t>();
-    a.stage_ebase = p.stage_ebase.as<int32_t>();
-    a.stage_e = p.stage_e.as<int32_t>();
     a.urows = p.urows.as<int32_t>();
-    a.ent = p.ent.as<uint32_t>();
-    a.z = p.z.as<uint16_t>();
-    a.ngroups = p.ngroups;
-    a.nchunks = p.nchunks;
+    a.blob = p.blob.as<uint32_t>();
+    a.units = p.units.as<UnitDesc>();
+    a.cta_unit0 = p.cta_unit0.as<int32_t>();
     a.cap_rows = p.cap_rows;
+    a.blob_cap = p.blob_cap;
     a.N = p.N;
     a.ldb = p.ldb;
     a.Bin = Bin;
@@ -466,10 +592,9 @@ int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *
     a.user_out = user_out;
     a.gdiag = gdiag;
     a.status = status;
-    const size_t smem = kHeader + 2 * (size_t)p.cap_rows * kRowBytes;
-    const int64_t total = (int64_t)p.ngroups * p.nchunks;
-    int64_t grid = std::min<int64_t>(total, (int64_t)di.sms);
-    if (grid < 1) return MP_OK;
+    const size_t smem = 2 * ((size_t)p.blob_cap * 4 + (size_t)p.cap_rows * kRowBytes) + kAccBytes;
+    const int64_t grid = p.grid;
+    if (grid < 1 || p.N < 1) return MP_OK;
     static bool attr_set[2][64] = {};
     const int kind = p.colconst ? 0 : 1;
     if (di.device < 64 && !attr_set[kind][di.device]) {

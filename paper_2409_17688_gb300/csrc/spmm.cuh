@@ -18,28 +18,44 @@ struct DevCsr {
     DevBuf row_ptr, col, val;
 };
 
+// One unit of a CTA's schedule: stage s of work item (group, chunk).
+struct UnitDesc {
+    int32_t chunk;  // column chunk (64 columns)
+    int32_t u0, u1; // the stage's rows in urows
+    int32_t bw;     // blob words
+    int64_t bo;     // blob offset (words)
+    int32_t last;   // last stage of its item
+    int32_t pad;
+};
+
 // The gather plan of a sparse A, built once on the host (see spmm.cu).
 struct PlanHost {
     int64_t N = 0, ldb = 0, nnz = 0;
-    int ngroups = 0, nchunks = 0, cap_rows = 0;
+    int ngroups = 0, nchunks = 0, cap_rows = 0, blob_cap = 0;
     bool colconst = false;
-    std::vector<int32_t> grp_row0, grp_stage0, stage_u0, stage_ebase, stage_e, urows;
-    std::vector<uint32_t> ent;
+    std::vector<int32_t> grp_row0, grp_stage0, stage_u0, urows;
+    std::vector<int64_t> blob_off;
+    std::vector<uint32_t> blob;
     std::vector<uint16_t> z;
+    int grid = 0;                         // CTAs the schedule is made for
+    std::vector<UnitDesc> units;          // every CTA's units, back to back
+    std::vector<int32_t> cta_unit0;       // [grid + 1] offsets into units
 };
 struct PlanDev {
     int64_t N = 0, ldb = 0, nnz = 0;
-    int ngroups = 0, nchunks = 0, cap_rows = 0;
+    int ngroups = 0, nchunks = 0, cap_rows = 0, blob_cap = 0;
     bool colconst = false;
     size_t h2d_bytes = 0;
-    DevBuf grp_row0, grp_stage0, stage_u0, stage_ebase, stage_e, urows, ent, z;
+    int grid = 0;
+    DevBuf grp_row0, grp_stage0, stage_u0, blob_off, blob, urows, z, units, cta_unit0;
 };
 
 struct SpStepArgs {
-    const int32_t *grp_row0, *grp_stage0, *stage_u0, *stage_ebase, *stage_e, *urows;
-    const uint32_t *ent;
-    const uint16_t *z;
-    int ngroups, nchunks, cap_rows;
+    const int32_t *urows;
+    const uint32_t *blob;
+    const UnitDesc *units;
+    const int32_t *cta_unit0;
+    int cap_rows, blob_cap;
     int64_t N, ldb;
     const uint16_t *Bin;
     uint16_t *Bout;
@@ -49,9 +65,9 @@ struct SpStepArgs {
 };
 
 int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_t> &z,
-                    int cap_rows, PlanHost *out);
+                    int cap_rows, int blob_cap, int grid, PlanHost *out);
 int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent);
-int sparse_cap_rows(int *cap_rows, int *blocks_per_sm);
+int sparse_cap_rows(int *cap_rows, int *blob_cap, int *grid);
 int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,
                 int32_t *gdiag, cudaStream_t s);
 int sparse_init_from_dense(const PlanDev &p, const int16_t *A, uint16_t *B0, int16_t *user0,
