@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dense", action="store_true", help="skip the N=8192 dense products")
     ap.add_argument("--profile", choices=["chain9", "chain8", "gemm8192", "gemm8192u8"],
                     help="run one small case for an ncu capture and exit")
     return ap.parse_args()
@@ -251,6 +252,9 @@ def run_ours(args):
            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * K_MAX * len(PATH_ORDERS),
            "api": "mp_gamma2_table (synchronous, host int64 output)"}
 
+    # ---- configs[1]-style dense products (K1), reported beside the chain
+    dense = dense_extras(mp, torch, flush, stream, peak_viaddmin) if not args.no_dense else None
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -278,12 +282,85 @@ def run_ours(args):
         "per_n": per_n, "setup_ms": {n: round(v, 2) for n, v in setup.items()},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
+    if dense is not None:
+        line["dense_gemm"] = dense
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def block_active_ops(X, Y, inf, block=128):
+    """Algorithmic terms of X (x) Y: M*N*K over the (I, K, J) 128-blocks whose
+    X and Y blocks both hold a finite entry (the others cannot lower a minimum)."""
+    import numpy as np
+    M, K = X.shape
+    N = Y.shape[1]
+    def occ(A):
+        r, c = A.shape
+        br, bc = -(-r // block), -(-c // block)
+        P = np.full((br * block, bc * block), inf, dtype=A.dtype)
+        P[:r, :c] = A
+        return (P.reshape(br, block, bc, block) != inf).any(axis=(1, 3))
+    ox, oy = occ(X), occ(Y)
+    rs = np.minimum(block, M - np.arange(ox.shape[0]) * block)
+    ks = np.minimum(block, K - np.arange(ox.shape[1]) * block)
+    cs = np.minimum(block, N - np.arange(oy.shape[1]) * block)
+    # sum over I, K, J of rows(I) * k(K) * cols(J) * ox[I,K] * oy[K,J]
+    a = (ox * rs[:, None]).astype(np.float64) * ks[None, :]
+    b = (oy * cs[None, :]).astype(np.float64)
+    return int(round(float((a @ b).sum())))
+
+
+def dense_extras(mp, torch, flush, stream, peak_viaddmin):
+    """N = 8192 products with 40% INF 128-blocks (int16 and uint8), one
+    product each, and the 16-step chain P_k = P_{k-1} (x) X (int16)."""
+    import numpy as np
+    from paper_2409_17688_gb300 import synth
+    N = 8192
+    out = {}
+
+    def timed(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            flush.fill_(7)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    for name, dt, inf in (("int16", np.int16, 0x7FFF), ("uint8", np.uint8, 0xFF)):
+        X = synth.block_inf_matrix(N, N, 1, dt, inf_frac=0.4)
+        Y = synth.block_inf_matrix(N, N, 2, dt, inf_frac=0.4)
+        alg = block_active_ops(X, Y, inf)
+        Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+        Zd = torch.empty_like(Xd)
+        mp.mp_minplus_mul(Xd, Yd, Zd)
+        ms = timed(lambda: mp.mp_minplus_mul(Xd, Yd, Zd))
+        out[name] = {"ms": round(ms, 3), "alg_ops": alg, "dense_ops": N ** 3,
+                     "alg_gops": round(alg / (ms * 1e-3) / 1e9, 1),
+                     "dense_equiv_gops": round(N ** 3 / (ms * 1e-3) / 1e9, 1),
+                     "pct_dpx_peak": round(100.0 * alg / (ms * 1e-3) / peak_viaddmin, 2)}
+        if name == "int16":
+            P = [torch.empty_like(Xd), torch.empty_like(Xd)]
+            def chain():
+                prev = Xd
+                for k in range(16):
+                    mp.mp_minplus_mul(prev, Xd, P[k & 1])
+                    prev = P[k & 1]
+            chain()
+            ms_c = timed(chain, reps=2)
+            out["int16_chain16"] = {"ms": round(ms_c, 3),
+                                    "dense_equiv_gops": round(16 * N ** 3 / (ms_c * 1e-3) / 1e9, 1)}
+        del Xd, Yd, Zd
+    out["workload"] = ("X (seed 1), Y (seed 2): N=8192, entries U[0,31], 128x128 blocks INF "
+                       "with prob 0.4; chain P_k = P_(k-1) (x) X, 16 products")
+    return out
 
 
 def cpu_baseline_sample(target_s: float = 12.0):

@@ -35,6 +35,7 @@
 // registers and folded into g[k] with one atomicMin per warp.
 #include <algorithm>
 #include <cstring>
+#include <iterator>
 
 #include "mp_internal.cuh"
 #include "spmm.cuh"
@@ -118,6 +119,33 @@ __device__ __forceinline__ UnitDesc load_unit(const SpStepArgs &a, int k, int k_
     return u;
 }
 
+// Minima of one segment of gathered rows into the accumulators of the
+// cluster rows named by MASK (bit j = row j of the cluster): every gathered
+// value is read once from shared memory and folded into each of those rows,
+// two values per __vimin3_u16x2.
+template <int MASK>
+__device__ __forceinline__ void gather_min(const uint32_t *ents, const uint8_t *sb, int e0, int e1,
+                                           uint32_t (&m)[3]) {
+#pragma unroll 2
+    for (int e = e0; e < e1; e += 8) {
+        const uint4 p = *reinterpret_cast<const uint4 *>(ents + e);
+        const uint4 q = *reinterpret_cast<const uint4 *>(ents + e + 4);
+        const uint32_t v0 = lds32(sb + p.x), v1 = lds32(sb + p.y);
+        const uint32_t v2 = lds32(sb + p.z), v3 = lds32(sb + p.w);
+        const uint32_t v4 = lds32(sb + q.x), v5 = lds32(sb + q.y);
+        const uint32_t v6 = lds32(sb + q.z), v7 = lds32(sb + q.w);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (MASK & (1 << j)) {
+                m[j] = __vimin3_u16x2(m[j], v0, v1);
+                m[j] = __vimin3_u16x2(m[j], v2, v3);
+                m[j] = __vimin3_u16x2(m[j], v4, v5);
+                m[j] = __vimin3_u16x2(m[j], v6, v7);
+            }
+        }
+    }
+}
+
 template <bool kColConst>
 __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -164,49 +192,55 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
         const uint8_t *buf = smem + b * buf_bytes;
         const uint32_t *blob = reinterpret_cast<const uint32_t *>(buf);
         const int row0 = (int)blob[0], nrows = (int)blob[1];
-        const int ntasks = (int)blob[3];
+        const int ntasks = (int)blob[3], nsegs = (int)blob[4];
         const uint32_t *tasks = blob + kBlobHeader;
-        const uint16_t *zs = reinterpret_cast<const uint16_t *>(tasks + ((2 * ntasks + 7) & ~7));
+        const uint32_t *segs = tasks + ((2 * ntasks + 7) & ~7);
+        const uint16_t *zs = reinterpret_cast<const uint16_t *>(segs + ((2 * nsegs + 7) & ~7));
         const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8;
         const uint8_t *sb = buf + blob_bytes + lane * 4;
         const int64_t c0 = (int64_t)cur.chunk * kChunk;
         const int t_end = (int)blob[8 + warp + 1];
         for (int t = (int)blob[8 + warp]; t < t_end; ++t) {
-            const uint32_t t0 = tasks[2 * t];
-            const int r = (int)(t0 >> 16), e0 = (int)(t0 & 0xFFFFu), e1 = (int)tasks[2 * t + 1];
-            uint32_t m;
-            if (kColConst) {
-                uint32_t m0 = 0xFFFFFFFFu, m1 = 0xFFFFFFFFu;
+            const uint32_t t0 = tasks[2 * t], t1 = tasks[2 * t + 1];
+            const int nr = (int)(t0 >> 24);
+            uint32_t m[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+            for (int sg = (int)(t1 & 0xFFFFu); sg < (int)(t1 >> 16); ++sg) {
+                const uint32_t s0 = segs[2 * sg];
+                const int e0 = (int)(s0 & 0xFFFFu), mask = (int)(s0 >> 16), e1 = (int)segs[2 * sg + 1];
+                if (kColConst) {
+                    switch (mask) {
+                        case 1: gather_min<1>(ents, sb, e0, e1, m); break;
+                        case 2: gather_min<2>(ents, sb, e0, e1, m); break;
+                        case 3: gather_min<3>(ents, sb, e0, e1, m); break;
+                        case 4: gather_min<4>(ents, sb, e0, e1, m); break;
+                        case 5: gather_min<5>(ents, sb, e0, e1, m); break;
+                        case 6: gather_min<6>(ents, sb, e0, e1, m); break;
+                        default: gather_min<7>(ents, sb, e0, e1, m); break;
+                    }
+                } else {
+                    // two entries (offset, label pair) per 16-byte read, four per iteration
+                    uint32_t mm = m[0];
 #pragma unroll 2
-                for (int e = e0; e < e1; e += 8) {
-                    const uint4 p = *reinterpret_cast<const uint4 *>(ents + e);
-                    const uint4 q = *reinterpret_cast<const uint4 *>(ents + e + 4);
-                    const uint32_t v0 = lds32(sb + p.x), v1 = lds32(sb + p.y);
-                    const uint32_t v2 = lds32(sb + p.z), v3 = lds32(sb + p.w);
-                    const uint32_t v4 = lds32(sb + q.x), v5 = lds32(sb + q.y);
-                    const uint32_t v6 = lds32(sb + q.z), v7 = lds32(sb + q.w);
-                    m0 = __vimin3_u16x2(m0, v0, v1);
-                    m1 = __vimin3_u16x2(m1, v2, v3);
-                    m0 = __vimin3_u16x2(m0, v4, v5);
-                    m1 = __vimin3_u16x2(m1, v6, v7);
-                }
-                m = __vminu2(m0, m1);
-            } else {
-                m = 0xFFFFFFFFu;
-                // two entries (offset, label pair) per 16-byte read, four per iteration
-#pragma unroll 2
-                for (int e = e0; e < e1; e += 8) {
-                    const uint4 p = *reinterpret_cast<const uint4 *>(ents + e);
-                    const uint4 q = *reinterpret_cast<const uint4 *>(ents + e + 4);
-                    m = __viaddmin_u16x2(lds32(sb + p.x), p.y, m);
-                    m = __viaddmin_u16x2(lds32(sb + p.z), p.w, m);
-                    m = __viaddmin_u16x2(lds32(sb + q.x), q.y, m);
-                    m = __viaddmin_u16x2(lds32(sb + q.z), q.w, m);
+                    for (int e = e0; e < e1; e += 8) {
+                        const uint4 p = *reinterpret_cast<const uint4 *>(ents + e);
+                        const uint4 q = *reinterpret_cast<const uint4 *>(ents + e + 4);
+                        mm = __viaddmin_u16x2(lds32(sb + p.x), p.y, mm);
+                        mm = __viaddmin_u16x2(lds32(sb + p.z), p.w, mm);
+                        mm = __viaddmin_u16x2(lds32(sb + q.x), q.y, mm);
+                        mm = __viaddmin_u16x2(lds32(sb + q.z), q.w, mm);
+                    }
+                    m[0] = mm;
                 }
             }
-            uint32_t *acc = accs + r * kChunk + 2 * lane;
-            atomicMin(acc, m & 0xFFFFu);
-            atomicMin(acc + 1, m >> 16);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (j < nr) {
+                    const int r = (int)((t0 >> (8 * j)) & 0xFFu);
+                    uint32_t *acc = accs + r * kChunk + 2 * lane;
+                    atomicMin(acc, m[j] & 0xFFFFu);
+                    atomicMin(acc + 1, m[j] >> 16);
+                }
+            }
         }
         if (cur.last) {
             __syncthreads();
@@ -343,8 +377,8 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
     const int pad_to = colconst ? 8 : 4;     // entries per unrolled iteration
     auto padded = [&](int64_t cnt) { return (cnt + pad_to - 1) / pad_to * pad_to; };
     auto blob_words = [&](int64_t rows, int64_t entry_words) {
-        return (int64_t)kBlobHeader + ((2 * (rows + kWarps) + 7) & ~7) + ((rows + 15) / 16) * 8 +
-               entry_words;
+        return (int64_t)kBlobHeader + ((2 * (rows + kWarps) + 7) & ~7) +
+               ((2 * (7 * rows + 2 * kWarps) + 7) & ~7) + ((rows + 15) / 16) * 8 + entry_words;
     };
 
     std::vector<int32_t> stamp((size_t)N, -1), local((size_t)N, -1);
@@ -352,7 +386,7 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
     P.grp_stage0.push_back(0);
     P.stage_u0.push_back(0);
     P.blob_off.push_back(0);
-    int32_t gid = 0;
+    int32_t gid = 0, attempt = 0;
     int64_t q = 0;
     while (q < N) {
         // grow the group while the union of gathered rows fits one buffer and
@@ -372,98 +406,221 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
             ewords += ew;
             ++q;
         }
-        // the union, sorted, cut into stages of at most umax rows
-        std::vector<int32_t> U;
-        U.reserve((size_t)ucount);
-        for (int64_t r = g0; r < q; ++r)
-            for (int64_t e = csr.row_ptr[r]; e < csr.row_ptr[r + 1]; ++e)
-                if (local[csr.col[e]] != gid) {
-                    local[csr.col[e]] = gid;
-                    U.push_back(csr.col[e]);
+        // Build the group's stages; if a stage's blob overflows its region
+        // (mask padding of the clusters can exceed the row-wise estimate),
+        // retry with fewer rows.
+        int64_t qend = q;
+        while (true) {
+            const size_t snap_urows = P.urows.size(), snap_su = P.stage_u0.size();
+            const size_t snap_blob = P.blob.size(), snap_bo = P.blob_off.size();
+            bool overflow = false;
+            ++attempt;
+            // the union, sorted, cut into stages of at most umax rows
+            std::vector<int32_t> U;
+            U.reserve((size_t)ucount);
+            for (int64_t r = g0; r < qend; ++r)
+                for (int64_t e = csr.row_ptr[r]; e < csr.row_ptr[r + 1]; ++e)
+                    if (local[csr.col[e]] != attempt) {
+                        local[csr.col[e]] = attempt;
+                        U.push_back(csr.col[e]);
+                    }
+            std::sort(U.begin(), U.end());
+            const int nst = U.empty() ? 1 : (int)((U.size() + umax - 1) / umax);
+            for (int st = 0; st < nst; ++st) {
+                const size_t ub = (size_t)st * umax, ue = std::min(U.size(), ub + (size_t)umax);
+                for (size_t u = ub; u < ue; ++u) P.urows.push_back(U[u]);
+                P.stage_u0.push_back((int32_t)P.urows.size());
+                const int64_t rows = qend - g0;
+                // gathered-row indices (local to the stage) of every row of the group
+                std::vector<std::vector<int32_t>> rloc((size_t)rows);
+                std::vector<std::vector<uint32_t>> rval((size_t)rows);
+                for (int64_t r = g0; r < qend; ++r) {
+                    std::vector<std::pair<int32_t, uint32_t>> es;
+                    for (int64_t e = csr.row_ptr[r]; e < csr.row_ptr[r + 1]; ++e) {
+                        const int32_t p = csr.col[e];
+                        const size_t u = (size_t)(std::lower_bound(U.begin(), U.end(), p) - U.begin());
+                        if (u < ub || u >= ue) continue;
+                        es.push_back({(int32_t)(u - ub), (uint32_t)(uint16_t)csr.val[e]});
+                    }
+                    std::sort(es.begin(), es.end());
+                    for (auto &pr : es) {
+                        rloc[r - g0].push_back(pr.first);
+                        rval[r - g0].push_back(pr.second);
+                    }
                 }
-        std::sort(U.begin(), U.end());
-        const int nst = U.empty() ? 1 : (int)((U.size() + umax - 1) / umax);
-        for (int st = 0; st < nst; ++st) {
-            const size_t ub = (size_t)st * umax, ue = std::min(U.size(), ub + (size_t)umax);
-            for (size_t u = ub; u < ue; ++u) P.urows.push_back(U[u]);
-            P.stage_u0.push_back((int32_t)P.urows.size());
-            // entries of every row of the group that gather from this stage
-            const int64_t rows = q - g0;
-            std::vector<std::vector<uint32_t>> rent((size_t)rows);
-            for (int64_t r = g0; r < q; ++r) {
-                std::vector<std::pair<int32_t, uint32_t>> es;
-                for (int64_t e = csr.row_ptr[r]; e < csr.row_ptr[r + 1]; ++e) {
-                    const int32_t p = csr.col[e];
-                    const size_t u = (size_t)(std::lower_bound(U.begin(), U.end(), p) - U.begin());
-                    if (u < ub || u >= ue) continue;
-                    es.push_back({(int32_t)(u - ub), (uint32_t)(uint16_t)csr.val[e]});
+                // clusters: with one label per gathered row (column-constant A)
+                // rows whose gather lists overlap share the reads; greedy clusters
+                // of up to 3 rows, each next row the one overlapping most
+                std::vector<std::vector<int>> clusters;
+                {
+                    std::vector<int> rem;
+                    for (int r = 0; r < (int)rows; ++r)
+                        if (!rloc[r].empty()) rem.push_back(r);
+                    auto overlap = [&](const std::vector<int32_t> &x, const std::vector<int32_t> &y) {
+                        size_t i = 0, j = 0, c = 0;
+                        while (i < x.size() && j < y.size()) {
+                            if (x[i] < y[j]) ++i;
+                            else if (y[j] < x[i]) ++j;
+                            else { ++c; ++i; ++j; }
+                        }
+                        return c;
+                    };
+                    const int kmax = colconst ? 3 : 1;
+                    while (!rem.empty()) {
+                        std::vector<int> cl{rem.front()};
+                        rem.erase(rem.begin());
+                        std::vector<int32_t> inter = rloc[cl[0]];
+                        while ((int)cl.size() < kmax && !rem.empty()) {
+                            size_t best = 0, bi = 0;
+                            for (size_t k = 0; k < rem.size(); ++k) {
+                                const size_t ov = overlap(inter, rloc[rem[k]]);
+                                if (ov > best) { best = ov; bi = k; }
+                            }
+                            if (best == 0) break;
+                            const int nxt = rem[bi];
+                            rem.erase(rem.begin() + (long)bi);
+                            std::vector<int32_t> ni;
+                            std::set_intersection(inter.begin(), inter.end(), rloc[nxt].begin(),
+                                                  rloc[nxt].end(), std::back_inserter(ni));
+                            inter.swap(ni);
+                            cl.push_back(nxt);
+                        }
+                        clusters.push_back(cl);
+                    }
                 }
-                std::sort(es.begin(), es.end());
-                while (es.size() % pad_to) es.push_back({umax, 0u});  // padding row
-                for (auto &pr : es) {
-                    rent[r - g0].push_back((uint32_t)pr.first * kRowBytes);
-                    if (!colconst) rent[r - g0].push_back(pr.second * 0x10001u);
+                // per cluster: its union split by membership mask into segments of
+                // entries (padded to whole unrolled iterations)
+                struct Seg { int mask; std::vector<uint32_t> words; };
+                struct Cl { std::vector<int> rows; std::vector<Seg> segs; int64_t words = 0; };
+                std::vector<Cl> cls;
+                for (auto &cl : clusters) {
+                    Cl c;
+                    c.rows = cl;
+                    std::vector<std::pair<int32_t, std::pair<int, uint32_t>>> all;  // (u, (row j, label))
+                    for (int j = 0; j < (int)cl.size(); ++j)
+                        for (size_t t = 0; t < rloc[cl[j]].size(); ++t)
+                            all.push_back({rloc[cl[j]][t], {j, rval[cl[j]][t]}});
+                    std::sort(all.begin(), all.end());
+                    std::vector<std::vector<std::pair<int32_t, uint32_t>>> bym(8);
+                    for (size_t i = 0; i < all.size();) {
+                        size_t k = i;
+                        int mask = 0;
+                        while (k < all.size() && all[k].first == all[i].first) mask |= 1 << all[k++].second.first;
+                        bym[mask].push_back({all[i].first, all[i].second.second});
+                        i = k;
+                    }
+                    for (int mask = 1; mask < 8; ++mask) {
+                        auto &v = bym[mask];
+                        if (v.empty()) continue;
+                        while (v.size() % pad_to) v.push_back({umax, 0u});  // padding row
+                        Seg sg;
+                        sg.mask = mask;
+                        for (auto &pr : v) {
+                            sg.words.push_back((uint32_t)pr.first * kRowBytes);
+                            if (!colconst) sg.words.push_back(pr.second * 0x10001u);
+                        }
+                        c.words += (int64_t)sg.words.size();
+                        c.segs.push_back(std::move(sg));
+                    }
+                    cls.push_back(std::move(c));
                 }
-            }
-            // tasks: rows, long rows cut into segments of about a warp's share
-            // (multiples of one unrolled iteration = 8 words), dealt longest first
-            int64_t words = 0;
-            for (auto &v : rent) words += (int64_t)v.size();
-            const int64_t share = std::max<int64_t>(8, (words / kWarps + 7) / 8 * 8);
-            struct Task { int r; int64_t e0, e1; };
-            std::vector<Task> tasks;
-            std::vector<int64_t> rbase((size_t)rows + 1, 0);
-            for (int64_t r = 0; r < rows; ++r) rbase[r + 1] = rbase[r] + (int64_t)rent[r].size();
-            for (int64_t r = 0; r < rows; ++r) {
-                const int64_t len = (int64_t)rent[r].size();
-                if (len == 0) continue;
-                const int64_t pieces = (len + share - 1) / share;
-                const int64_t step = ((len + pieces - 1) / pieces + 7) / 8 * 8;
-                for (int64_t e = 0; e < len; e += step)
-                    tasks.push_back({(int)r, rbase[r] + e, rbase[r] + std::min(len, e + step)});
-            }
-            std::stable_sort(tasks.begin(), tasks.end(), [](const Task &x, const Task &y) {
-                return (x.e1 - x.e0) > (y.e1 - y.e0);
-            });
-            std::vector<std::vector<Task>> per_warp(kWarps);
-            std::vector<int64_t> load(kWarps, 0);
-            for (auto &t : tasks) {
-                const int wsel = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-                per_warp[wsel].push_back(t);
-                load[wsel] += t.e1 - t.e0;
-            }
-            const int ntasks = (int)tasks.size();
-            std::vector<uint32_t> blob((size_t)kBlobHeader + (size_t)((2 * ntasks + 7) & ~7), 0u);
-            blob[0] = (uint32_t)g0;
-            blob[1] = (uint32_t)rows;
-            blob[2] = (st == 0 ? 1u : 0u) | (st == nst - 1 ? 2u : 0u);
-            blob[3] = (uint32_t)ntasks;
-            int tcount = 0;
-            for (int wv = 0; wv < kWarps; ++wv) {
-                blob[8 + wv] = (uint32_t)tcount;
-                for (auto &t : per_warp[wv]) {
-                    blob[kBlobHeader + 2 * tcount] = (uint32_t)t.e0 | ((uint32_t)t.r << 16);
-                    blob[kBlobHeader + 2 * tcount + 1] = (uint32_t)t.e1;
-                    ++tcount;
+                // entries laid out cluster by cluster; tasks = clusters, long ones cut
+                // into pieces of about a warp's share, dealt to warps longest first
+                int64_t words = 0;
+                for (auto &c : cls) words += c.words;
+                const int64_t share = std::max<int64_t>(8, (words / kWarps + 7) / 8 * 8);
+                struct SegRef { int mask; int64_t e0, e1; };
+                struct Task { int ci; std::vector<SegRef> segs; int64_t len; };
+                std::vector<Task> tasks;
+                std::vector<uint32_t> ents;
+                for (int ci = 0; ci < (int)cls.size(); ++ci) {
+                    Task cur{ci, {}, 0};
+                    for (auto &sg : cls[ci].segs) {
+                        int64_t e = (int64_t)ents.size();
+                        ents.insert(ents.end(), sg.words.begin(), sg.words.end());
+                        const int64_t end = (int64_t)ents.size();
+                        while (e < end) {
+                            const int64_t take = std::min<int64_t>(end - e, std::max<int64_t>(8, share - cur.len));
+                            const int64_t take8 = (take + 7) / 8 * 8;
+                            cur.segs.push_back({sg.mask, e, std::min(end, e + take8)});
+                            cur.len += std::min(end, e + take8) - e;
+                            e += take8;
+                            if (cur.len >= share) {
+                                tasks.push_back(cur);
+                                cur = Task{ci, {}, 0};
+                            }
+                        }
+                    }
+                    if (!cur.segs.empty()) tasks.push_back(cur);
                 }
+                std::stable_sort(tasks.begin(), tasks.end(),
+                                 [](const Task &x, const Task &y) { return x.len > y.len; });
+                std::vector<std::vector<int>> per_warp(kWarps);
+                std::vector<int64_t> load(kWarps, 0);
+                for (int ti = 0; ti < (int)tasks.size(); ++ti) {
+                    const int wsel = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                    per_warp[wsel].push_back(ti);
+                    load[wsel] += tasks[ti].len;
+                }
+                int nsegs = 0;
+                for (auto &t : tasks) nsegs += (int)t.segs.size();
+                const int ntasks = (int)tasks.size();
+                std::vector<uint32_t> blob((size_t)kBlobHeader, 0u);
+                blob[0] = (uint32_t)g0;
+                blob[1] = (uint32_t)rows;
+                blob[2] = (st == 0 ? 1u : 0u) | (st == nst - 1 ? 2u : 0u);
+                blob[3] = (uint32_t)ntasks;
+                blob[4] = (uint32_t)nsegs;
+                std::vector<uint32_t> ttab((size_t)((2 * ntasks + 7) & ~7), 0u);
+                std::vector<uint32_t> stab((size_t)((2 * nsegs + 7) & ~7), 0u);
+                int tcount = 0, scount = 0;
+                for (int wv = 0; wv < kWarps; ++wv) {
+                    blob[8 + wv] = (uint32_t)tcount;
+                    for (int ti : per_warp[wv]) {
+                        const Task &t = tasks[ti];
+                        const auto &cr = cls[t.ci].rows;
+                        uint32_t w0 = (uint32_t)cr.size() << 24;
+                        for (int j = 0; j < (int)cr.size(); ++j) w0 |= (uint32_t)cr[j] << (8 * j);
+                        ttab[2 * tcount] = w0;
+                        ttab[2 * tcount + 1] = (uint32_t)scount | ((uint32_t)(scount + t.segs.size()) << 16);
+                        for (auto &sr : t.segs) {
+                            stab[2 * scount] = (uint32_t)sr.e0 | ((uint32_t)sr.mask << 16);
+                            stab[2 * scount + 1] = (uint32_t)sr.e1;
+                            ++scount;
+                        }
+                        ++tcount;
+                    }
+                }
+                blob[8 + kWarps] = (uint32_t)tcount;
+                blob.insert(blob.end(), ttab.begin(), ttab.end());
+                blob.insert(blob.end(), stab.begin(), stab.end());
+                // labels of the group's rows (16-bit), added when a row is written
+                std::vector<uint32_t> zw((size_t)((rows + 15) / 16) * 8, 0u);
+                for (int64_t r = 0; r < rows; ++r)
+                    zw[(size_t)(r >> 1)] |= (uint32_t)P.z[(size_t)(g0 + r)] << (16 * (r & 1));
+                blob.insert(blob.end(), zw.begin(), zw.end());
+                blob.insert(blob.end(), ents.begin(), ents.end());
+                while (blob.size() % 8) blob.push_back(0u);  // 32-byte granules for the copy
+                if ((int64_t)ents.size() > 0xFFFF || nsegs > 0xFFFF)
+                    return set_error(MP_EINVAL, "stage entry list of %zu words too long", ents.size());
+                if ((int64_t)blob.size() > blob_cap) {
+                    overflow = true;
+                    break;
+                }
+                P.blob.insert(P.blob.end(), blob.begin(), blob.end());
+                P.blob_off.push_back((int64_t)P.blob.size());
             }
-            blob[8 + kWarps] = (uint32_t)tcount;
-            // labels of the group's rows (16-bit), added when a row is written
-            std::vector<uint32_t> zw((size_t)((rows + 15) / 16) * 8, 0u);
-            for (int64_t r = 0; r < rows; ++r)
-                zw[(size_t)(r >> 1)] |= (uint32_t)P.z[(size_t)(g0 + r)] << (16 * (r & 1));
-            blob.insert(blob.end(), zw.begin(), zw.end());
-            for (auto &v : rent) blob.insert(blob.end(), v.begin(), v.end());
-            while (blob.size() % 8) blob.push_back(0u);  // 32-byte granules for the copy
-            if (words > 0xFFFF)
-                return set_error(MP_EINVAL, "stage entry list of %lld words too long",
-                                 (long long)words);
-            if ((int64_t)blob.size() > blob_cap)
-                return set_error(MP_EINVAL, "stage blob of %zu words exceeds the %d-word region",
-                                 blob.size(), blob_cap);
-            P.blob.insert(P.blob.end(), blob.begin(), blob.end());
-            P.blob_off.push_back((int64_t)P.blob.size());
+            if (!overflow) break;
+            if (qend - g0 == 1)
+                return set_error(MP_EINVAL, "a single row's stage blob exceeds the %d-word region",
+                                 blob_cap);
+            P.urows.resize(snap_urows);
+            P.stage_u0.resize(snap_su);
+            P.blob.resize(snap_blob);
+            P.blob_off.resize(snap_bo);
+            qend = g0 + std::max<int64_t>(1, (qend - g0) * 3 / 4);
         }
+        q = qend;
         P.grp_row0.push_back((int32_t)q);
         P.grp_stage0.push_back((int32_t)(P.stage_u0.size() - 1));
         ++gid;
