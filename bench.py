@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense", action="store_true", help="skip the N=8192 dense products")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 96-product batch")
     ap.add_argument("--profile", choices=["chain9", "chain8", "gemm8192", "gemm8192u8"],
                     help="run one small case for an ncu capture and exit")
     return ap.parse_args()
@@ -120,6 +121,22 @@ class ClockSampler:
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def profiled_traffic(summary: str, source: str):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel's source changed since the counters were taken."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, summary)).read()
+        sha = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    fields = dict(l.split(": ", 1) for l in text.splitlines()
+                  if l.startswith(("source_sha256: ", "traffic_bytes_per_launch: ")))
+    if fields.get("source_sha256", "").strip() != sha:
+        return None
+    return int(fields["traffic_bytes_per_launch"])
 
 
 def run_ours(args):
@@ -235,7 +252,11 @@ def run_ours(args):
     achieved = Ns[9] * nnz[9] / (step_ms * 1e-3)  # terms / s
     roofline = {"bound": "alu", "kernel": "sparse_step_kernel<colconst> (n=9, N=3447)",
                 "achieved": round(achieved / 1e9, 1), "peak": round(peak_vimin3 / 1e9, 1),
-                "unit": "Gop/s", "frac": round(achieved / peak_vimin3, 4), "traffic": None,
+                "unit": "Gop/s", "frac": round(achieved / peak_vimin3, 4),
+                "traffic": profiled_traffic("profiles/k2_transfer_step_n9.md",
+                                            "paper_2409_17688_gb300/csrc/spmm.cu"),
+                "traffic_unit": "bytes per launch (ncu dram read+write, cold cache)",
+                "algorithmic_bytes": 4 * Ns[9] * Ns[9],
                 "peak_source": "K6 __vimin3_u16x2 rate measured in this run (4 terms/instr)",
                 "launch_us": round(step_ms * 1e3, 2)}
 
@@ -254,6 +275,7 @@ def run_ours(args):
 
     # ---- configs[1]-style dense products (K1), reported beside the chain
     dense = dense_extras(mp, torch, flush, stream, peak_viaddmin) if not args.no_dense else None
+    batched = batched_extras(mp, torch, flush) if not args.no_batched else None
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
     cpu = None
@@ -284,6 +306,8 @@ def run_ours(args):
     }
     if dense is not None:
         line["dense_gemm"] = dense
+    if batched is not None:
+        line["batched"] = batched
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -360,6 +384,59 @@ def dense_extras(mp, torch, flush, stream, peak_viaddmin):
         del Xd, Yd, Zd
     out["workload"] = ("X (seed 1), Y (seed 2): N=8192, entries U[0,31], 128x128 blocks INF "
                        "with prob 0.4; chain P_k = P_(k-1) (x) X, 16 products")
+    return out
+
+
+def batched_extras(mp, torch, flush):
+    """96 square products, N log-uniform in [64, 8192] (seed 7), int16 entries
+    U[0,31] with 30% INF 128-blocks, each product seeded on its own.  The
+    tile shapes come from the autotuner run here; each mode is captured in a
+    CUDA graph once and replayed: mode 0 one persistent launch, mode 1 one
+    launch per product."""
+    import numpy as np
+    from paper_2409_17688_gb300 import synth
+    sizes = synth.batch_sizes(96, 64, 8192, seed=7)
+    probs, alg, dense = [], 0, 0
+    for i, N in enumerate(sizes):
+        X = synth.block_inf_matrix(N, N, 1000 + 2 * i, np.int16, inf_frac=0.3)
+        Y = synth.block_inf_matrix(N, N, 1001 + 2 * i, np.int16, inf_frac=0.3)
+        alg += block_active_ops(X, Y, 0x7FFF)
+        dense += N ** 3
+        Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+        probs.append((Xd, Yd, torch.empty_like(Xd)))
+    table = mp.mp_autotune()
+    batch = mp.Batch(probs)
+    s = torch.cuda.Stream()
+    out = {"count": len(sizes), "n_min": min(sizes), "n_max": max(sizes),
+           "dense_ops": dense, "alg_ops": alg, "tile_table_int16": table[0].tolist(),
+           "tile_table_note": "size classes min(M,N) <128,<256,<512,<1024,<2048,>=2048; 0=128x128, 1=64x64"}
+    for mode, name in ((0, "persistent_graph"), (1, "per_product_graph")):
+        with torch.cuda.stream(s):
+            batch.run(mode)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            batch.run(mode, stream=s)
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            flush.fill_(5)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.replay()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = min(ts)
+        out[name] = {"ms": round(ms, 3), "alg_gops": round(alg / (ms * 1e-3) / 1e9, 1),
+                     "dense_equiv_gops": round(dense / (ms * 1e-3) / 1e9, 1),
+                     "launches": 2 if mode == 0 else 2 * len(sizes)}
+        del g
+    out["speedup_persistent_vs_per_product"] = round(
+        out["per_product_graph"]["ms"] / out["persistent_graph"]["ms"], 3)
+    batch.close()
     return out
 
 

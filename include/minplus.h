@@ -183,11 +183,40 @@ typedef struct mp_problem {
 } mp_problem;
 
 /* Runs every product of probs[0..count) (HOST array).  mode 0: one
- * persistent launch over a tile work list of all products; mode 1: one
- * launch per product (the plain form, for comparison).  No output may
- * overlap any input of any problem.  Asynchronous.  Errors: MP_EINVAL,
- * MP_EALIAS, MP_ENOMEM, MP_ECUDA. */
+ * occupancy-mask launch and one persistent launch over a tile work list of
+ * all products; mode 1: a mask launch and a product launch per product (the
+ * plain form, for comparison).  No output may overlap any input of any
+ * problem.  Prepares, runs and releases a batch (below) and synchronizes
+ * the stream before returning.  Errors: MP_EINVAL, MP_EALIAS, MP_ENOMEM,
+ * MP_ECUDA. */
 int mp_minplus_mul_batched(const mp_problem *probs, int count, int mode, void *stream);
+
+/* A prepared batch: the tile work list (every output tile of every product
+ * in the tile shape the tuning table gives its size class, most expensive
+ * first), the problem descriptors and the mask-block list are uploaded once
+ * (synchronously) and owned by the opaque handle, together with the mask
+ * buffer.  mp_batch_run only enqueues kernels and one memset on stream, so
+ * it may be captured in a CUDA graph and replayed; the operands may change
+ * between runs but not their addresses or shapes.  One batch must not run
+ * concurrently with itself.  mp_batch_destroy frees the handle (the caller
+ * makes sure no run is in flight). */
+typedef struct mp_batch mp_batch;
+int mp_batch_prepare(const mp_problem *probs, int count, mp_batch **out);
+int mp_batch_run(mp_batch *batch, int mode, void *stream);
+int mp_batch_destroy(mp_batch *batch);
+
+/* ---- tile-shape autotuner ---------------------------------------------------
+ * The dense product uses a 128x128 (shape 0) or 64x64 (shape 1) output
+ * tile chosen per element type and size class of min(M, N): [0,128),
+ * [128,256), [256,512), [512,1024), [1024,2048), [2048,inf).  The table is
+ * int32[2][6] (row 0 int16, row 1 uint8), per device.  mp_autotune times both
+ * shapes on one synthetic square product per class on the current device,
+ * installs the faster ones and writes the table to table_out (HOST, may be
+ * NULL); synchronous.  mp_tuning_set installs a table (e.g. from a cache);
+ * mp_tuning_get reads the current one (a built-in default until tuned). */
+int mp_autotune(int32_t *table_out);
+int mp_tuning_set(const int32_t *table);
+int mp_tuning_get(int32_t *table);
 
 /* ---- K6: DPX add-min peak ------------------------------------------------
  * Runs independent __viaddmin_u16x2 chains on every SM for `iters`

@@ -64,6 +64,12 @@ def lib() -> ctypes.CDLL:
         "mp_diag_min": (I, [P, I64, I64, P, P]),
         "mp_min_trace": (I, [P, P, I64, I64, I64, P, P]),
         "mp_minplus_mul_batched": (I, [P, I, I, P]),
+        "mp_batch_prepare": (I, [P, I, P]),
+        "mp_batch_run": (I, [P, I, P]),
+        "mp_batch_destroy": (I, [P]),
+        "mp_autotune": (I, [P]),
+        "mp_tuning_set": (I, [P]),
+        "mp_tuning_get": (I, [P]),
         "mp_dpx_peak": (I, [I, I64, P]),
         "mp_device_status": (I, []),
         "mp_last_error": (ctypes.c_char_p, []),
@@ -153,6 +159,88 @@ def mp_minplus_mul_batched(problems, mode: int = 0, stream=None):
                             max(Z.stride(0), 1), dtype, 0)
     _check(lib().mp_minplus_mul_batched(ctypes.cast(arr, ctypes.c_void_p), len(problems),
                                         int(mode), _stream(stream)))
+
+
+class Batch:
+    """A prepared batch of products (mp_batch_prepare); run() is graph-capturable."""
+
+    def __init__(self, problems):
+        import torch
+        self._keep = list(problems)
+        arr = (mp_problem * len(problems))()
+        for i, (X, Y, Z) in enumerate(problems):
+            dtype = {torch.int16: MP_I16, torch.uint8: MP_U8}[X.dtype]
+            arr[i] = mp_problem(X.data_ptr(), Y.data_ptr(), Z.data_ptr(), X.shape[0], Y.shape[1],
+                                X.shape[1], max(X.stride(0), 1), max(Y.stride(0), 1),
+                                max(Z.stride(0), 1), dtype, 0)
+        h = ctypes.c_void_p()
+        _check(lib().mp_batch_prepare(ctypes.cast(arr, ctypes.c_void_p), len(problems),
+                                      ctypes.byref(h)))
+        self._h = h
+
+    def run(self, mode: int = 0, stream=None):
+        _check(lib().mp_batch_run(self._h, int(mode), _stream(stream)))
+
+    def close(self):
+        if self._h:
+            lib().mp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mp_autotune() -> np.ndarray:
+    """Times both tile shapes per size class on this device and installs the
+    faster; returns the int32[2][6] table (row 0 int16, row 1 uint8)."""
+    t = np.zeros((2, 6), dtype=np.int32)
+    _check(lib().mp_autotune(t.ctypes.data))
+    return t
+
+
+def mp_tuning_get() -> np.ndarray:
+    t = np.zeros((2, 6), dtype=np.int32)
+    _check(lib().mp_tuning_get(t.ctypes.data))
+    return t
+
+
+def mp_tuning_set(table) -> None:
+    t = np.ascontiguousarray(table, dtype=np.int32).reshape(2, 6)
+    _check(lib().mp_tuning_set(t.ctypes.data))
+
+
+def save_tuning(path: str) -> None:
+    """Writes the current table to a JSON cache keyed by the GPU's name."""
+    import json
+
+    import torch
+    key = torch.cuda.get_device_name()
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+    data[key] = mp_tuning_get().tolist()
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1)
+
+
+def load_tuning(path: str) -> bool:
+    """Installs the cached table for this GPU, if the cache has one."""
+    import json
+
+    import torch
+    if not os.path.exists(path):
+        return False
+    with open(path) as f:
+        data = json.load(f)
+    t = data.get(torch.cuda.get_device_name())
+    if t is None:
+        return False
+    mp_tuning_set(t)
+    return True
 
 
 # ------------------------------------------------------------ power chains

@@ -19,6 +19,12 @@ int dense_minplus_noalloc(const void *X, const void *Y, void *Z, int64_t M, int6
                           int64_t K, int64_t ldx, int64_t ldy, int64_t ldz, int dtype,
                           cudaStream_t s);
 int batched_run(const mp_problem *probs, int count, int mode, cudaStream_t s);
+int batch_prepare(const mp_problem *probs, int count, mp_batch **out);
+int batch_run(mp_batch *b, int mode, cudaStream_t s);
+int batch_destroy(mp_batch *b);
+int autotune(int32_t *table_out);
+int tuning_set(const int32_t *table);
+int tuning_get(int32_t *table);
 
 // ------------------------------------------------------------------ errors
 static thread_local char g_err[1024] = "";
@@ -458,6 +464,30 @@ int mp_minplus_mul_batched(const mp_problem *probs, int count, int mode, void *s
     if (count < 0 || (count > 0 && !probs)) return set_error(MP_EINVAL, "bad problem list");
     if (mode != 0 && mode != 1) return set_error(MP_EINVAL, "mode %d", mode);
     return batched_run(probs, count, mode, (cudaStream_t)stream);
+}
+
+int mp_batch_prepare(const mp_problem *probs, int count, mp_batch **out) {
+    if (!out) return set_error(MP_EINVAL, "out is NULL");
+    *out = nullptr;
+    return batch_prepare(probs, count, out);
+}
+
+int mp_batch_run(mp_batch *batch, int mode, void *stream) {
+    return batch_run(batch, mode, (cudaStream_t)stream);
+}
+
+int mp_batch_destroy(mp_batch *batch) { return batch_destroy(batch); }
+
+int mp_autotune(int32_t *table_out) { return autotune(table_out); }
+
+int mp_tuning_set(const int32_t *table) {
+    if (!table) return set_error(MP_EINVAL, "table is NULL");
+    return tuning_set(table);
+}
+
+int mp_tuning_get(int32_t *table) {
+    if (!table) return set_error(MP_EINVAL, "table is NULL");
+    return tuning_get(table);
 }
 
 int mp_dpx_peak(int variant, int64_t iters, double *ops_per_s) {

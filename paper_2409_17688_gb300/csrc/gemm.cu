@@ -16,7 +16,10 @@
 // INF in X or in Y (a precomputed occupancy mask per operand) cannot lower
 // any minimum, so their K-range is skipped for the tile.
 #include <algorithm>
+#include <map>
+#include <memory>
 #include <mutex>
+#include <cstring>
 
 #include "mp_internal.cuh"
 
@@ -53,94 +56,109 @@ __global__ void block_mask_kernel(const T *__restrict__ A, int64_t rows, int64_t
     if (threadIdx.x == 0) mask[bi * nbc + bj] = (uint8_t)(found ? 1 : 0);
 }
 
-template <typename T>
+// Tile shapes.  Both use 256 threads as a 16 x 16 grid, each thread owning
+// TM rows x TN columns of the output tile (TN/2 packed accumulators per row).
+template <int BM_, int BN_>
+struct TileCfg {
+    static constexpr int BM = BM_, BN = BN_;
+    static constexpr int TM = BM_ / 16, TN = BN_ / 16;
+    static constexpr int XSPLIT = THREADS / BM_;       // threads per X row
+    static constexpr int XK = BK / XSPLIT;              // k values per thread (16 or 8)
+    static constexpr int YP = BK * BN_ / 8 / THREADS;  // 8-column pieces of Y per thread
+};
+using Tile128 = TileCfg<128, 128>;
+using Tile64 = TileCfg<64, 64>;
+
+template <typename Cfg>
 struct Stage {
-    // register staging of one K-step: 16 X values and 16 Y values per thread
-    uint32_t x[8];   // X[m][k0+kh .. +16] as 8 words of two 16-bit values
-    uint32_t y[8];   // Y[k][n0+nc .. +16] widened to 16-bit, 8 words
+    uint32_t x[Cfg::XK / 2];     // X[m][k0+kb .. +XK] as pairs of 16-bit values
+    uint32_t y[Cfg::YP][4];      // Y[k][n0+nc .. +8] widened to 16-bit pairs
+};
+
+// Shared-memory tiles, sized for the larger shape and reused by the smaller.
+struct TileSmem {
+    uint32_t Xs[2][BK][BM];  // X^T, each value duplicated into both halves
+    uint16_t Ys[2][BK][BN];
 };
 
 template <typename T>
+__device__ __forceinline__ void widen8(const T *src, bool vec, uint32_t (&w)[4]) {
+    if (sizeof(T) == 2) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(src));
+        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    } else {
+        const uint2 a = __ldg(reinterpret_cast<const uint2 *>(src));
+        w[0] = __byte_perm(a.x, 0, 0x4140);
+        w[1] = __byte_perm(a.x, 0, 0x4342);
+        w[2] = __byte_perm(a.y, 0, 0x4140);
+        w[3] = __byte_perm(a.y, 0, 0x4342);
+    }
+}
+
+template <typename T, typename Cfg>
 __device__ __forceinline__ void load_tile(const T *__restrict__ X, const T *__restrict__ Y,
                                           int64_t M, int64_t N, int64_t K, int64_t ldx,
                                           int64_t ldy, int64_t m0, int64_t n0, int64_t k0,
-                                          bool vecx_ok, bool vecy_ok, Stage<T> &st) {
+                                          bool vecx_ok, bool vecy_ok, Stage<Cfg> &st) {
     const int t = threadIdx.x;
     const uint32_t inf = Elem<T>::inf;
-    // X: row m = t/2, k half kh = (t&1)*16
     {
-        int64_t m = m0 + (t >> 1), k = k0 + (t & 1) * 16;
-        if (vecx_ok && m < M && k + 16 <= K) {
-            const T *src = X + m * ldx + k;
-            if (sizeof(T) == 2) {
-                uint4 a = __ldg(reinterpret_cast<const uint4 *>(src));
-                uint4 b = __ldg(reinterpret_cast<const uint4 *>(src) + 1);
-                st.x[0] = a.x; st.x[1] = a.y; st.x[2] = a.z; st.x[3] = a.w;
-                st.x[4] = b.x; st.x[5] = b.y; st.x[6] = b.z; st.x[7] = b.w;
+        const int64_t m = m0 + t / Cfg::XSPLIT, k = k0 + (t % Cfg::XSPLIT) * Cfg::XK;
+#pragma unroll
+        for (int pc = 0; pc < Cfg::XK / 8; ++pc) {
+            const int64_t kk = k + 8 * pc;
+            if (vecx_ok && m < M && kk + 8 <= K) {
+                uint32_t w[4];
+                widen8<T>(X + m * ldx + kk, true, w);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) st.x[4 * pc + j] = w[j];
             } else {
-                uint4 a = __ldg(reinterpret_cast<const uint4 *>(src));
-                uint32_t w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    st.x[2 * j] = __byte_perm(w[j], 0, 0x4140);
-                    st.x[2 * j + 1] = __byte_perm(w[j], 0, 0x4342);
+                    uint32_t lo = inf, hi = inf;
+                    if (m < M && kk + 2 * j < K) lo = (uint32_t)X[m * ldx + kk + 2 * j];
+                    if (m < M && kk + 2 * j + 1 < K) hi = (uint32_t)X[m * ldx + kk + 2 * j + 1];
+                    st.x[4 * pc + j] = lo | (hi << 16);
                 }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                uint32_t lo = inf, hi = inf;
-                if (m < M && k + 2 * j < K) lo = (uint32_t)X[m * ldx + k + 2 * j];
-                if (m < M && k + 2 * j + 1 < K) hi = (uint32_t)X[m * ldx + k + 2 * j + 1];
-                st.x[j] = lo | (hi << 16);
             }
         }
     }
-    // Y: row k = t/8, columns nc = (t&7)*16
-    {
-        int64_t k = k0 + (t >> 3), n = n0 + (t & 7) * 16;
-        if (vecy_ok && k < K && n + 16 <= N) {
-            const T *src = Y + k * ldy + n;
-            if (sizeof(T) == 2) {
-                uint4 a = __ldg(reinterpret_cast<const uint4 *>(src));
-                uint4 b = __ldg(reinterpret_cast<const uint4 *>(src) + 1);
-                st.y[0] = a.x; st.y[1] = a.y; st.y[2] = a.z; st.y[3] = a.w;
-                st.y[4] = b.x; st.y[5] = b.y; st.y[6] = b.z; st.y[7] = b.w;
-            } else {
-                uint4 a = __ldg(reinterpret_cast<const uint4 *>(src));
-                uint32_t w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    st.y[2 * j] = __byte_perm(w[j], 0, 0x4140);
-                    st.y[2 * j + 1] = __byte_perm(w[j], 0, 0x4342);
-                }
-            }
+    for (int i = 0; i < Cfg::YP; ++i) {
+        const int pc = t + i * THREADS;
+        const int64_t k = k0 + pc / (Cfg::BN / 8), n = n0 + (pc % (Cfg::BN / 8)) * 8;
+        if (vecy_ok && k < K && n + 8 <= N) {
+            widen8<T>(Y + k * ldy + n, true, st.y[i]);
         } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < 4; ++j) {
                 uint32_t lo = inf, hi = inf;
                 if (k < K && n + 2 * j < N) lo = (uint32_t)Y[k * ldy + n + 2 * j];
                 if (k < K && n + 2 * j + 1 < N) hi = (uint32_t)Y[k * ldy + n + 2 * j + 1];
-                st.y[j] = lo | (hi << 16);
+                st.y[i][j] = lo | (hi << 16);
             }
         }
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void store_tile(const Stage<T> &st, uint32_t (*Xs)[BM],
-                                           uint16_t (*Ys)[BN]) {
+template <typename Cfg>
+__device__ __forceinline__ void store_tile(const Stage<Cfg> &st, TileSmem &sm, int buf) {
     const int t = threadIdx.x;
-    const int m = t >> 1, kh = (t & 1) * 16;
+    const int m = t / Cfg::XSPLIT, kb = (t % Cfg::XSPLIT) * Cfg::XK;
+    uint32_t *xs = &sm.Xs[buf][0][0];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        Xs[kh + 2 * j][m] = dup16(st.x[j] & 0xFFFFu);
-        Xs[kh + 2 * j + 1][m] = dup16(st.x[j] >> 16);
+    for (int j = 0; j < Cfg::XK / 2; ++j) {
+        xs[(kb + 2 * j) * Cfg::BM + m] = dup16(st.x[j] & 0xFFFFu);
+        xs[(kb + 2 * j + 1) * Cfg::BM + m] = dup16(st.x[j] >> 16);
     }
-    const int k = t >> 3, nc = (t & 7) * 16;
-    uint4 *dst = reinterpret_cast<uint4 *>(&Ys[k][nc]);
-    dst[0] = make_uint4(st.y[0], st.y[1], st.y[2], st.y[3]);
-    dst[1] = make_uint4(st.y[4], st.y[5], st.y[6], st.y[7]);
+    uint16_t *ys = &sm.Ys[buf][0][0];
+#pragma unroll
+    for (int i = 0; i < Cfg::YP; ++i) {
+        const int pc = t + i * THREADS;
+        const int k = pc / (Cfg::BN / 8), nc = (pc % (Cfg::BN / 8)) * 8;
+        *reinterpret_cast<uint4 *>(ys + k * Cfg::BN + nc) =
+            make_uint4(st.y[i][0], st.y[i][1], st.y[i][2], st.y[i][3]);
+    }
 }
 
 template <typename T>
@@ -149,72 +167,76 @@ struct TileArgs {
     const T *Y;
     T *Z;
     int64_t M, N, K, ldx, ldy, ldz;
-    const uint8_t *xmask, *ymask;  // occupancy masks, or NULL for "all active"
-    int64_t kblocks, nblocks;
+    const uint8_t *xmask, *ymask;  // occupancy masks (128-blocks), or NULL for "all active"
+    int64_t kblocks, nblocks;      // mask grid: K and N in 128-blocks
     int vecx, vecy, vecz;
     int32_t *gdiag;
 };
 
-// One 128 x 128 output tile (bi, bj) of Z = X (x) Y.  Ends with every thread
-// past its last shared-memory read, so a persistent caller may start the
-// next tile at once.
-template <typename T>
+// One output tile (bi, bj) of Z = X (x) Y in shape Cfg.  Ends with every
+// thread past its last shared-memory read, so a persistent caller may start
+// the next tile at once.
+template <typename T, typename Cfg>
 __device__ __forceinline__ void gemm_tile(const TileArgs<T> &a, int64_t bi, int64_t bj,
-                                          uint32_t (*Xs)[BK][BM], uint16_t (*Ys)[BK][BN]) {
-    const T *__restrict__ X = a.X;
-    const T *__restrict__ Y = a.Y;
-    T *__restrict__ Z = a.Z;
-    const int64_t M = a.M, N = a.N, K = a.K, ldx = a.ldx, ldy = a.ldy, ldz = a.ldz;
-    const uint8_t *__restrict__ xmask = a.xmask;
-    const uint8_t *__restrict__ ymask = a.ymask;
-    const int64_t kblocks = a.kblocks, nblocks = a.nblocks;
-    const int vecx = a.vecx, vecy = a.vecy, vecz = a.vecz;
-    int32_t *__restrict__ gdiag = a.gdiag;
-    const int64_t m0 = bi * BM, n0 = bj * BN;
+                                          TileSmem &sm) {
+    constexpr int TM = Cfg::TM, TW = Cfg::TN / 2;
+    const int64_t m0 = bi * Cfg::BM, n0 = bj * Cfg::BN;
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     const uint32_t inf2 = Elem<T>::inf * 0x10001u;
+    const int64_t mb = m0 / MASK_BLOCK, nbk = n0 / MASK_BLOCK;
 
-    uint32_t acc[8][4];
+    uint32_t acc[TM][TW];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+    for (int r = 0; r < TM; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = inf2;
+        for (int c = 0; c < TW; ++c) acc[r][c] = inf2;
 
-    const int64_t ktiles = (K + BK - 1) / BK;
+    const int64_t ktiles = (a.K + BK - 1) / BK;
     auto active = [&](int64_t kt) -> bool {
-        if (!xmask) return true;
-        int64_t kb = (kt * BK) / MASK_BLOCK;
-        return xmask[bi * kblocks + kb] && ymask[kb * nblocks + bj];
+        if (!a.xmask) return true;
+        const int64_t kb = (kt * BK) / MASK_BLOCK;
+        return a.xmask[mb * a.kblocks + kb] && a.ymask[kb * a.nblocks + nbk];
     };
     auto next_active = [&](int64_t kt) -> int64_t {
         while (kt < ktiles && !active(kt)) ++kt;
         return kt;
     };
 
-    Stage<T> st;
+    Stage<Cfg> st;
     int64_t kt = next_active(0);
     int buf = 0;
     if (kt < ktiles) {
-        load_tile<T>(X, Y, M, N, K, ldx, ldy, m0, n0, kt * BK, vecx, vecy, st);
-        store_tile<T>(st, Xs[0], Ys[0]);
+        load_tile<T, Cfg>(a.X, a.Y, a.M, a.N, a.K, a.ldx, a.ldy, m0, n0, kt * BK, a.vecx, a.vecy, st);
+        store_tile<Cfg>(st, sm, 0);
     }
     __syncthreads();
     while (kt < ktiles) {
-        int64_t kn = next_active(kt + 1);
-        if (kn < ktiles) load_tile<T>(X, Y, M, N, K, ldx, ldy, m0, n0, kn * BK, vecx, vecy, st);
+        const int64_t kn = next_active(kt + 1);
+        if (kn < ktiles)
+            load_tile<T, Cfg>(a.X, a.Y, a.M, a.N, a.K, a.ldx, a.ldy, m0, n0, kn * BK, a.vecx, a.vecy, st);
+        const uint32_t *xs = &sm.Xs[buf][0][0];
+        const uint16_t *ys = &sm.Ys[buf][0][0];
 #pragma unroll 4
         for (int k = 0; k < BK; ++k) {
-            uint4 xa = *reinterpret_cast<const uint4 *>(&Xs[buf][k][ty * 8]);
-            uint4 xb = *reinterpret_cast<const uint4 *>(&Xs[buf][k][ty * 8 + 4]);
-            uint4 yv = *reinterpret_cast<const uint4 *>(&Ys[buf][k][tx * 8]);
-            const uint32_t xr[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-            const uint32_t yr[4] = {yv.x, yv.y, yv.z, yv.w};
+            uint32_t xr[TM], yr[TW];
 #pragma unroll
-            for (int r = 0; r < 8; ++r)
+            for (int r = 0; r < TM; r += 4) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(xs + k * Cfg::BM + ty * TM + r);
+                xr[r] = v.x; xr[r + 1] = v.y; xr[r + 2] = v.z; xr[r + 3] = v.w;
+            }
+            if (TW == 4) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(ys + k * Cfg::BN + tx * Cfg::TN);
+                yr[0] = v.x; yr[1] = v.y; yr[2 % TW] = v.z; yr[3 % TW] = v.w;
+            } else {
+                const uint2 v = *reinterpret_cast<const uint2 *>(ys + k * Cfg::BN + tx * Cfg::TN);
+                yr[0] = v.x; yr[1 % TW] = v.y;
+            }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = __viaddmin_u16x2(xr[r], yr[c], acc[r][c]);
+            for (int r = 0; r < TM; ++r)
+#pragma unroll
+                for (int c = 0; c < TW; ++c) acc[r][c] = __viaddmin_u16x2(xr[r], yr[c], acc[r][c]);
         }
-        if (kn < ktiles) store_tile<T>(st, Xs[buf ^ 1], Ys[buf ^ 1]);
+        if (kn < ktiles) store_tile<Cfg>(st, sm, buf ^ 1);
         __syncthreads();
         buf ^= 1;
         kt = kn;
@@ -223,57 +245,130 @@ __device__ __forceinline__ void gemm_tile(const TileArgs<T> &a, int64_t bi, int6
     // epilogue
     int32_t dmin = 0x7FFFFFFF;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        int64_t m = m0 + ty * 8 + r;
-        if (m >= M) continue;
-        int64_t nb = n0 + tx * 8;
-        T *zrow = Z + m * ldz;
-        if (vecz && nb + 8 <= N) {
+    for (int r = 0; r < TM; ++r) {
+        const int64_t m = m0 + ty * TM + r;
+        if (m >= a.M) continue;
+        const int64_t nb = n0 + tx * Cfg::TN;
+        T *zrow = a.Z + m * a.ldz;
+        if (a.vecz && nb + Cfg::TN <= a.N) {
             if (sizeof(T) == 2) {
-                *reinterpret_cast<uint4 *>(zrow + nb) = make_uint4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+                if (TW == 4)
+                    *reinterpret_cast<uint4 *>(zrow + nb) = make_uint4(acc[r][0], acc[r][1 % TW], acc[r][2 % TW], acc[r][3 % TW]);
+                else
+                    *reinterpret_cast<uint2 *>(zrow + nb) = make_uint2(acc[r][0], acc[r][1 % TW]);
             } else {
-                uint32_t lo = __byte_perm(acc[r][0], acc[r][1], 0x6420);
-                uint32_t hi = __byte_perm(acc[r][2], acc[r][3], 0x6420);
-                *reinterpret_cast<uint2 *>(zrow + nb) = make_uint2(lo, hi);
+                const uint32_t lo = __byte_perm(acc[r][0], acc[r][1 % TW], 0x6420);
+                if (TW == 4) {
+                    const uint32_t hi = __byte_perm(acc[r][2 % TW], acc[r][3 % TW], 0x6420);
+                    *reinterpret_cast<uint2 *>(zrow + nb) = make_uint2(lo, hi);
+                } else {
+                    *reinterpret_cast<uint32_t *>(zrow + nb) = lo;
+                }
             }
         } else {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (nb + 2 * c < N) zrow[nb + 2 * c] = (T)(acc[r][c] & 0xFFFFu);
-                if (nb + 2 * c + 1 < N) zrow[nb + 2 * c + 1] = (T)(acc[r][c] >> 16);
+            for (int c = 0; c < TW; ++c) {
+                if (nb + 2 * c < a.N) zrow[nb + 2 * c] = (T)(acc[r][c] & 0xFFFFu);
+                if (nb + 2 * c + 1 < a.N) zrow[nb + 2 * c + 1] = (T)(acc[r][c] >> 16);
             }
         }
-        if (gdiag) {
+        if (a.gdiag) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < TW; ++c) {
                 if (nb + 2 * c == m) dmin = min(dmin, (int32_t)(acc[r][c] & 0xFFFFu));
                 if (nb + 2 * c + 1 == m) dmin = min(dmin, (int32_t)(acc[r][c] >> 16));
             }
         }
     }
-    if (gdiag && dmin != 0x7FFFFFFF) atomicMin(gdiag, dmin);
+    if (a.gdiag && dmin != 0x7FFFFFFF) atomicMin(a.gdiag, dmin);
+}
+
+template <typename T, typename Cfg>
+__global__ void __launch_bounds__(THREADS) dense_minplus_kernel(TileArgs<T> a) {
+    __shared__ __align__(16) TileSmem sm;
+    gemm_tile<T, Cfg>(a, blockIdx.y, blockIdx.x, sm);
+}
+
+// ------------------------------------------------------- tile-shape tuning
+// Size classes by min(M, N): [0,128) [128,256) [256,512) [512,1024)
+// [1024,2048) [2048,inf).  The table holds the tile shape (0: 128x128,
+// 1: 64x64) per element type and class, per device; mp_autotune measures it.
+constexpr int kClasses = 6;
+struct TuneTable {
+    int32_t cfg[2][kClasses];
+};
+std::mutex g_tune_mu;
+std::map<int, TuneTable> g_tune;
+
+int size_class(int64_t M, int64_t N) {
+    const int64_t s = std::min(M, N);
+    int c = 0;
+    for (int64_t lim = 128; c < kClasses - 1 && s >= lim; lim *= 2) ++c;
+    return c;
+}
+
+TuneTable default_table() {
+    TuneTable t;
+    for (int d = 0; d < 2; ++d)
+        for (int c = 0; c < kClasses; ++c) t.cfg[d][c] = c < 2 ? 1 : 0;
+    return t;
+}
+
+int current_table(TuneTable *out) {
+    int dev = -1;
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(dev);
+    *out = it == g_tune.end() ? default_table() : it->second;
+    return MP_OK;
+}
+
+int choose_cfg(int dtype, int64_t M, int64_t N, int *cfg) {
+    TuneTable t;
+    MP_TRY(current_table(&t));
+    *cfg = t.cfg[dtype == MP_U8 ? 1 : 0][size_class(M, N)];
+    return MP_OK;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(THREADS) dense_minplus_kernel(TileArgs<T> a) {
-    __shared__ __align__(16) uint32_t Xs[2][BK][BM];
-    __shared__ __align__(16) uint16_t Ys[2][BK][BN];
-    gemm_tile<T>(a, blockIdx.y, blockIdx.x, Xs, Ys);
+TileArgs<T> make_args(const T *X, const T *Y, T *Z, int64_t M, int64_t N, int64_t K, int64_t ldx,
+                      int64_t ldy, int64_t ldz, const uint8_t *xm, const uint8_t *ym,
+                      int32_t *gdiag) {
+    const int64_t nb128 = (N + MASK_BLOCK - 1) / MASK_BLOCK;
+    const int64_t kb = (K + MASK_BLOCK - 1) / MASK_BLOCK;
+    TileArgs<T> ta;
+    ta.X = X; ta.Y = Y; ta.Z = Z;
+    ta.M = M; ta.N = N; ta.K = K; ta.ldx = ldx; ta.ldy = ldy; ta.ldz = ldz;
+    ta.xmask = xm; ta.ymask = ym; ta.kblocks = kb; ta.nblocks = nb128;
+    // vector loads of 8 elements need 8-element-aligned rows
+    ta.vecx = ((uintptr_t)X % (8 * sizeof(T)) == 0) && (ldx % 8 == 0);
+    ta.vecy = ((uintptr_t)Y % (8 * sizeof(T)) == 0) && (ldy % 8 == 0);
+    // the epilogue stores up to 8 outputs of a row at once
+    ta.vecz = ((uintptr_t)Z % 16 == 0) && (ldz % 8 == 0);
+    ta.gdiag = gdiag;
+    return ta;
+}
+
+template <typename T>
+int launch_product(const TileArgs<T> &ta, int cfg, cudaStream_t s) {
+    const int bm = cfg == 1 ? 64 : 128;
+    const int64_t mb = (ta.M + bm - 1) / bm, nb = (ta.N + bm - 1) / bm;
+    if (mb > 65535) return set_error(MP_EINVAL, "M = %lld too large for one launch", (long long)ta.M);
+    dim3 grid((unsigned)nb, (unsigned)mb);
+    if (cfg == 1) dense_minplus_kernel<T, Tile64><<<grid, THREADS, 0, s>>>(ta);
+    else dense_minplus_kernel<T, Tile128><<<grid, THREADS, 0, s>>>(ta);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
 }
 
 template <typename T>
 int run_dense(const T *X, const T *Y, T *Z, int64_t M, int64_t N, int64_t K, int64_t ldx,
-              int64_t ldy, int64_t ldz, int32_t *gdiag, bool use_mask, cudaStream_t s) {
-    const int64_t elems16 = 16 / (int64_t)sizeof(T);
-    int vecx = ((uintptr_t)X % 16 == 0) && (ldx % elems16 == 0);
-    int vecy = ((uintptr_t)Y % 16 == 0) && (ldy % elems16 == 0);
-    // epilogue stores 8 outputs per row at a time: 16 B (int16) or 8 B (uint8)
-    int vecz = ((uintptr_t)Z % 16 == 0) && (ldz % 8 == 0);
-    const int64_t mb = (M + BM - 1) / BM, nb = (N + BN - 1) / BN;
+              int64_t ldy, int64_t ldz, int32_t *gdiag, int cfg, cudaStream_t s) {
+    const int64_t mb = (M + MASK_BLOCK - 1) / MASK_BLOCK, nb = (N + MASK_BLOCK - 1) / MASK_BLOCK;
     const int64_t kb = (K + MASK_BLOCK - 1) / MASK_BLOCK;
     DevBuf masks;
     const uint8_t *xm = nullptr, *ym = nullptr;
-    if (use_mask && K > 0) {
+    if (K > 0) {
         MP_TRY(masks.alloc((size_t)(mb * kb + kb * nb), s));
         uint8_t *xmw = masks.as<uint8_t>(), *ymw = xmw + mb * kb;
         block_mask_kernel<T><<<dim3((unsigned)kb, (unsigned)mb), 256, 0, s>>>(X, M, K, ldx, xmw, kb);
@@ -282,12 +377,7 @@ int run_dense(const T *X, const T *Y, T *Z, int64_t M, int64_t N, int64_t K, int
         xm = xmw;
         ym = ymw;
     }
-    if (mb > 65535) return set_error(MP_EINVAL, "M = %lld too large for one launch", (long long)M);
-    dim3 grid((unsigned)nb, (unsigned)mb);
-    TileArgs<T> ta{X, Y, Z, M, N, K, ldx, ldy, ldz, xm, ym, kb, nb, vecx, vecy, vecz, gdiag};
-    dense_minplus_kernel<T><<<grid, THREADS, 0, s>>>(ta);
-    MP_CUDA_TRY(cudaGetLastError());
-    return MP_OK;
+    return launch_product<T>(make_args<T>(X, Y, Z, M, N, K, ldx, ldy, ldz, xm, ym, gdiag), cfg, s);
 }
 
 }  // namespace
@@ -296,21 +386,26 @@ int dense_minplus(const void *X, const void *Y, void *Z, int64_t M, int64_t N, i
                   int64_t ldx, int64_t ldy, int64_t ldz, int dtype, int32_t *gdiag,
                   cudaStream_t s) {
     if (M == 0 || N == 0) return MP_OK;
+    int cfg = 0;
+    MP_TRY(choose_cfg(dtype, M, N, &cfg));
     if (dtype == MP_I16)
         return run_dense<uint16_t>((const uint16_t *)X, (const uint16_t *)Y, (uint16_t *)Z, M, N,
-                                   K, ldx, ldy, ldz, gdiag, true, s);
+                                   K, ldx, ldy, ldz, gdiag, cfg, s);
     if (dtype == MP_U8)
         return run_dense<uint8_t>((const uint8_t *)X, (const uint8_t *)Y, (uint8_t *)Z, M, N, K,
-                                  ldx, ldy, ldz, gdiag, true, s);
+                                  ldx, ldy, ldz, gdiag, cfg, s);
     return set_error(MP_EINVAL, "unknown dtype %d", dtype);
 }
 
 // ------------------------------------------------------------------ K5
-// Many products of uneven sizes in one persistent launch.  The host lists
-// every 128 x 128 output tile of every product, longest K first, and the
-// CTAs (a full wave: 3 per SM) take tiles from an atomic counter until the
-// list is exhausted.  The occupancy masks of all operands come from one
-// preceding launch over a list of mask blocks.
+// Many products of uneven sizes.  mp_batch_prepare lists every output tile
+// of every product (in the tile shape the tuning table gives its size
+// class), most expensive first, uploads that list with the problem
+// descriptors and the list of occupancy-mask blocks, and owns the mask
+// buffer.  mp_batch_run then only launches kernels (so it can be captured
+// in a CUDA graph): mode 0 one mask launch and one persistent launch whose
+// CTAs (a full wave) take tiles from an atomic counter; mode 1 a mask launch
+// and a product launch per problem, the plain form.
 
 namespace {
 
@@ -321,9 +416,10 @@ struct BatchProb {
     const uint8_t *xmask, *ymask;
     int64_t kblocks, nblocks;
     int32_t dtype, vecx, vecy, vecz;
+    int32_t cfg, job0, job1, pad;
 };
 struct BatchTile {
-    int32_t prob, bi, bj, pad;
+    int32_t prob, bi, bj, cfg;
 };
 struct MaskJob {
     const void *A;
@@ -350,11 +446,22 @@ __global__ void batched_mask_kernel(const MaskJob *__restrict__ jobs) {
     if (threadIdx.x == 0) j.mask[j.bi * j.nbc + j.bj] = (uint8_t)(found ? 1 : 0);
 }
 
+template <typename T>
+__device__ __forceinline__ TileArgs<T> prob_args(const BatchProb &p) {
+    TileArgs<T> a;
+    a.X = (const T *)p.X; a.Y = (const T *)p.Y; a.Z = (T *)p.Z;
+    a.M = p.M; a.N = p.N; a.K = p.K; a.ldx = p.ldx; a.ldy = p.ldy; a.ldz = p.ldz;
+    a.xmask = p.xmask; a.ymask = p.ymask; a.kblocks = p.kblocks; a.nblocks = p.nblocks;
+    a.vecx = p.vecx; a.vecy = p.vecy; a.vecz = p.vecz;
+    a.gdiag = nullptr;
+    return a;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(THREADS, 2)
 batched_minplus_kernel(const BatchProb *__restrict__ probs, const BatchTile *__restrict__ tiles,
                        int ntiles, int *counter) {
-    __shared__ __align__(16) uint32_t Xs[2][BK][BM];
-    __shared__ __align__(16) uint16_t Ys[2][BK][BN];
+    __shared__ __align__(16) TileSmem sm;
     __shared__ int next;
     while (true) {
         if (threadIdx.x == 0) next = atomicAdd(counter, 1);
@@ -363,37 +470,38 @@ batched_minplus_kernel(const BatchProb *__restrict__ probs, const BatchTile *__r
         __syncthreads();
         if (t >= ntiles) break;
         const BatchTile tl = tiles[t];
-        const BatchProb &p = probs[tl.prob];
-        if (p.dtype == MP_I16) {
-            TileArgs<uint16_t> a{(const uint16_t *)p.X, (const uint16_t *)p.Y, (uint16_t *)p.Z,
-                                 p.M, p.N, p.K, p.ldx, p.ldy, p.ldz, p.xmask, p.ymask,
-                                 p.kblocks, p.nblocks, p.vecx, p.vecy, p.vecz, nullptr};
-            gemm_tile<uint16_t>(a, tl.bi, tl.bj, Xs, Ys);
-        } else {
-            TileArgs<uint8_t> a{(const uint8_t *)p.X, (const uint8_t *)p.Y, (uint8_t *)p.Z,
-                                p.M, p.N, p.K, p.ldx, p.ldy, p.ldz, p.xmask, p.ymask,
-                                p.kblocks, p.nblocks, p.vecx, p.vecy, p.vecz, nullptr};
-            gemm_tile<uint8_t>(a, tl.bi, tl.bj, Xs, Ys);
-        }
+        const TileArgs<T> a = prob_args<T>(probs[tl.prob]);
+        if (tl.cfg == 1) gemm_tile<T, Tile64>(a, tl.bi, tl.bj, sm);
+        else gemm_tile<T, Tile128>(a, tl.bi, tl.bj, sm);
     }
 }
 
 }  // namespace
 
-int batched_run(const mp_problem *probs, int count, int mode, cudaStream_t s) {
-    if (count == 0) return MP_OK;
-    // validation (shared by both modes)
+}  // namespace mp
+
+struct mp_batch {
+    int count = 0, ntiles = 0, njobs = 0, grid = 0;
+    int ntiles16 = 0;  // the int16 tiles come first in the list, then the uint8 ones
+    std::vector<mp::BatchProb> host_probs;
+    mp::DevBuf masks, probs, tiles, jobs, counter;
+};
+
+namespace mp {
+
+int batch_prepare(const mp_problem *probs, int count, mp_batch **out) {
+    if (count < 0 || (count > 0 && !probs)) return set_error(MP_EINVAL, "bad problem list");
     for (int i = 0; i < count; ++i) {
         const mp_problem &p = probs[i];
         if (p.dtype != MP_I16 && p.dtype != MP_U8)
             return set_error(MP_EINVAL, "problem %d: dtype %d", i, p.dtype);
-        if (p.M < 0 || p.N < 0 || p.K < 0)
-            return set_error(MP_EINVAL, "problem %d: negative size", i);
+        if (p.M < 0 || p.N < 0 || p.K < 0) return set_error(MP_EINVAL, "problem %d: negative size", i);
         if (p.M == 0 || p.N == 0) continue;
         if (!p.Z || (p.K > 0 && (!p.X || !p.Y)))
             return set_error(MP_EINVAL, "problem %d: NULL pointer", i);
         if (p.ldx < std::max<int64_t>(p.K, 1) || p.ldy < p.N || p.ldz < p.N)
             return set_error(MP_EINVAL, "problem %d: leading dimension too small", i);
+        if ((p.M + 63) / 64 > 65535) return set_error(MP_EINVAL, "problem %d: M too large", i);
     }
     for (int i = 0; i < count; ++i) {
         const mp_problem &pi = probs[i];
@@ -410,49 +518,45 @@ int batched_run(const mp_problem *probs, int count, int mode, cudaStream_t s) {
                 return set_error(MP_EALIAS, "problem %d's output overlaps problem %d", i, j);
         }
     }
-    if (mode == 1) {
-        for (int i = 0; i < count; ++i) {
-            const mp_problem &p = probs[i];
-            MP_TRY(dense_minplus(p.X, p.Y, p.Z, p.M, p.N, p.K, p.ldx, p.ldy, p.ldz, p.dtype,
-                                 nullptr, s));
-        }
-        return MP_OK;
-    }
-    // mode 0: masks for all operands in one launch, then one persistent launch
-    std::vector<BatchProb> bp((size_t)count);
+    TuneTable tune;
+    MP_TRY(current_table(&tune));
+    DeviceInfo di;
+    MP_TRY(device_info(&di));
+    auto b = std::make_unique<mp_batch>();
+    b->count = count;
+    b->host_probs.resize((size_t)count);
     std::vector<MaskJob> jobs;
-    std::vector<BatchTile> tiles;
-    std::vector<std::pair<int64_t, size_t>> order;  // (K, tile index) for longest-first
+    std::vector<std::pair<double, BatchTile>> order;
     size_t mask_bytes = 0;
     std::vector<size_t> xoff((size_t)count), yoff((size_t)count);
     for (int i = 0; i < count; ++i) {
         const mp_problem &p = probs[i];
-        const int64_t mb = (p.M + BM - 1) / BM, nb = (p.N + BN - 1) / BN;
+        const int64_t mb = (p.M + MASK_BLOCK - 1) / MASK_BLOCK, nb = (p.N + MASK_BLOCK - 1) / MASK_BLOCK;
         const int64_t kb = (p.K + MASK_BLOCK - 1) / MASK_BLOCK;
         xoff[i] = mask_bytes;
         mask_bytes += (size_t)(mb * kb);
         yoff[i] = mask_bytes;
         mask_bytes += (size_t)(kb * nb);
     }
-    DevBuf dmask, dprob, dtile, djob, dcnt;
-    MP_TRY(dmask.alloc(std::max<size_t>(mask_bytes, 16), s));
-    uint8_t *mbase = dmask.as<uint8_t>();
+    MP_TRY(b->masks.alloc(std::max<size_t>(mask_bytes, 16), nullptr, true));
+    uint8_t *mbase = b->masks.as<uint8_t>();
     for (int i = 0; i < count; ++i) {
         const mp_problem &p = probs[i];
-        const int64_t e = p.dtype == MP_I16 ? 2 : 1;
-        const int64_t mb = (p.M + BM - 1) / BM, nb = (p.N + BN - 1) / BN;
+        const int64_t mb = (p.M + MASK_BLOCK - 1) / MASK_BLOCK, nb = (p.N + MASK_BLOCK - 1) / MASK_BLOCK;
         const int64_t kb = (p.K + MASK_BLOCK - 1) / MASK_BLOCK;
-        BatchProb &q = bp[i];
+        const int cfg = tune.cfg[p.dtype == MP_U8 ? 1 : 0][size_class(p.M, p.N)];
+        BatchProb &q = b->host_probs[i];
+        const size_t e = p.dtype == MP_I16 ? 2 : 1;
         q.X = p.X; q.Y = p.Y; q.Z = p.Z;
         q.M = p.M; q.N = p.N; q.K = p.K; q.ldx = p.ldx; q.ldy = p.ldy; q.ldz = p.ldz;
-        q.kblocks = kb; q.nblocks = nb; q.dtype = p.dtype;
-        q.vecx = ((uintptr_t)p.X % 16 == 0) && (p.ldx % (16 / e) == 0);
-        q.vecy = ((uintptr_t)p.Y % 16 == 0) && (p.ldy % (16 / e) == 0);
+        q.kblocks = kb; q.nblocks = nb; q.dtype = p.dtype; q.cfg = cfg;
+        q.vecx = ((uintptr_t)p.X % (8 * e) == 0) && (p.ldx % 8 == 0);
+        q.vecy = ((uintptr_t)p.Y % (8 * e) == 0) && (p.ldy % 8 == 0);
         q.vecz = ((uintptr_t)p.Z % 16 == 0) && (p.ldz % 8 == 0);
         q.xmask = p.K > 0 ? mbase + xoff[i] : nullptr;
         q.ymask = p.K > 0 ? mbase + yoff[i] : nullptr;
-        if (p.M == 0 || p.N == 0) continue;
-        if (p.K > 0) {
+        q.job0 = (int32_t)jobs.size();
+        if (p.M > 0 && p.N > 0 && p.K > 0) {
             for (int64_t bi = 0; bi < mb; ++bi)
                 for (int64_t bk = 0; bk < kb; ++bk)
                     jobs.push_back({p.X, p.M, p.K, p.ldx, bi, bk, kb, mbase + xoff[i], p.dtype, 0});
@@ -460,44 +564,201 @@ int batched_run(const mp_problem *probs, int count, int mode, cudaStream_t s) {
                 for (int64_t bj = 0; bj < nb; ++bj)
                     jobs.push_back({p.Y, p.K, p.N, p.ldy, bk, bj, nb, mbase + yoff[i], p.dtype, 0});
         }
-        for (int64_t bi = 0; bi < mb; ++bi)
-            for (int64_t bj = 0; bj < nb; ++bj) {
-                order.push_back({p.K, tiles.size()});
-                tiles.push_back({i, (int32_t)bi, (int32_t)bj, 0});
-            }
+        q.job1 = (int32_t)jobs.size();
+        q.pad = 0;
+        if (p.M == 0 || p.N == 0) continue;
+        const int bm = cfg == 1 ? 64 : 128;
+        const int64_t tm = (p.M + bm - 1) / bm, tn = (p.N + bm - 1) / bm;
+        for (int64_t bi = 0; bi < tm; ++bi)
+            for (int64_t bj = 0; bj < tn; ++bj)
+                order.push_back({(double)p.K * bm * bm, {i, (int32_t)bi, (int32_t)bj, cfg}});
     }
+    // int16 tiles first, then uint8 (one persistent launch per element
+    // type); within each, the most expensive first
+    auto is8 = [&](const BatchTile &t) { return probs[t.prob].dtype == MP_U8; };
     std::stable_sort(order.begin(), order.end(),
-                     [](const std::pair<int64_t, size_t> &a, const std::pair<int64_t, size_t> &b) {
-                         return a.first > b.first;
+                     [&](const std::pair<double, BatchTile> &x, const std::pair<double, BatchTile> &y) {
+                         if (is8(x.second) != is8(y.second)) return !is8(x.second);
+                         return x.first > y.first;
                      });
-    std::vector<BatchTile> sorted(tiles.size());
-    for (size_t t = 0; t < order.size(); ++t) sorted[t] = tiles[order[t].second];
-    MP_TRY(dprob.alloc(bp.size() * sizeof(BatchProb), s));
-    MP_TRY(dtile.alloc(std::max<size_t>(sorted.size(), 1) * sizeof(BatchTile), s));
-    MP_TRY(djob.alloc(std::max<size_t>(jobs.size(), 1) * sizeof(MaskJob), s));
-    MP_TRY(dcnt.alloc(sizeof(int), s));
-    MP_CUDA_TRY(cudaMemcpyAsync(dprob.p, bp.data(), bp.size() * sizeof(BatchProb),
-                                cudaMemcpyHostToDevice, s));
-    if (!sorted.empty())
-        MP_CUDA_TRY(cudaMemcpyAsync(dtile.p, sorted.data(), sorted.size() * sizeof(BatchTile),
-                                    cudaMemcpyHostToDevice, s));
+    std::vector<BatchTile> tiles(order.size());
+    int n16 = 0;
+    for (size_t t = 0; t < order.size(); ++t) {
+        tiles[t] = order[t].second;
+        if (!is8(tiles[t])) ++n16;
+    }
+    b->ntiles16 = n16;
+    b->ntiles = (int)tiles.size();
+    b->njobs = (int)jobs.size();
+    b->grid = (int)std::min<int64_t>((int64_t)tiles.size(), (int64_t)di.sms * 2);
+    MP_TRY(b->probs.alloc(std::max<size_t>(b->host_probs.size(), 1) * sizeof(BatchProb), nullptr, true));
+    MP_TRY(b->tiles.alloc(std::max<size_t>(tiles.size(), 1) * sizeof(BatchTile), nullptr, true));
+    MP_TRY(b->jobs.alloc(std::max<size_t>(jobs.size(), 1) * sizeof(MaskJob), nullptr, true));
+    MP_TRY(b->counter.alloc(2 * sizeof(int), nullptr, true));
+    if (count)
+        MP_CUDA_TRY(cudaMemcpy(b->probs.p, b->host_probs.data(), b->host_probs.size() * sizeof(BatchProb),
+                               cudaMemcpyHostToDevice));
+    if (!tiles.empty())
+        MP_CUDA_TRY(cudaMemcpy(b->tiles.p, tiles.data(), tiles.size() * sizeof(BatchTile),
+                               cudaMemcpyHostToDevice));
     if (!jobs.empty())
-        MP_CUDA_TRY(cudaMemcpyAsync(djob.p, jobs.data(), jobs.size() * sizeof(MaskJob),
-                                    cudaMemcpyHostToDevice, s));
-    MP_CUDA_TRY(cudaMemsetAsync(dcnt.p, 0, sizeof(int), s));
-    for (size_t j0 = 0; j0 < jobs.size(); j0 += 1u << 30) {
-        const size_t nj = std::min<size_t>(jobs.size() - j0, 1u << 30);
-        batched_mask_kernel<<<(unsigned)nj, 256, 0, s>>>(djob.as<MaskJob>() + j0);
-    }
-    MP_CUDA_TRY(cudaGetLastError());
-    if (!sorted.empty()) {
-        DeviceInfo di;
-        MP_TRY(device_info(&di));
-        const int64_t grid = std::min<int64_t>((int64_t)sorted.size(), (int64_t)di.sms * 3);
-        batched_minplus_kernel<<<(unsigned)grid, THREADS, 0, s>>>(
-            dprob.as<BatchProb>(), dtile.as<BatchTile>(), (int)sorted.size(), dcnt.as<int>());
+        MP_CUDA_TRY(cudaMemcpy(b->jobs.p, jobs.data(), jobs.size() * sizeof(MaskJob),
+                               cudaMemcpyHostToDevice));
+    *out = b.release();
+    return MP_OK;
+}
+
+int batch_run(mp_batch *b, int mode, cudaStream_t s) {
+    if (!b) return set_error(MP_EINVAL, "NULL batch");
+    if (mode != 0 && mode != 1) return set_error(MP_EINVAL, "mode %d", mode);
+    const MaskJob *jobs = b->jobs.as<MaskJob>();
+    if (mode == 0) {
+        for (int j0 = 0; j0 < b->njobs; j0 += 1 << 30) {
+            const int nj = std::min(b->njobs - j0, 1 << 30);
+            batched_mask_kernel<<<(unsigned)nj, 256, 0, s>>>(jobs + j0);
+        }
         MP_CUDA_TRY(cudaGetLastError());
+        if (b->ntiles > 0) {
+            MP_CUDA_TRY(cudaMemsetAsync(b->counter.p, 0, 2 * sizeof(int), s));
+            const int n16 = b->ntiles16, n8 = b->ntiles - b->ntiles16;
+            if (n16 > 0)
+                batched_minplus_kernel<uint16_t><<<(unsigned)std::min(b->grid, n16), THREADS, 0, s>>>(
+                    b->probs.as<BatchProb>(), b->tiles.as<BatchTile>(), n16, b->counter.as<int>());
+            if (n8 > 0)
+                batched_minplus_kernel<uint8_t><<<(unsigned)std::min(b->grid, n8), THREADS, 0, s>>>(
+                    b->probs.as<BatchProb>(), b->tiles.as<BatchTile>() + n16, n8,
+                    b->counter.as<int>() + 1);
+            MP_CUDA_TRY(cudaGetLastError());
+        }
+        return MP_OK;
     }
+    for (int i = 0; i < b->count; ++i) {
+        const BatchProb &p = b->host_probs[i];
+        if (p.M == 0 || p.N == 0) continue;
+        if (p.job1 > p.job0) batched_mask_kernel<<<(unsigned)(p.job1 - p.job0), 256, 0, s>>>(jobs + p.job0);
+        MP_CUDA_TRY(cudaGetLastError());
+        if (p.dtype == MP_I16) {
+            TileArgs<uint16_t> ta = make_args<uint16_t>((const uint16_t *)p.X, (const uint16_t *)p.Y,
+                                                        (uint16_t *)p.Z, p.M, p.N, p.K, p.ldx, p.ldy,
+                                                        p.ldz, p.xmask, p.ymask, nullptr);
+            MP_TRY(launch_product<uint16_t>(ta, p.cfg, s));
+        } else {
+            TileArgs<uint8_t> ta = make_args<uint8_t>((const uint8_t *)p.X, (const uint8_t *)p.Y,
+                                                      (uint8_t *)p.Z, p.M, p.N, p.K, p.ldx, p.ldy,
+                                                      p.ldz, p.xmask, p.ymask, nullptr);
+            MP_TRY(launch_product<uint8_t>(ta, p.cfg, s));
+        }
+    }
+    return MP_OK;
+}
+
+int batch_destroy(mp_batch *b) {
+    delete b;
+    return MP_OK;
+}
+
+int batched_run(const mp_problem *probs, int count, int mode, cudaStream_t s) {
+    if (mode != 0 && mode != 1) return set_error(MP_EINVAL, "mode %d", mode);
+    mp_batch *b = nullptr;
+    MP_TRY(batch_prepare(probs, count, &b));
+    int rc = batch_run(b, mode, s);
+    // the descriptors must outlive the launches
+    cudaError_t e = cudaStreamSynchronize(s);
+    batch_destroy(b);
+    if (rc != MP_OK) return rc;
+    if (e != cudaSuccess) return set_error(MP_ECUDA, "stream sync: %s", cudaGetErrorString(e));
+    return MP_OK;
+}
+
+// ------------------------------------------------------------ autotuner
+namespace {
+
+__global__ void fill_test_kernel(void *A, int64_t n, int dtype, uint32_t seed) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)i * 2654435761u ^ seed;
+        h ^= h >> 13;
+        h *= 0x5bd1e995u;
+        h ^= h >> 15;
+        const uint32_t v = (h & 7) == 0 ? (dtype == MP_I16 ? 0x7FFFu : 0xFFu) : (h >> 8) & 31;
+        if (dtype == MP_I16) ((uint16_t *)A)[i] = (uint16_t)v;
+        else ((uint8_t *)A)[i] = (uint8_t)v;
+    }
+}
+
+}  // namespace
+
+int autotune(int32_t *table_out) {
+    static const int64_t sizes[kClasses] = {96, 192, 384, 768, 1536, 3072};
+    TuneTable t = default_table();
+    const int64_t nmax = sizes[kClasses - 1];
+    DevBuf buf;
+    MP_TRY(buf.alloc((size_t)nmax * nmax * 2 * 3, nullptr, true));
+    cudaEvent_t e0, e1;
+    MP_CUDA_TRY(cudaEventCreate(&e0));
+    MP_CUDA_TRY(cudaEventCreate(&e1));
+    for (int d = 0; d < 2; ++d) {
+        const int dtype = d == 0 ? MP_I16 : MP_U8;
+        const size_t es = d == 0 ? 2 : 1;
+        for (int c = 0; c < kClasses; ++c) {
+            const int64_t n = sizes[c];
+            uint8_t *X = buf.as<uint8_t>(), *Y = X + (size_t)n * n * es, *Z = Y + (size_t)n * n * es;
+            fill_test_kernel<<<256, 256>>>(X, n * n, dtype, 17u + c);
+            fill_test_kernel<<<256, 256>>>(Y, n * n, dtype, 91u + c);
+            float best = 1e30f;
+            for (int cfg = 0; cfg < 2; ++cfg) {
+                float bt = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    MP_CUDA_TRY(cudaEventRecord(e0));
+                    int rc = dtype == MP_I16
+                                 ? run_dense<uint16_t>((uint16_t *)X, (uint16_t *)Y, (uint16_t *)Z, n, n, n,
+                                                       n, n, n, nullptr, cfg, nullptr)
+                                 : run_dense<uint8_t>(X, Y, Z, n, n, n, n, n, n, nullptr, cfg, nullptr);
+                    if (rc != MP_OK) return rc;
+                    MP_CUDA_TRY(cudaEventRecord(e1));
+                    MP_CUDA_TRY(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    MP_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                    bt = std::min(bt, ms);
+                }
+                if (bt < best) {
+                    best = bt;
+                    t.cfg[d][c] = cfg;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int dev = -1;
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[dev] = t;
+    }
+    if (table_out) memcpy(table_out, &t.cfg[0][0], sizeof t.cfg);
+    return MP_OK;
+}
+
+int tuning_set(const int32_t *table) {
+    TuneTable t;
+    for (int d = 0; d < 2; ++d)
+        for (int c = 0; c < kClasses; ++c) {
+            const int32_t v = table[d * kClasses + c];
+            if (v != 0 && v != 1) return set_error(MP_EINVAL, "tile shape %d not 0 or 1", v);
+            t.cfg[d][c] = v;
+        }
+    int dev = -1;
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[dev] = t;
+    return MP_OK;
+}
+
+int tuning_get(int32_t *table) {
+    TuneTable t;
+    MP_TRY(current_table(&t));
+    memcpy(table, &t.cfg[0][0], sizeof t.cfg);
     return MP_OK;
 }
 
@@ -557,11 +818,10 @@ int run_dense_noalloc(const T *X, const T *Y, T *Z, int64_t M, int64_t N, int64_
         xm = xmw;
         ym = ymw;
     }
-    dim3 grid((unsigned)nb, (unsigned)mb);
-    TileArgs<T> ta{X, Y, Z, M, N, K, ldx, ldy, ldz, xm, ym, kb, nb, vecx, vecy, vecz, nullptr};
-    dense_minplus_kernel<T><<<grid, THREADS, 0, s>>>(ta);
-    MP_CUDA_TRY(cudaGetLastError());
-    return MP_OK;
+    (void)vecx;
+    (void)vecy;
+    (void)vecz;
+    return launch_product<T>(make_args<T>(X, Y, Z, M, N, K, ldx, ldy, ldz, xm, ym, nullptr), 0, s);
 }
 
 }  // namespace

@@ -20,7 +20,7 @@ def block_inf_matrix(rows: int, cols: int, seed: int, dtype=np.int16, inf_frac: 
     the edges) is set entirely to INF with probability inf_frac."""
     rng = np.random.Generator(np.random.PCG64(seed))
     inf = INF16 if np.dtype(dtype) == np.int16 else INF8
-    X = rng.integers(lo, hi + 1, size=(rows, cols)).astype(dtype)
+    X = rng.integers(lo, hi + 1, size=(rows, cols), dtype=dtype)
     br, bc = math.ceil(rows / block), math.ceil(cols / block)
     mask = rng.random((br, bc)) < inf_frac
     for i, j in zip(*np.nonzero(mask)):
@@ -33,7 +33,7 @@ def entry_inf_matrix(rows: int, cols: int, seed: int, dtype=np.int16, inf_frac: 
     """Entries uniform in [lo, hi], each INF independently with prob inf_frac."""
     rng = np.random.Generator(np.random.PCG64(seed))
     inf = INF16 if np.dtype(dtype) == np.int16 else INF8
-    X = rng.integers(lo, hi + 1, size=(rows, cols)).astype(dtype)
+    X = rng.integers(lo, hi + 1, size=(rows, cols), dtype=dtype)
     X[rng.random((rows, cols)) < inf_frac] = inf
     return X
 

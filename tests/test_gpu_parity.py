@@ -299,6 +299,64 @@ def test_batched_alias_rejected(mp, torch):
     assert e.value.code == -2
 
 
+@pytest.mark.parametrize("shape_cfg", [0, 1])
+@pytest.mark.parametrize("dtype", [np.int16, np.uint8])
+def test_each_tile_shape(mp, torch, shape_cfg, dtype):
+    """Both tile shapes (128x128 and 64x64) on ragged sizes, forced for every
+    size class through the tuning table."""
+    saved = mp.mp_tuning_get()
+    try:
+        mp.mp_tuning_set(np.full((2, 6), shape_cfg, dtype=np.int32))
+        for M, K, N in [(1, 1, 1), (63, 65, 64), (130, 257, 129), (300, 200, 517)]:
+            X = synth.block_inf_matrix(M, K, M + K, dtype, inf_frac=0.3, block=64)
+            Y = synth.entry_inf_matrix(K, N, N + K, dtype, inf_frac=0.2)
+            Z = mp.mp_minplus_mul(to_dev(torch, X), to_dev(torch, Y))
+            torch.cuda.synchronize()
+            assert np.array_equal(host(Z), oracle.minplus_mul(X, Y, threads=THREADS)), (M, K, N)
+    finally:
+        mp.mp_tuning_set(saved)
+
+
+def test_batch_graph_replay(mp, torch):
+    """A prepared batch captured in a CUDA graph: every replay, in both modes,
+    gives the oracle's products; operands changed between replays are seen."""
+    sizes = [64, 100, 129, 200, 517, 1000, 70]
+    Xs, Ys, Zs, probs = [], [], [], []
+    for i, N in enumerate(sizes):
+        X = synth.block_inf_matrix(N, N, 300 + i, np.int16, inf_frac=0.3)
+        Y = synth.block_inf_matrix(N, N, 400 + i, np.int16, inf_frac=0.3)
+        Xs.append(to_dev(torch, X)); Ys.append(to_dev(torch, Y)); Zs.append(torch.empty_like(Xs[-1]))
+        probs.append((Xs[-1], Ys[-1], Zs[-1]))
+    b = mp.Batch(probs)
+    for mode in (0, 1):
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            b.run(mode)  # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b.run(mode, stream=s)
+        for rep in range(2):
+            for i, N in enumerate(sizes):  # new operand values, same buffers
+                Xs[i].copy_(to_dev(torch, synth.block_inf_matrix(N, N, 500 + 10 * rep + i, np.int16, inf_frac=0.3)))
+                Zs[i].fill_(1)
+            g.replay()
+            torch.cuda.synchronize()
+            for i in range(len(sizes)):
+                assert np.array_equal(host(Zs[i]), oracle.minplus_mul(host(Xs[i]), host(Ys[i]), threads=THREADS))
+    b.close()
+
+
+def test_autotune_installs_a_valid_table(mp):
+    saved = mp.mp_tuning_get()
+    try:
+        t = mp.mp_autotune()
+        assert t.shape == (2, 6) and set(np.unique(t)) <= {0, 1}
+        assert np.array_equal(mp.mp_tuning_get(), t)
+    finally:
+        mp.mp_tuning_set(saved)
+
+
 # --------------------------------------------------------------- misc
 
 def test_dpx_peak_positive(mp):
