@@ -144,13 +144,34 @@ int mp_transfer_power_sequence(int n, int k_max, int16_t *powers_opt,
 
 /* ---- a6: gamma_2 of one cylinder --------------------------------------------
  * Theorem 2: gamma_2(P_n x C_m) = min_i (A^m)_ii, for n >= 1 and m >= 3.
- * Synchronous; *out is a HOST int64.  Uses the cached transfer plan and
- * either the chain or repeated squaring S_j = S_{j-1} (x) S_{j-1} followed
- * by a min-trace of the last two factors.  Errors: MP_EINVAL (n out of
- * range, m < 3), MP_ERANGE (m * n >= 32767: exact values could reach the
- * int16 INF code), MP_ENOMEM, MP_ECUDA.
+ * Synchronous; *out is a HOST int64.  When the recurrence of n is known
+ * (mp_transfer_recurrence, run automatically for n <= 11 and m > 64) the
+ * answer comes from Theorem 3 for any m.  Otherwise it uses the cached
+ * transfer plan and either the chain or repeated squaring
+ * S_j = S_{j-1} (x) S_{j-1} followed by a min-trace of the last two factors.
+ * Errors: MP_EINVAL (n out of range, m < 3), MP_ERANGE (no recurrence and
+ * m * n >= 32767: exact values could reach the int16 INF code),
+ * MP_ENOMEM, MP_ECUDA.
  */
 int mp_gamma2_cylinder(int n, int64_t m, int64_t *out);
+
+/* ---- NEXT f1: the recurrence of Theorem 3 ---------------------------------
+ * mp_diff_const (K4): for two DEVICE int16 arrays of count entries, writes to
+ * DEVICE int32 out[4]: out[0] = min and out[1] = max of X - Y over the
+ * entries finite in both, out[2] = 1 if some entry is INF in exactly one of
+ * them (else 0), out[3] = 1 if some entry is finite in both.  X - Y is a
+ * constant matrix (Algorithm 3's test, with equal INF patterns) exactly when
+ * out[2] == 0, out[3] == 1 and out[0] == out[1].  Asynchronous.
+ *
+ * mp_transfer_recurrence: Algorithm 3 over K stored powers of A(D_n), then
+ * Algorithm 4 (Section 3): out (HOST int32[4]) = {r0, a, b, n0}; a = 0 when
+ * no constant difference exists among the K powers.  With K = 50 this is
+ * Table 3's (r0, a, b) and Table 4's n0.  Synchronous; needs K*N^2*2 bytes
+ * of device memory (MP_ENOMEM otherwise).  A found recurrence is cached per
+ * device and used by mp_gamma2_cylinder (Theorem 3), which then answers any
+ * m >= 3 without the int16 range limit. */
+int mp_diff_const(const int16_t *X, const int16_t *Y, int64_t count, int32_t *out, void *stream);
+int mp_transfer_recurrence(int n, int K, int32_t *out);
 
 /* The gamma_2 table of one path order: out[m] = gamma_2(P_n x C_m) for
  * m = 3..k_max (Theorem 2 / Algorithm 5 over the chain), out[0..2] = -1.

@@ -62,6 +62,8 @@ def lib() -> ctypes.CDLL:
         "mp_gamma2_cylinder": (I, [I, I64, P]),
         "mp_gamma2_table": (I, [I, I, P]),
         "mp_diag_min": (I, [P, I64, I64, P, P]),
+        "mp_diff_const": (I, [P, P, I64, P, P]),
+        "mp_transfer_recurrence": (I, [I, I, P]),
         "mp_min_trace": (I, [P, P, I64, I64, I64, P, P]),
         "mp_minplus_mul_batched": (I, [P, I, I, P]),
         "mp_batch_prepare": (I, [P, I, P]),
@@ -283,6 +285,21 @@ def mp_gamma2_table(n: int, k_max: int) -> np.ndarray:
 
 
 # -------------------------------------------------------------- reductions
+
+def mp_diff_const(X, Y, stream=None):
+    """(min, max, inf_mismatch, any_finite) of X - Y over both-finite entries."""
+    import torch
+    out = torch.empty(4, dtype=torch.int32, device=X.device)
+    _check(lib().mp_diff_const(_dev(X), _dev(Y), X.numel(), _dev(out), _stream(stream)))
+    return out
+
+
+def mp_transfer_recurrence(n: int, K: int = 50):
+    """Algorithms 3 and 4 on the device: (r0, a, b, n0) for A(D_n) over K powers."""
+    out = np.zeros(4, dtype=np.int32)
+    _check(lib().mp_transfer_recurrence(int(n), int(K), out.ctypes.data))
+    return tuple(int(v) for v in out)
+
 
 def mp_diag_min(P, stream=None):
     import torch

@@ -193,6 +193,75 @@ static int run_dense_chain(const int16_t *A, int64_t N, int k_max, int16_t *powe
     return MP_OK;
 }
 
+// ------------------------------------------------ recurrence (Algorithms 3, 4)
+struct Recurrence {
+    int K = 0, r0 = 0, a = 0, b = 0, n0 = 0;
+    std::vector<int32_t> gdiag;  // min diag A^k, k = 1..K
+};
+static std::map<std::pair<int, int>, Recurrence> g_rec;
+
+static int diff_constant(const int16_t *X, const int16_t *Y, int64_t count, int32_t *d_out,
+                         cudaStream_t s, bool *is_const, int32_t *b) {
+    MP_TRY(launch_diff_const(X, Y, count, d_out, s));
+    int32_t h[4];
+    MP_CUDA_TRY(cudaMemcpyAsync(h, d_out, sizeof h, cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    *is_const = h[2] == 0 && h[3] == 1 && h[0] == h[1];
+    *b = h[0];
+    return MP_OK;
+}
+
+// Algorithm 3 over K stored powers of A(D_n), then Algorithm 4.
+static int transfer_recurrence(int n, int K, Recurrence *out, cudaStream_t s) {
+    TransferEntry *te;
+    MP_TRY(transfer_entry(n, s, &te));
+    const int64_t N = te->N;
+    const size_t mat = (size_t)N * (size_t)N;
+    size_t free_b = 0, total_b = 0;
+    MP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    if ((double)mat * 2.0 * (K + 3) > 0.9 * (double)free_b)
+        return set_error(MP_ENOMEM, "%d powers of N = %lld do not fit the free device memory", K,
+                         (long long)N);
+    DevBuf P, g, d;
+    MP_TRY(P.alloc(mat * 2 * (size_t)K, s));
+    MP_TRY(g.alloc(sizeof(int32_t) * (size_t)K, s));
+    MP_TRY(d.alloc(sizeof(int32_t) * 4, s));
+    MP_TRY(mp_transfer_power_sequence(n, K, P.as<int16_t>(), g.as<int32_t>(), s));
+    Recurrence r;
+    r.K = K;
+    r.gdiag.resize((size_t)K);
+    MP_CUDA_TRY(cudaMemcpyAsync(r.gdiag.data(), g.p, sizeof(int32_t) * (size_t)K,
+                                cudaMemcpyDeviceToHost, s));
+    auto pw = [&](int k) { return P.as<int16_t>() + (size_t)(k - 1) * mat; };
+    bool found = false;
+    for (int i = K; i >= 1 && !found; --i)
+        for (int j = i - 1; j >= 1; --j) {
+            bool c;
+            int32_t b;
+            MP_TRY(diff_constant(pw(i), pw(j), (int64_t)mat, d.as<int32_t>(), s, &c, &b));
+            if (c) {
+                r.a = i - j;
+                r.b = b;
+                r.r0 = j;
+                found = true;
+                break;
+            }
+        }
+    if (found) {
+        r.n0 = -1;
+        for (int i = r.r0 + r.a; i >= r.a + 1; --i) {
+            bool c;
+            int32_t b;
+            MP_TRY(diff_constant(pw(i), pw(i - r.a), (int64_t)mat, d.as<int32_t>(), s, &c, &b));
+            if (!c || b != r.b) break;
+            r.n0 = i - r.a;
+        }
+    }
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = r;
+    return MP_OK;
+}
+
 static int check_n(int n) {
     if (n < 1 || n > MP_MAX_PATH_ORDER)
         return set_error(MP_EINVAL, "path order n = %d outside [1, %d]", n, MP_MAX_PATH_ORDER);
@@ -373,6 +442,33 @@ int mp_gamma2_table(int n, int k_max, int64_t *out) {
     return MP_OK;
 }
 
+int mp_diff_const(const int16_t *X, const int16_t *Y, int64_t count, int32_t *out, void *stream) {
+    if (!X || !Y || !out || count < 0) return set_error(MP_EINVAL, "bad diff_const arguments");
+    return launch_diff_const(X, Y, count, out, (cudaStream_t)stream);
+}
+
+int mp_transfer_recurrence(int n, int K, int32_t *out) {
+    MP_TRY(check_n(n));
+    if (K < 2 || !out) return set_error(MP_EINVAL, "need K >= 2 and an output array");
+    if ((int64_t)K * n >= (int64_t)kInf16)
+        return set_error(MP_ERANGE, "K * n reaches the int16 INF code");
+    DeviceState *st;
+    MP_TRY(device_state(&st));
+    Recurrence r;
+    MP_TRY(transfer_recurrence(n, K, &r, st->sync_stream));
+    if (r.a > 0 && r.n0 >= 1) {
+        int dev = -1;
+        MP_CUDA_TRY(cudaGetDevice(&dev));
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_rec[{dev, n}] = r;
+    }
+    out[0] = r.r0;
+    out[1] = r.a;
+    out[2] = r.b;
+    out[3] = r.n0;
+    return MP_OK;
+}
+
 int mp_diag_min(const int16_t *P, int64_t N, int64_t ld, int32_t *out, void *stream) {
     if (!P || !out || N < 0 || ld < N) return set_error(MP_EINVAL, "bad diag_min arguments");
     return launch_diag_min(P, N, ld, out, true, (cudaStream_t)stream);
@@ -389,12 +485,48 @@ int mp_gamma2_cylinder(int n, int64_t m, int64_t *out) {
     MP_TRY(check_n(n));
     if (m < 3) return set_error(MP_EINVAL, "cycle length m = %lld < 3", (long long)m);
     if (!out) return set_error(MP_EINVAL, "out is NULL");
-    if (m * (int64_t)n >= (int64_t)kInf16)
-        return set_error(MP_ERANGE, "m * n = %lld reaches the int16 INF code",
-                         (long long)(m * n));
     DeviceState *st;
     MP_TRY(device_state(&st));
     cudaStream_t s = st->sync_stream;
+    // Theorem 3: with A^{n0+a} = b + A^{n0}, gamma_2(m + a) = gamma_2(m) + b for
+    // m >= n0, so every m past the stored powers reduces to one of them.
+    {
+        int dev = -1;
+        MP_CUDA_TRY(cudaGetDevice(&dev));
+        Recurrence r;
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            auto it = g_rec.find({dev, n});
+            if (it != g_rec.end()) {
+                r = it->second;
+                have = true;
+            }
+        }
+        if (!have && m > 64 && n <= 11) {
+            int32_t tmp[4];
+            if (mp_transfer_recurrence(n, 50, tmp) == MP_OK) {
+                std::lock_guard<std::mutex> lk(g_mu);
+                auto it = g_rec.find({dev, n});
+                if (it != g_rec.end()) {
+                    r = it->second;
+                    have = true;
+                }
+            }
+        }
+        if (have) {
+            if (m <= r.K) {
+                *out = r.gdiag[(size_t)m - 1];
+                return MP_OK;
+            }
+            const int64_t t = (m - r.n0) / r.a;  // m - t*a in [n0, n0 + a)
+            *out = (int64_t)r.gdiag[(size_t)(m - t * r.a) - 1] + t * (int64_t)r.b;
+            return MP_OK;
+        }
+    }
+    if (m * (int64_t)n >= (int64_t)kInf16)
+        return set_error(MP_ERANGE, "m * n = %lld reaches the int16 INF code",
+                         (long long)(m * n));
     TransferEntry *te;
     MP_TRY(transfer_entry(n, s, &te));
     const int64_t N = te->N;

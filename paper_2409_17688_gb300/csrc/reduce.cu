@@ -6,6 +6,8 @@
 // repeated-squaring path uses for the last two factors of A^m.  Both reduce
 // in registers, then across the warp with shuffles, then one atomicMin per
 // warp into a 32-bit result that starts at INF.
+#include <algorithm>
+
 #include "mp_internal.cuh"
 
 namespace mp {
@@ -59,6 +61,68 @@ __global__ void min_trace_kernel(const int16_t *__restrict__ X, const int16_t *_
 
 __global__ void set_one_kernel(int32_t *out, int32_t v) { *out = v; }
 
+// K4: is X - Y a constant matrix (Algorithms 3 and 4)?  out[0] = min and
+// out[1] = max of X - Y over entries finite in both, out[2] = 1 when some
+// entry is INF in exactly one of them, out[3] = 1 when some entry is finite
+// in both.  The difference is constant exactly when out[2] = 0, out[3] = 1
+// and out[0] = out[1].
+__global__ void diff_init_kernel(int32_t *out) {
+    out[0] = 0x7FFFFFFF;
+    out[1] = (int32_t)0x80000000;
+    out[2] = 0;
+    out[3] = 0;
+}
+
+__global__ void diff_const_kernel(const int16_t *__restrict__ X, const int16_t *__restrict__ Y,
+                                  int64_t count, int32_t *out) {
+    int32_t lo = 0x7FFFFFFF, hi = (int32_t)0x80000000, mism = 0, fin = 0;
+    const int64_t n2 = count / 2;
+    const uint32_t *x2 = reinterpret_cast<const uint32_t *>(X);
+    const uint32_t *y2 = reinterpret_cast<const uint32_t *>(Y);
+    const bool vec = ((uintptr_t)X % 4 == 0) && ((uintptr_t)Y % 4 == 0);
+    auto one = [&](uint32_t a, uint32_t b) {
+        const bool fa = a < kInf16, fb = b < kInf16;
+        if (fa != fb) mism = 1;
+        if (fa && fb) {
+            const int32_t d = (int32_t)a - (int32_t)b;
+            lo = min(lo, d);
+            hi = max(hi, d);
+            fin = 1;
+        }
+    };
+    if (vec) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const uint32_t a = x2[i], b = y2[i];
+            one(a & 0xFFFFu, b & 0xFFFFu);
+            one(a >> 16, b >> 16);
+        }
+        if (count & 1) {
+            if (blockIdx.x == 0 && threadIdx.x == 0)
+                one((uint16_t)X[count - 1], (uint16_t)Y[count - 1]);
+        }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+             i += (int64_t)gridDim.x * blockDim.x)
+            one((uint16_t)X[i], (uint16_t)Y[i]);
+    }
+    lo = warp_min(lo);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+        mism |= __shfl_xor_sync(0xFFFFFFFFu, mism, o);
+        fin |= __shfl_xor_sync(0xFFFFFFFFu, fin, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (fin) {
+            atomicMin(&out[0], lo);
+            atomicMax(&out[1], hi);
+            atomicOr(&out[3], 1);
+        }
+        if (mism) atomicOr(&out[2], 1);
+    }
+}
+
 }  // namespace
 
 int launch_fill_i32(int32_t *p, int64_t count, int32_t v, cudaStream_t s) {
@@ -80,6 +144,20 @@ int launch_diag_min(const int16_t *P, int64_t N, int64_t ld, int32_t *out, bool 
     int64_t blocks = (N + 255) / 256;
     if (blocks > 256) blocks = 256;
     diag_min_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, N, ld, out);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+int launch_diff_const(const int16_t *X, const int16_t *Y, int64_t count, int32_t *out,
+                      cudaStream_t s) {
+    diff_init_kernel<<<1, 1, 0, s>>>(out);
+    MP_CUDA_TRY(cudaGetLastError());
+    if (count <= 0) return MP_OK;
+    DeviceInfo di;
+    MP_TRY(device_info(&di));
+    int64_t blocks = (count / 2 + 255) / 256;
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)di.sms * 8));
+    diff_const_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, Y, count, out);
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

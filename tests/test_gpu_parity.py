@@ -267,8 +267,65 @@ def test_gamma2_cylinder_errors(mp):
         mp.mp_gamma2_cylinder(3, 2)
     assert e.value.code == -1
     with pytest.raises(mp.MinplusError) as e:
-        mp.mp_gamma2_cylinder(10, 4000)
+        mp.mp_gamma2_cylinder(0, 10)
+    assert e.value.code == -1
+    # a table past the int16 range is refused rather than saturated
+    with pytest.raises(mp.MinplusError) as e:
+        mp.mp_gamma2_table(10, 4000)
     assert e.value.code == -4
+
+
+# ------------------------------------------------- NEXT f1: recurrence
+
+def test_diff_const_kernel(mp, torch):
+    rng = np.random.default_rng(21)
+    for N in (1, 7, 130, 513):
+        X = synth.entry_inf_matrix(N, N, N, np.int16, inf_frac=0.2)
+        cases = [np.where(X < INF, X + 5, INF).astype(np.int16),           # constant shift
+                 np.where(X < INF, X + rng.integers(0, 2, X.shape), INF).astype(np.int16),
+                 np.full_like(X, INF), X.copy()]
+        cases[3].flat[0] = INF if cases[3].flat[0] != INF else 3          # INF pattern differs
+        for Y in cases:
+            d = host(mp.mp_diff_const(to_dev(torch, Y), to_dev(torch, X)))
+            ok, b = oracle.diff_is_constant(Y, X)
+            got = bool(d[2] == 0 and d[3] == 1 and d[0] == d[1])
+            assert got == ok, N
+            if ok:
+                assert d[0] == b
+
+
+T3 = {2: (48, 2, 2), 3: (44, 6, 8), 4: (42, 8, 14), 5: (43, 7, 15), 6: (39, 11, 28),
+      7: (32, 18, 53), 8: (47, 3, 10), 9: (47, 3, 11), 10: (47, 3, 12), 11: (47, 3, 13)}
+T4_N0 = {2: 4, 3: 7, 4: 9, 5: 31, 6: 19, 7: 23, 8: 25, 9: 22, 10: 21, 11: 24}
+
+
+@pytest.mark.parametrize("n", list(range(2, 12)))
+def test_recurrence_tables_3_4(mp, torch, n):
+    """Algorithms 3 and 4 on the device over K = 50 powers reproduce the
+    paper's Table 3 (r0, a, b) and Table 4 (n0), n = 2..11 (n = 10, 11 are
+    pinned by the paper's printed values alone)."""
+    N = mp.mp_transfer_size(n)
+    free, _ = torch.cuda.mem_get_info()
+    if 50 * N * N * 2 * 1.2 > free:
+        pytest.skip("not enough device memory for 50 powers")
+    r0, a, b, n0 = mp.mp_transfer_recurrence(n, 50)
+    assert (r0, a, b) == T3[n]
+    assert n0 == T4_N0[n]
+
+
+def test_gamma2_any_m_by_recurrence(mp):
+    """Theorem 3 answers every m, past the int16 range too: the closed form
+    of Section 4 with Table 5's alpha, m from n0 to 10^5."""
+    import math
+    alpha_ones = {2: (2, set()), 3: (6, set()), 4: (8, {4, 5}), 5: (7, set()), 6: (11, {5, 9}),
+                  7: (18, {1, 2, 4, 5}), 8: (3, set()), 9: (3, set()), 10: (3, {1, 2}),
+                  11: (3, {2})}
+    for n in range(2, 12):
+        a, ones = alpha_ones[n]
+        b = T3[n][2]
+        for m in [T4_N0[n], T4_N0[n] + 1, 97, 1000, 4001, 33333, 100000]:
+            want = math.ceil(b * m / a) + (1 if (m % a) in ones else 0)
+            assert mp.mp_gamma2_cylinder(n, m) == want, (n, m)
 
 
 # ------------------------------------------------------------------ a7
