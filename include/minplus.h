@@ -239,6 +239,47 @@ int mp_autotune(int32_t *table_out);
 int mp_tuning_set(const int32_t *table);
 int mp_tuning_get(int32_t *table);
 
+/* ---- serving: continuous batching of gamma_2 queries ---------------------
+ * A server answers gamma_2(P_n x C_m) (Theorem 2) for a stream of queries.
+ * For each path order it serves it keeps powers of A(D_n) resident on the
+ * current device: A^1..A^B and A^{tB} for t = 2..T, with B = ceil(sqrt(max_m))
+ * and T = ceil(max_m / B), so every m <= max_m is one min-trace of two
+ * resident powers.  A worker thread batches the queries whose path order is
+ * resident into one launch (two batches may be in flight); a query for a
+ * path order that is not resident admits it: its footprint
+ * (B + T - 1) * N^2 * 2 bytes is checked against hbm_budget, idle path
+ * orders are evicted least recently used first, and a builder thread
+ * computes the powers on its own stream while other batches run.
+ *
+ * mp_server_create: hbm_budget in bytes, max_batch queries per launch,
+ *   max_m the largest cycle length served, max_tickets the capacity of the
+ *   ticket table (the server's lifetime query count).  The server lives on
+ *   the current device.
+ * mp_server_submit: enqueues (n, m) and returns a ticket; never blocks.
+ *   MP_EINVAL for n outside [1, 16] or m outside [3, max_m], MP_ERANGE for
+ *   m * n >= 32767, MP_EBUSY when the ticket table is full.
+ * mp_server_poll: MP_OK with *gamma2 set (HOST int64) once answered,
+ *   MP_ENOTREADY before, MP_ENOMEM if the path order can never fit the
+ *   budget, MP_EINVAL if the ticket was cancelled or is unknown.
+ * mp_server_cancel: withdraws a query not yet answered (MP_EBUSY if it
+ *   already was).
+ * mp_server_latency: submit and completion times (seconds on a monotonic
+ *   clock) of an answered ticket, MP_ENOTREADY before.
+ * mp_server_stats: out (HOST int64[8]) = submitted, completed, failed,
+ *   cancelled, batches launched, path orders built, evictions, resident bytes.
+ * mp_server_destroy: finishes in-flight work, frees everything.
+ * Thread safety: submit, poll, cancel, latency and stats may be called from
+ * any host thread; create and destroy from one. */
+typedef struct mp_server mp_server;
+int mp_server_create(size_t hbm_budget, int max_batch, int64_t max_m, int64_t max_tickets,
+                     mp_server **out);
+int mp_server_submit(mp_server *server, int n, int64_t m, uint64_t *ticket);
+int mp_server_poll(mp_server *server, uint64_t ticket, int64_t *gamma2);
+int mp_server_cancel(mp_server *server, uint64_t ticket);
+int mp_server_latency(mp_server *server, uint64_t ticket, double *submit_s, double *done_s);
+int mp_server_stats(mp_server *server, int64_t *out);
+int mp_server_destroy(mp_server *server);
+
 /* ---- K6: DPX add-min peak ------------------------------------------------
  * Runs independent __viaddmin_u16x2 chains on every SM for `iters`
  * iterations and writes the achieved add-min rate (two per instruction) in

@@ -72,6 +72,13 @@ def lib() -> ctypes.CDLL:
         "mp_autotune": (I, [P]),
         "mp_tuning_set": (I, [P]),
         "mp_tuning_get": (I, [P]),
+        "mp_server_create": (I, [ctypes.c_size_t, I, I64, I64, P]),
+        "mp_server_submit": (I, [P, I, I64, P]),
+        "mp_server_poll": (I, [P, ctypes.c_uint64, P]),
+        "mp_server_cancel": (I, [P, ctypes.c_uint64]),
+        "mp_server_latency": (I, [P, ctypes.c_uint64, P, P]),
+        "mp_server_stats": (I, [P, P]),
+        "mp_server_destroy": (I, [P]),
         "mp_dpx_peak": (I, [I, I64, P]),
         "mp_device_status": (I, []),
         "mp_last_error": (ctypes.c_char_p, []),
@@ -314,6 +321,73 @@ def mp_min_trace(X, Y, stream=None):
     _check(lib().mp_min_trace(_dev(X), _dev(Y), X.shape[0], X.stride(0), Y.stride(0), _dev(out),
                               _stream(stream)))
     return out
+
+
+# ----------------------------------------------------------------- serving
+
+class Server:
+    """A gamma_2(n, m) server (mp_server_*): submit() returns tickets, poll()
+    returns the value or None while pending."""
+
+    def __init__(self, hbm_budget: int, max_batch: int = 256, max_m: int = 2000,
+                 max_tickets: int = 1 << 16):
+        h = ctypes.c_void_p()
+        _check(lib().mp_server_create(int(hbm_budget), int(max_batch), int(max_m),
+                                      int(max_tickets), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, n: int, m: int) -> int:
+        t = ctypes.c_uint64(0)
+        _check(lib().mp_server_submit(self._h, int(n), int(m), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        v = ctypes.c_int64(0)
+        rc = lib().mp_server_poll(self._h, int(ticket), ctypes.byref(v))
+        if rc == -8:
+            return None
+        _check(rc)
+        return int(v.value)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        import time
+        t0 = time.perf_counter()
+        while True:
+            v = self.poll(ticket)
+            if v is not None:
+                return v
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError(f"ticket {ticket} not answered in {timeout_s} s")
+            time.sleep(0.0002)
+
+    def cancel(self, ticket: int) -> None:
+        _check(lib().mp_server_cancel(self._h, int(ticket)))
+
+    def latency(self, ticket: int):
+        a, b = ctypes.c_double(0), ctypes.c_double(0)
+        rc = lib().mp_server_latency(self._h, int(ticket), ctypes.byref(a), ctypes.byref(b))
+        if rc == -8:
+            return None
+        _check(rc)
+        return float(a.value), float(b.value)
+
+    def stats(self) -> dict:
+        out = np.zeros(8, dtype=np.int64)
+        _check(lib().mp_server_stats(self._h, out.ctypes.data))
+        keys = ["submitted", "completed", "failed", "cancelled", "batches", "builds",
+                "evictions", "resident_bytes"]
+        return dict(zip(keys, (int(v) for v in out)))
+
+    def close(self):
+        if self._h:
+            lib().mp_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------------- misc

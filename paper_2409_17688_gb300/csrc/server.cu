@@ -1,0 +1,556 @@
+// Serving: a continuous-batching gamma_2(P_n x C_m) server (Theorem 2).
+//
+// For every path order it serves, the server keeps powers of A(D_n)
+// resident on the device: the "baby steps" A^1..A^B (from the sparse chain)
+// and the "giant steps" A^{tB}, t = 2..T (dense products A^{(t-1)B} (x) A^B).
+// Any m in [2, B(T+1)] splits as m = x + y with both powers resident, and
+// gamma_2 = min_i (A^x (x) A^y)_ii = min_{i,l} A^x_il + A^y_li is one
+// O(N^2) min-trace, so a query costs one pass over two resident matrices.
+//
+// Requests enter a queue (mp_server_submit, any host thread).  A worker
+// thread drains it continuously: queries whose n is resident join the next
+// batch, which runs as one launch of the batched min-trace kernel on the
+// compute stream (at most two batches in flight, so a new batch is formed
+// while the previous one runs).  A query for a path order that is not
+// resident triggers its admission: the footprint (B + T - 1) N^2 int16 is
+// checked against the device-memory budget, least recently used path orders
+// with no queries in flight are evicted until it fits, and a builder thread
+// computes the powers on its own stream, so building overlaps the batches
+// of other path orders.  Queries that arrive meanwhile wait for it.
+// Footprints larger than the whole budget are refused with MP_ENOMEM; a full
+// ticket table is refused with MP_EBUSY.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "mp_internal.cuh"
+
+extern "C" int mp_transfer_power_sequence(int n, int k_max, int16_t *powers_opt,
+                                          int32_t *gdiag_opt, void *stream);
+
+namespace mp {
+
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct TraceJob {
+    const int16_t *X;
+    const int16_t *Y;
+    int64_t N;
+    int64_t tile0;  // first global tile index of this job
+    int64_t side;   // tiles per side (ceil(N / 32))
+};
+
+// One 32 x 32 block (I, L) of min_{i,l} X_il + Y_li per CTA step, over all
+// jobs of a batch (a persistent grid walks the global tile index).
+__global__ void batched_trace_kernel(const TraceJob *__restrict__ jobs, int njobs,
+                                     int64_t total, int32_t *__restrict__ out) {
+    __shared__ int32_t ys[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {  // last job with tile0 <= t
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].tile0 <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const TraceJob j = jobs[lo];
+        const int64_t loc = t - j.tile0;
+        const int64_t i0 = (loc / j.side) * 32, l0 = (loc % j.side) * 32;
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t l = l0 + r, i = i0 + tx;
+            ys[r][tx] = (l < j.N && i < j.N) ? (int32_t)(uint16_t)j.Y[l * j.N + i] : (int32_t)kInf16;
+        }
+        __syncthreads();
+        int32_t v = 2 * (int32_t)kInf16;
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t i = i0 + r, l = l0 + tx;
+            const int32_t x = (i < j.N && l < j.N) ? (int32_t)(uint16_t)j.X[i * j.N + l] : (int32_t)kInf16;
+            v = min(v, x + ys[tx][r]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+        v = min(v, (int32_t)kInf16);
+        if (tx == 0 && v < (int32_t)kInf16) atomicMin(&out[lo], v);
+        __syncthreads();
+    }
+}
+
+__global__ void fill_inf_kernel(int32_t *p, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        p[i] = (int32_t)kInf16;
+}
+
+enum SlotState : int { kFree = 0, kQueued = 1, kDone = 2, kFailed = 3, kCancelled = 4 };
+
+struct Slot {
+    std::atomic<int> state{kFree};
+    int64_t value = 0;
+    int err = 0;
+    int n = 0;
+    int64_t m = 0;
+    double t_submit = 0, t_done = 0;
+};
+
+struct Query {
+    uint64_t ticket;
+    int n;
+    int64_t m;
+};
+
+enum NStatus { kAbsent = 0, kBuilding = 1, kResident = 2 };
+
+struct PathState {
+    int n = 0;
+    int64_t N = 0;
+    int status = kAbsent;
+    size_t bytes = 0;
+    int16_t *powers = nullptr;  // [B + T - 1][N][N]: A^1..A^B, then A^{2B}..A^{TB}
+    std::atomic<int> built{0};  // set by the builder thread (1 ok, -1 failed)
+    int build_err = 0;
+    std::thread builder;
+    uint64_t last_use = 0;
+    int inflight = 0;
+    std::deque<Query> waiting;
+};
+
+struct Batch {
+    std::vector<Query> qs;
+    std::vector<std::pair<int, int>> uses;  // path orders touched (n, count)
+    int32_t *d_out = nullptr;
+    int32_t *h_out = nullptr;
+    TraceJob *d_jobs = nullptr;
+    TraceJob *h_jobs = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+};
+
+}  // namespace
+
+}  // namespace mp
+
+struct mp_server {
+    // configuration
+    int device = 0;
+    size_t budget = 0;
+    int max_batch = 0;
+    int64_t max_m = 0;
+    int B = 0, T = 0;
+    int sms = 0;
+    // tickets
+    std::vector<mp::Slot> slots;
+    std::atomic<uint64_t> next_ticket{0};
+    // queue
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<mp::Query> queue;
+    bool stop = false;
+    // worker state
+    std::thread worker;
+    cudaStream_t compute = nullptr;
+    std::map<int, std::unique_ptr<mp::PathState>> paths;
+    size_t used = 0;
+    uint64_t clock = 0;
+    mp::Batch batches[2];
+    std::deque<mp::Query> deferred;
+    // statistics
+    std::atomic<uint64_t> stat_completed{0}, stat_failed{0}, stat_batches{0}, stat_builds{0},
+        stat_evictions{0}, stat_cancelled{0};
+    std::atomic<uint64_t> stat_resident_bytes{0};
+};
+
+namespace mp {
+
+namespace {
+
+size_t footprint(const mp_server *sv, int64_t N) {
+    return (size_t)(sv->B + sv->T - 1) * (size_t)N * (size_t)N * 2;
+}
+
+int64_t words_count(int n) {
+    std::vector<uint32_t> w;
+    enumerate_words(n, &w);
+    return (int64_t)w.size();
+}
+
+// Builder thread body: baby steps by the sparse chain, giant steps by
+// dense products, all on a private stream.
+void build_path(mp_server *sv, PathState *ps) {
+    cudaSetDevice(sv->device);
+    cudaStream_t s = nullptr;
+    int rc = MP_OK;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = MP_ECUDA;
+    const int64_t N = ps->N;
+    const size_t mat = (size_t)N * (size_t)N;
+    if (rc == MP_OK && cudaMallocAsync((void **)&ps->powers, footprint(sv, N), s) != cudaSuccess) {
+        ps->powers = nullptr;
+        rc = MP_ENOMEM;
+    }
+    if (rc == MP_OK) rc = mp_transfer_power_sequence(ps->n, sv->B, ps->powers, nullptr, s);
+    const int16_t *AB = ps->powers + (size_t)(sv->B - 1) * mat;
+    for (int t = 2; rc == MP_OK && t <= sv->T; ++t) {
+        const int16_t *prev = t == 2 ? AB : ps->powers + (size_t)(sv->B + t - 3) * mat;
+        int16_t *outp = ps->powers + (size_t)(sv->B + t - 2) * mat;
+        rc = dense_minplus(prev, AB, outp, N, N, N, N, N, N, MP_I16, nullptr, s);
+    }
+    if (s) {
+        if (cudaStreamSynchronize(s) != cudaSuccess && rc == MP_OK) rc = MP_ECUDA;
+        cudaStreamDestroy(s);
+    }
+    ps->build_err = rc;
+    ps->built.store(rc == MP_OK ? 1 : -1, std::memory_order_release);
+    sv->cv.notify_all();
+}
+
+void finish(mp_server *sv, uint64_t ticket, int err, int64_t value) {
+    Slot &sl = sv->slots[ticket];
+    sl.value = value;
+    sl.err = err;
+    sl.t_done = now_s();
+    int expect = kQueued;
+    if (sl.state.compare_exchange_strong(expect, err == MP_OK ? kDone : kFailed)) {
+        if (err == MP_OK) sv->stat_completed++;
+        else sv->stat_failed++;
+    }
+}
+
+// Powers (x, y) with x + y = m, both resident: baby steps 1..B, giant tB.
+void split(const mp_server *sv, int64_t m, int *slot_x, int *slot_y) {
+    const int B = sv->B;
+    if (m <= B) {
+        const int x = (int)(m / 2), y = (int)(m - m / 2);
+        *slot_x = x - 1;
+        *slot_y = y - 1;
+        return;
+    }
+    const int64_t t = (m - 1) / B;  // giant step tB < m, remainder x = m - tB in [1, B]
+    const int x = (int)(m - t * B);
+    *slot_x = x - 1;
+    *slot_y = t == 1 ? B - 1 : (int)(B + t - 2);
+}
+
+// Route incoming queries: resident -> ready; building -> waiting; absent ->
+// admission (evict, start a builder) or refusal.
+void route(mp_server *sv, const Query &q, std::vector<Query> &ready) {
+    auto it = sv->paths.find(q.n);
+    if (it != sv->paths.end() && it->second->status == kResident) {
+        ready.push_back(q);
+        return;
+    }
+    if (it != sv->paths.end() && it->second->status == kBuilding) {
+        it->second->waiting.push_back(q);
+        return;
+    }
+    const int64_t N = words_count(q.n);
+    const size_t need = footprint(sv, N);
+    if (need > sv->budget) {
+        set_error(MP_ENOMEM, "path order %d needs %zu bytes, budget %zu", q.n, need, sv->budget);
+        finish(sv, q.ticket, MP_ENOMEM, 0);
+        return;
+    }
+    // evict least recently used idle path orders until the new one fits
+    while (sv->used + need > sv->budget) {
+        PathState *victim = nullptr;
+        for (auto &kv : sv->paths) {
+            PathState *p = kv.second.get();
+            if (p->status == kResident && p->inflight == 0 && p->waiting.empty() &&
+                (!victim || p->last_use < victim->last_use))
+                victim = p;
+        }
+        if (!victim) break;
+        cudaFreeAsync(victim->powers, sv->compute);
+        victim->powers = nullptr;
+        victim->status = kAbsent;
+        sv->used -= victim->bytes;
+        victim->bytes = 0;
+        sv->stat_evictions++;
+    }
+    if (sv->used + need > sv->budget) {
+        sv->deferred.push_back(q);  // admitted once memory frees up
+        return;
+    }
+    auto &ptr = sv->paths[q.n];
+    if (!ptr) ptr.reset(new PathState());
+    PathState *ps = ptr.get();
+    if (ps->builder.joinable()) ps->builder.join();
+    ps->n = q.n;
+    ps->N = N;
+    ps->status = kBuilding;
+    ps->bytes = need;
+    ps->built.store(0);
+    sv->used += need;
+    sv->stat_builds++;
+    ps->waiting.push_back(q);
+    ps->builder = std::thread(build_path, sv, ps);
+}
+
+int launch_batch(mp_server *sv, Batch &b, std::vector<Query> &ready) {
+    const int cnt = (int)std::min<size_t>(ready.size(), (size_t)sv->max_batch);
+    b.qs.assign(ready.begin(), ready.begin() + cnt);
+    ready.erase(ready.begin(), ready.begin() + cnt);
+    std::map<int, int> use;
+    int64_t tiles = 0;
+    for (int i = 0; i < cnt; ++i) {
+        const Query &q = b.qs[i];
+        PathState *ps = sv->paths[q.n].get();
+        const size_t mat = (size_t)ps->N * (size_t)ps->N;
+        int sx, sy;
+        split(sv, q.m, &sx, &sy);
+        TraceJob &j = b.h_jobs[i];
+        j.X = ps->powers + (size_t)sx * mat;
+        j.Y = ps->powers + (size_t)sy * mat;
+        j.N = ps->N;
+        j.side = (ps->N + 31) / 32;
+        j.tile0 = tiles;
+        tiles += j.side * j.side;
+        ps->inflight++;
+        ps->last_use = ++sv->clock;
+        use[q.n]++;
+    }
+    b.uses.assign(use.begin(), use.end());
+    MP_CUDA_TRY(cudaMemcpyAsync(b.d_jobs, b.h_jobs, sizeof(TraceJob) * (size_t)cnt,
+                                cudaMemcpyHostToDevice, sv->compute));
+    fill_inf_kernel<<<(cnt + 255) / 256, 256, 0, sv->compute>>>(b.d_out, cnt);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sv->sms * 8));
+    batched_trace_kernel<<<(unsigned)grid, 256, 0, sv->compute>>>(b.d_jobs, cnt, tiles, b.d_out);
+    MP_CUDA_TRY(cudaGetLastError());
+    MP_CUDA_TRY(cudaMemcpyAsync(b.h_out, b.d_out, sizeof(int32_t) * (size_t)cnt,
+                                cudaMemcpyDeviceToHost, sv->compute));
+    MP_CUDA_TRY(cudaEventRecord(b.done, sv->compute));
+    b.busy = true;
+    sv->stat_batches++;
+    return MP_OK;
+}
+
+void complete_batch(mp_server *sv, Batch &b) {
+    for (size_t i = 0; i < b.qs.size(); ++i) finish(sv, b.qs[i].ticket, MP_OK, b.h_out[i]);
+    for (auto &u : b.uses) sv->paths[u.first]->inflight -= u.second;
+    b.qs.clear();
+    b.busy = false;
+}
+
+void worker_main(mp_server *sv) {
+    cudaSetDevice(sv->device);
+    std::vector<Query> ready;
+    while (true) {
+        std::deque<Query> incoming;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            const bool idle = sv->queue.empty() && ready.empty() && !sv->batches[0].busy &&
+                              !sv->batches[1].busy;
+            if (idle && !sv->stop) {
+                bool building = false;
+                for (auto &kv : sv->paths) building |= kv.second->status == kBuilding;
+                sv->cv.wait_for(lk, std::chrono::microseconds(building ? 100 : 2000));
+            }
+            if (sv->stop) break;
+            incoming.swap(sv->queue);
+        }
+        // builds that finished: their waiting queries become ready
+        for (auto &kv : sv->paths) {
+            PathState *ps = kv.second.get();
+            if (ps->status != kBuilding) continue;
+            const int st = ps->built.load(std::memory_order_acquire);
+            if (st == 0) continue;
+            if (ps->builder.joinable()) ps->builder.join();
+            if (st > 0) {
+                ps->status = kResident;
+                for (auto &q : ps->waiting) ready.push_back(q);
+            } else {
+                for (auto &q : ps->waiting) finish(sv, q.ticket, ps->build_err, 0);
+                if (ps->powers) cudaFreeAsync(ps->powers, sv->compute);
+                ps->powers = nullptr;
+                ps->status = kAbsent;
+                sv->used -= ps->bytes;
+                ps->bytes = 0;
+            }
+            ps->waiting.clear();
+        }
+        // deferred admissions retry once memory may have freed up
+        if (!sv->deferred.empty()) {
+            std::deque<Query> d;
+            d.swap(sv->deferred);
+            for (auto &q : d) incoming.push_back(q);
+        }
+        for (auto &q : incoming) {
+            if (sv->slots[q.ticket].state.load() == kCancelled) continue;
+            route(sv, q, ready);
+        }
+        // drop cancelled queries before they are batched
+        ready.erase(std::remove_if(ready.begin(), ready.end(),
+                                   [&](const Query &q) {
+                                       return sv->slots[q.ticket].state.load() == kCancelled;
+                                   }),
+                    ready.end());
+        // completed batches
+        for (auto &b : sv->batches)
+            if (b.busy && cudaEventQuery(b.done) == cudaSuccess) complete_batch(sv, b);
+        // new batches while a slot is free
+        for (auto &b : sv->batches)
+            if (!b.busy && !ready.empty()) {
+                if (launch_batch(sv, b, ready) != MP_OK) {
+                    for (auto &q : b.qs) finish(sv, q.ticket, MP_ECUDA, 0);
+                    b.qs.clear();
+                }
+            }
+        sv->stat_resident_bytes = sv->used;
+        if (!sv->batches[0].busy && !sv->batches[1].busy && ready.empty()) continue;
+        std::this_thread::yield();
+    }
+    // shutdown: let in-flight work finish
+    for (auto &b : sv->batches)
+        if (b.busy) {
+            cudaEventSynchronize(b.done);
+            complete_batch(sv, b);
+        }
+}
+
+}  // namespace
+
+}  // namespace mp
+
+using namespace mp;
+
+extern "C" {
+
+int mp_server_create(size_t hbm_budget, int max_batch, int64_t max_m, int64_t max_tickets,
+                     mp_server **out) {
+    if (!out || max_batch < 1 || max_m < 3 || max_tickets < 1)
+        return set_error(MP_EINVAL, "bad server parameters");
+    *out = nullptr;
+    auto sv = std::make_unique<mp_server>();
+    MP_CUDA_TRY(cudaGetDevice(&sv->device));
+    DeviceInfo di;
+    MP_TRY(device_info(&di));
+    sv->sms = di.sms;
+    sv->budget = hbm_budget;
+    sv->max_batch = max_batch;
+    sv->max_m = max_m;
+    int B = 1;
+    while ((int64_t)B * B < max_m) ++B;
+    sv->B = B;
+    sv->T = (int)std::max<int64_t>(2, (max_m + B - 1) / B);
+    sv->slots = std::vector<Slot>((size_t)max_tickets);
+    MP_CUDA_TRY(cudaStreamCreateWithFlags(&sv->compute, cudaStreamNonBlocking));
+    for (auto &b : sv->batches) {
+        MP_CUDA_TRY(cudaMalloc(&b.d_out, sizeof(int32_t) * (size_t)max_batch));
+        MP_CUDA_TRY(cudaMalloc(&b.d_jobs, sizeof(TraceJob) * (size_t)max_batch));
+        MP_CUDA_TRY(cudaMallocHost(&b.h_out, sizeof(int32_t) * (size_t)max_batch));
+        MP_CUDA_TRY(cudaMallocHost(&b.h_jobs, sizeof(TraceJob) * (size_t)max_batch));
+        MP_CUDA_TRY(cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+    }
+    mp_server *raw = sv.release();
+    raw->worker = std::thread(worker_main, raw);
+    *out = raw;
+    return MP_OK;
+}
+
+int mp_server_submit(mp_server *sv, int n, int64_t m, uint64_t *ticket) {
+    if (!sv || !ticket) return set_error(MP_EINVAL, "NULL server or ticket");
+    if (n < 1 || n > MP_MAX_PATH_ORDER || m < 3 || m > sv->max_m)
+        return set_error(MP_EINVAL, "query (n = %d, m = %lld) outside n in [1, %d], m in [3, %lld]",
+                         n, (long long)m, MP_MAX_PATH_ORDER, (long long)sv->max_m);
+    if (m * (int64_t)n >= (int64_t)kInf16)
+        return set_error(MP_ERANGE, "m * n = %lld reaches the int16 INF code", (long long)(m * n));
+    const uint64_t t = sv->next_ticket.fetch_add(1);
+    if (t >= sv->slots.size()) {
+        sv->next_ticket.fetch_sub(1);
+        return set_error(MP_EBUSY, "ticket table full (%zu)", sv->slots.size());
+    }
+    Slot &sl = sv->slots[t];
+    sl.n = n;
+    sl.m = m;
+    sl.t_submit = now_s();
+    sl.state.store(kQueued);
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->queue.push_back({t, n, m});
+    }
+    sv->cv.notify_one();
+    *ticket = t;
+    return MP_OK;
+}
+
+int mp_server_poll(mp_server *sv, uint64_t ticket, int64_t *gamma2) {
+    if (!sv || ticket >= sv->next_ticket.load()) return set_error(MP_EINVAL, "unknown ticket");
+    Slot &sl = sv->slots[ticket];
+    const int st = sl.state.load(std::memory_order_acquire);
+    if (st == kQueued) return MP_ENOTREADY;
+    if (st == kCancelled) return set_error(MP_EINVAL, "ticket %llu was cancelled", (unsigned long long)ticket);
+    if (st == kFailed) return set_error(sl.err, "query failed");
+    if (gamma2) *gamma2 = sl.value;
+    return MP_OK;
+}
+
+int mp_server_cancel(mp_server *sv, uint64_t ticket) {
+    if (!sv || ticket >= sv->next_ticket.load()) return set_error(MP_EINVAL, "unknown ticket");
+    int expect = kQueued;
+    if (sv->slots[ticket].state.compare_exchange_strong(expect, kCancelled)) {
+        sv->stat_cancelled++;
+        return MP_OK;
+    }
+    return set_error(MP_EBUSY, "ticket %llu already finished", (unsigned long long)ticket);
+}
+
+int mp_server_latency(mp_server *sv, uint64_t ticket, double *submit_s, double *done_s) {
+    if (!sv || ticket >= sv->next_ticket.load()) return set_error(MP_EINVAL, "unknown ticket");
+    Slot &sl = sv->slots[ticket];
+    const int st = sl.state.load(std::memory_order_acquire);
+    if (st != kDone && st != kFailed) return MP_ENOTREADY;
+    if (submit_s) *submit_s = sl.t_submit;
+    if (done_s) *done_s = sl.t_done;
+    return MP_OK;
+}
+
+int mp_server_stats(mp_server *sv, int64_t *out) {
+    if (!sv || !out) return set_error(MP_EINVAL, "NULL argument");
+    out[0] = (int64_t)sv->next_ticket.load();
+    out[1] = (int64_t)sv->stat_completed.load();
+    out[2] = (int64_t)sv->stat_failed.load();
+    out[3] = (int64_t)sv->stat_cancelled.load();
+    out[4] = (int64_t)sv->stat_batches.load();
+    out[5] = (int64_t)sv->stat_builds.load();
+    out[6] = (int64_t)sv->stat_evictions.load();
+    out[7] = (int64_t)sv->stat_resident_bytes.load();
+    return MP_OK;
+}
+
+int mp_server_destroy(mp_server *sv) {
+    if (!sv) return MP_OK;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    for (auto &kv : sv->paths) {
+        PathState *ps = kv.second.get();
+        if (ps->builder.joinable()) ps->builder.join();
+        if (ps->powers) cudaFreeAsync(ps->powers, sv->compute);
+    }
+    cudaStreamSynchronize(sv->compute);
+    for (auto &b : sv->batches) {
+        cudaFree(b.d_out);
+        cudaFree(b.d_jobs);
+        cudaFreeHost(b.h_out);
+        cudaFreeHost(b.h_jobs);
+        cudaEventDestroy(b.done);
+    }
+    cudaStreamDestroy(sv->compute);
+    delete sv;
+    return MP_OK;
+}
+
+}  // extern "C"
