@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense", action="store_true", help="skip the N=8192 dense products")
     ap.add_argument("--no-batched", action="store_true", help="skip the 96-product batch")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served query stream")
     ap.add_argument("--profile", choices=["chain9", "chain8", "gemm8192", "gemm8192u8"],
                     help="run one small case for an ncu capture and exit")
     return ap.parse_args()
@@ -276,6 +277,7 @@ def run_ours(args):
     # ---- configs[1]-style dense products (K1), reported beside the chain
     dense = dense_extras(mp, torch, flush, stream, peak_viaddmin) if not args.no_dense else None
     batched = batched_extras(mp, torch, flush) if not args.no_batched else None
+    serving = serving_extras(mp, torch) if not args.no_serving else None
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
     cpu = None
@@ -308,6 +310,8 @@ def run_ours(args):
         line["dense_gemm"] = dense
     if batched is not None:
         line["batched"] = batched
+    if serving is not None:
+        line["serving"] = serving
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -437,6 +441,50 @@ def batched_extras(mp, torch, flush):
     out["speedup_persistent_vs_per_product"] = round(
         out["per_product_graph"]["ms"] / out["persistent_graph"]["ms"], 3)
     batch.close()
+    return out
+
+
+def serving_extras(mp, torch):
+    """10,000 gamma_2(n, m) queries: n uniform in {2..10}, m log-uniform in
+    [3, 2000] (seed 11).  Capacity mu = the rate with all queries submitted at
+    once; then Poisson arrivals (seed 11) at 0.5, 0.9 and 1.5 mu, latency =
+    answer time - submit time from the server's own clock.  Every answer is
+    checked against Theorem 3 (mp_gamma2_cylinder, recurrence cached)."""
+    import numpy as np
+    from paper_2409_17688_gb300 import synth
+    ns, ms = synth.serving_queries(10000, seed=11)
+    truth = {}
+    # largest m first: the first call per n caches its recurrence (Theorem 3)
+    for n, m in sorted(set(zip(ns.tolist(), ms.tolist())), key=lambda q: -q[1]):
+        truth[(n, m)] = mp.mp_gamma2_cylinder(n, m)
+    srv = mp.Server(hbm_budget=64 << 30, max_batch=512, max_m=2000, max_tickets=1 << 17)
+    t0 = time.perf_counter()
+    warm = [srv.submit(n, 1000) for n in range(2, 11)]
+    for t in warm:
+        srv.wait(t, timeout_s=600)
+    setup_s = time.perf_counter() - t0
+    resident = srv.stats()["resident_bytes"]
+
+    def run(arrivals):
+        # the library's load generator submits at the arrival times
+        tickets = [int(t) for t in srv.replay(ns, ms, arrivals)]
+        vals = [srv.wait(t, timeout_s=600) for t in tickets]
+        bad = sum(1 for i, v in enumerate(vals) if v != truth[(int(ns[i]), int(ms[i]))])
+        lat = np.array([srv.latency(t) for t in tickets])
+        span = lat[:, 1].max() - lat[:, 0].min()
+        d = lat[:, 1] - lat[:, 0]
+        return {"qps": round(len(ns) / span, 1), "p50_ms": round(float(np.percentile(d, 50)) * 1e3, 3),
+                "p99_ms": round(float(np.percentile(d, 99)) * 1e3, 3), "wrong": bad}
+
+    cap = run(None)
+    mu = cap["qps"]
+    out = {"queries": len(ns), "setup_s": round(setup_s, 2), "resident_bytes": resident,
+           "capacity": cap}
+    for f in (0.5, 0.9, 1.5):
+        arr = synth.poisson_arrivals(len(ns), f * mu, seed=11)
+        out[f"rate_{f}mu"] = dict(run(arr), offered_qps=round(f * mu, 1))
+    out["stats"] = srv.stats()
+    srv.close()
     return out
 
 

@@ -242,12 +242,13 @@ int mp_tuning_get(int32_t *table);
 /* ---- serving: continuous batching of gamma_2 queries ---------------------
  * A server answers gamma_2(P_n x C_m) (Theorem 2) for a stream of queries.
  * For each path order it serves it keeps powers of A(D_n) resident on the
- * current device: A^1..A^B and A^{tB} for t = 2..T, with B = ceil(sqrt(max_m))
- * and T = ceil(max_m / B), so every m <= max_m is one min-trace of two
- * resident powers.  A worker thread batches the queries whose path order is
+ * current device: A^1..A^B and, transposed, A^{tB} for t = 1..T, with
+ * B = ceil(sqrt(max_m)) and T = ceil(max_m / B).  m <= B is answered from
+ * the min-diagonals kept on the host; every larger m <= max_m is one
+ * streaming min of A^x + (A^{tB})^T over two resident powers (m = x + tB).  A worker thread batches the queries whose path order is
  * resident into one launch (two batches may be in flight); a query for a
  * path order that is not resident admits it: its footprint
- * (B + T - 1) * N^2 * 2 bytes is checked against hbm_budget, idle path
+ * (B + T) * N^2 * 2 bytes (slots rounded to 8 entries) is checked against hbm_budget, idle path
  * orders are evicted least recently used first, and a builder thread
  * computes the powers on its own stream while other batches run.
  *
@@ -256,6 +257,10 @@ int mp_tuning_get(int32_t *table);
  *   ticket table (the server's lifetime query count).  The server lives on
  *   the current device.
  * mp_server_submit: enqueues (n, m) and returns a ticket; never blocks.
+ * mp_server_replay: a load generator: submits query i of the HOST arrays
+ *   n[i], m[i] at t_offsets[i] seconds after the call (busy-waiting on a
+ *   monotonic clock; t_offsets NULL submits at once), writes the tickets,
+ *   and returns once all are submitted (not answered).
  *   MP_EINVAL for n outside [1, 16] or m outside [3, max_m], MP_ERANGE for
  *   m * n >= 32767, MP_EBUSY when the ticket table is full.
  * mp_server_poll: MP_OK with *gamma2 set (HOST int64) once answered,
@@ -274,6 +279,8 @@ typedef struct mp_server mp_server;
 int mp_server_create(size_t hbm_budget, int max_batch, int64_t max_m, int64_t max_tickets,
                      mp_server **out);
 int mp_server_submit(mp_server *server, int n, int64_t m, uint64_t *ticket);
+int mp_server_replay(mp_server *server, const int32_t *n, const int64_t *m,
+                     const double *t_offsets, int64_t count, uint64_t *tickets);
 int mp_server_poll(mp_server *server, uint64_t ticket, int64_t *gamma2);
 int mp_server_cancel(mp_server *server, uint64_t ticket);
 int mp_server_latency(mp_server *server, uint64_t ticket, double *submit_s, double *done_s);

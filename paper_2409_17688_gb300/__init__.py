@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
         "mp_tuning_get": (I, [P]),
         "mp_server_create": (I, [ctypes.c_size_t, I, I64, I64, P]),
         "mp_server_submit": (I, [P, I, I64, P]),
+        "mp_server_replay": (I, [P, P, P, P, I64, P]),
         "mp_server_poll": (I, [P, ctypes.c_uint64, P]),
         "mp_server_cancel": (I, [P, ctypes.c_uint64]),
         "mp_server_latency": (I, [P, ctypes.c_uint64, P, P]),
@@ -340,6 +341,17 @@ class Server:
         t = ctypes.c_uint64(0)
         _check(lib().mp_server_submit(self._h, int(n), int(m), ctypes.byref(t)))
         return int(t.value)
+
+    def replay(self, ns, ms, offsets=None):
+        """Native load generator: submit query i at offsets[i] seconds (or at once)."""
+        ns = np.ascontiguousarray(ns, dtype=np.int32)
+        ms = np.ascontiguousarray(ms, dtype=np.int64)
+        tk = np.zeros(len(ns), dtype=np.uint64)
+        off = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.float64)
+        _check(lib().mp_server_replay(self._h, ns.ctypes.data, ms.ctypes.data,
+                                      None if off is None else off.ctypes.data, len(ns),
+                                      tk.ctypes.data))
+        return tk
 
     def poll(self, ticket: int):
         v = ctypes.c_int64(0)

@@ -165,8 +165,7 @@ static int transfer_entry(int n, cudaStream_t s, TransferEntry **out) {
 
 // The chain over a prepared sparse plan; B0 already holds P_1.
 static int run_sparse_chain(const PlanDev &plan, uint16_t *B0, uint16_t *B1, int k_max,
-                            int16_t *powers, int32_t *gdiag, cudaStream_t s) {
-    const size_t slot = (size_t)plan.N * (size_t)plan.N;
+                            int16_t *powers, size_t slot, int32_t *gdiag, cudaStream_t s) {
     uint16_t *buf[2] = {B0, B1};
     for (int k = 2; k <= k_max; ++k) {
         MP_TRY(sparse_step(plan, buf[(k - 2) & 1], buf[(k - 1) & 1],
@@ -260,6 +259,27 @@ static int transfer_recurrence(int n, int K, Recurrence *out, cudaStream_t s) {
     MP_CUDA_TRY(cudaStreamSynchronize(s));
     *out = r;
     return MP_OK;
+}
+
+// The transfer chain with slot k-1 of the powers at powers + (k-1)*slot
+// (slot >= N*N elements; the caller may pad slots for alignment).
+int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
+                            int32_t *gdiag_opt, cudaStream_t s) {
+    if (k_max < 1) return set_error(MP_EINVAL, "k_max = %d < 1", k_max);
+    TransferEntry *te;
+    MP_TRY(transfer_entry(n, s, &te));
+    const PlanDev &plan = te->plan;
+    if (slot < (size_t)te->N * (size_t)te->N) return set_error(MP_EINVAL, "slot stride too small");
+    if (powers_opt && gdiag_opt &&
+        ranges_overlap(gdiag_opt, (size_t)k_max * 4, powers_opt, slot * 2 * (size_t)k_max))
+        return set_error(MP_EALIAS, "gdiag overlaps the powers");
+    if (gdiag_opt) MP_TRY(launch_fill_i32(gdiag_opt, k_max, (int32_t)kInf16, s));
+    DevBuf B;
+    MP_TRY(B.alloc(2 * (size_t)plan.N * (size_t)plan.ldb * 2, s));
+    uint16_t *B0 = B.as<uint16_t>(), *B1 = B0 + (size_t)plan.N * (size_t)plan.ldb;
+    MP_TRY(sparse_init_from_csr(plan, te->csr.row_ptr.as<int64_t>(), te->csr.col.as<int32_t>(),
+                                te->csr.val.as<int16_t>(), B0, powers_opt, gdiag_opt, s));
+    return run_sparse_chain(plan, B0, B1, k_max, powers_opt, slot, gdiag_opt, s);
 }
 
 static int check_n(int n) {
@@ -394,7 +414,7 @@ int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max, int16_t *p
     MP_TRY(B.alloc(2 * (size_t)plan.N * (size_t)plan.ldb * 2, s));
     uint16_t *B0 = B.as<uint16_t>(), *B1 = B0 + (size_t)plan.N * (size_t)plan.ldb;
     MP_TRY(sparse_init_from_dense(plan, A, B0, powers_opt, gdiag_opt, s));
-    MP_TRY(run_sparse_chain(plan, B0, B1, k_max, powers_opt, gdiag_opt, s));
+    MP_TRY(run_sparse_chain(plan, B0, B1, k_max, powers_opt, (size_t)N * (size_t)N, gdiag_opt, s));
     // the host-side plan vectors were copied from pageable memory: make sure
     // the copies are done before they go out of scope
     MP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -404,22 +424,10 @@ int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max, int16_t *p
 int mp_transfer_power_sequence(int n, int k_max, int16_t *powers_opt, int32_t *gdiag_opt,
                                void *stream) {
     MP_TRY(check_n(n));
-    if (k_max < 1) return set_error(MP_EINVAL, "k_max = %d < 1", k_max);
-    cudaStream_t s = (cudaStream_t)stream;
-    TransferEntry *te;
-    MP_TRY(transfer_entry(n, s, &te));
-    const PlanDev &plan = te->plan;
-    const size_t slot = (size_t)te->N * (size_t)te->N * 2;
-    if (powers_opt && gdiag_opt &&
-        ranges_overlap(gdiag_opt, (size_t)k_max * 4, powers_opt, slot * (size_t)k_max))
-        return set_error(MP_EALIAS, "gdiag overlaps the powers");
-    if (gdiag_opt) MP_TRY(launch_fill_i32(gdiag_opt, k_max, (int32_t)kInf16, s));
-    DevBuf B;
-    MP_TRY(B.alloc(2 * (size_t)plan.N * (size_t)plan.ldb * 2, s));
-    uint16_t *B0 = B.as<uint16_t>(), *B1 = B0 + (size_t)plan.N * (size_t)plan.ldb;
-    MP_TRY(sparse_init_from_csr(plan, te->csr.row_ptr.as<int64_t>(), te->csr.col.as<int32_t>(),
-                                te->csr.val.as<int16_t>(), B0, powers_opt, gdiag_opt, s));
-    return run_sparse_chain(plan, B0, B1, k_max, powers_opt, gdiag_opt, s);
+    std::vector<uint32_t> w;
+    enumerate_words(n, &w);
+    const size_t N = w.size();
+    return transfer_powers_strided(n, k_max, powers_opt, N * N, gdiag_opt, (cudaStream_t)stream);
 }
 
 int mp_gamma2_table(int n, int k_max, int64_t *out) {

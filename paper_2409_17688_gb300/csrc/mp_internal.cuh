@@ -125,6 +125,9 @@ int launch_diff_const(const int16_t *X, const int16_t *Y, int64_t count, int32_t
                       cudaStream_t s);
 int launch_min_trace(const int16_t *X, const int16_t *Y, int64_t N, int64_t ldx,
                      int64_t ldy, int32_t *out, cudaStream_t s);
+// The transfer chain of A(D_n) with a caller-chosen slot stride (elements).
+int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
+                            int32_t *gdiag_opt, cudaStream_t s);
 // Dense (min,+) product; gdiag (optional) gets atomicMin of the diagonal.
 int dense_minplus(const void *X, const void *Y, void *Z, int64_t M, int64_t N,
                   int64_t K, int64_t ldx, int64_t ldy, int64_t ldz, int dtype,

@@ -2,10 +2,12 @@
 //
 // For every path order it serves, the server keeps powers of A(D_n)
 // resident on the device: the "baby steps" A^1..A^B (from the sparse chain)
-// and the "giant steps" A^{tB}, t = 2..T (dense products A^{(t-1)B} (x) A^B).
-// Any m in [2, B(T+1)] splits as m = x + y with both powers resident, and
-// gamma_2 = min_i (A^x (x) A^y)_ii = min_{i,l} A^x_il + A^y_li is one
-// O(N^2) min-trace, so a query costs one pass over two resident matrices.
+// and, transposed, the "giant steps" A^{tB}, t = 1..T (dense products
+// A^{tB} = A^{(t-1)B} (x) A^B).  For m <= B the answer is the min-diagonal
+// of A^m, kept on the host from the chain.  Any larger m <= B(T+1) splits as
+// m = x + tB with x in [1, B], and gamma_2 = min_i (A^x (x) A^{tB})_ii =
+// min_{i,l} A^x_il + (A^{tB})^T_il: one streaming pass over two resident
+// matrices (a min of elementwise sums, 16-bit pairs, 16-byte loads).
 //
 // Requests enter a queue (mp_server_submit, any host thread).  A worker
 // thread drains it continuously: queries whose n is resident join the next
@@ -46,45 +48,69 @@ double now_s() {
 }
 
 struct TraceJob {
-    const int16_t *X;
-    const int16_t *Y;
-    int64_t N;
-    int64_t tile0;  // first global tile index of this job
-    int64_t side;   // tiles per side (ceil(N / 32))
+    const int16_t *X;   // A^x, N*N entries
+    const int16_t *YT;  // (A^{tB})^T, N*N entries
+    int64_t count;      // N*N
+    int64_t cta0;       // first CTA of this job
 };
 
-// One 32 x 32 block (I, L) of min_{i,l} X_il + Y_li per CTA step, over all
-// jobs of a batch (a persistent grid walks the global tile index).
-__global__ void batched_trace_kernel(const TraceJob *__restrict__ jobs, int njobs,
-                                     int64_t total, int32_t *__restrict__ out) {
-    __shared__ int32_t ys[32][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        int lo = 0, hi = njobs - 1;
-        while (lo < hi) {  // last job with tile0 <= t
-            const int mid = (lo + hi + 1) >> 1;
-            if (jobs[mid].tile0 <= t) lo = mid;
-            else hi = mid - 1;
-        }
-        const TraceJob j = jobs[lo];
-        const int64_t loc = t - j.tile0;
-        const int64_t i0 = (loc / j.side) * 32, l0 = (loc % j.side) * 32;
-        for (int r = ty; r < 32; r += 8) {
-            const int64_t l = l0 + r, i = i0 + tx;
-            ys[r][tx] = (l < j.N && i < j.N) ? (int32_t)(uint16_t)j.Y[l * j.N + i] : (int32_t)kInf16;
-        }
-        __syncthreads();
-        int32_t v = 2 * (int32_t)kInf16;
-        for (int r = ty; r < 32; r += 8) {
-            const int64_t i = i0 + r, l = l0 + tx;
-            const int32_t x = (i < j.N && l < j.N) ? (int32_t)(uint16_t)j.X[i * j.N + l] : (int32_t)kInf16;
-            v = min(v, x + ys[tx][r]);
-        }
+constexpr int kTraceThreads = 256;
+constexpr int64_t kTraceSpan = (int64_t)kTraceThreads * 8 * 16;  // entries per CTA
+
+// min over e of X[e] + YT[e] for every job; each CTA takes one contiguous
+// span of one job (both slots start on 16-byte boundaries, spans are
+// multiples of 8 entries), folds 16-bit pairs with __viaddmin_u16x2 and
+// issues one atomicMin.
+__global__ void __launch_bounds__(kTraceThreads)
+trace_stream_kernel(const TraceJob *__restrict__ jobs, int njobs, int32_t *__restrict__ out) {
+    int lo = 0, hi = njobs - 1;
+    const int64_t b = blockIdx.x;
+    while (lo < hi) {  // last job with cta0 <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].cta0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const TraceJob j = jobs[lo];
+    const int64_t start = (b - j.cta0) * kTraceSpan;
+    const int64_t end = min(j.count, start + kTraceSpan);
+    const int64_t vend = start + ((end - start) & ~(int64_t)7);
+    uint32_t acc = 0xFFFFFFFFu;
+    for (int64_t e = start + 8 * (int64_t)threadIdx.x; e < vend; e += 8 * kTraceThreads) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(j.X + e));
+        const uint4 y = __ldg(reinterpret_cast<const uint4 *>(j.YT + e));
+        acc = __viaddmin_u16x2(x.x, y.x, acc);
+        acc = __viaddmin_u16x2(x.y, y.y, acc);
+        acc = __viaddmin_u16x2(x.z, y.z, acc);
+        acc = __viaddmin_u16x2(x.w, y.w, acc);
+    }
+    int32_t v = (int32_t)min(acc & 0xFFFFu, acc >> 16);
+    for (int64_t e = vend + threadIdx.x; e < end; e += kTraceThreads)
+        v = min(v, (int32_t)(uint16_t)j.X[e] + (int32_t)(uint16_t)j.YT[e]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    __shared__ int32_t wmin[kTraceThreads / 32];
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kTraceThreads / 32; ++w) v = min(v, wmin[w]);
         v = min(v, (int32_t)kInf16);
-        if (tx == 0 && v < (int32_t)kInf16) atomicMin(&out[lo], v);
-        __syncthreads();
+        if (v < (int32_t)kInf16) atomicMin(&out[lo], v);
+    }
+}
+
+// out[c][r] = in[r][c] for an N x N matrix (both with leading dimension ld_in / N).
+__global__ void transpose_kernel(const int16_t *__restrict__ in, int64_t ld_in,
+                                 int16_t *__restrict__ out, int64_t N) {
+    __shared__ int16_t t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t rr = r0 + r, cc = c0 + threadIdx.x;
+        if (rr < N && cc < N) t[r][threadIdx.x] = in[rr * ld_in + cc];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t oc = c0 + r, orow = r0 + threadIdx.x;  // out[oc][orow] = in[orow][oc]
+        if (oc < N && orow < N) out[oc * N + orow] = t[threadIdx.x][r];
     }
 }
 
@@ -117,7 +143,9 @@ struct PathState {
     int64_t N = 0;
     int status = kAbsent;
     size_t bytes = 0;
-    int16_t *powers = nullptr;  // [B + T - 1][N][N]: A^1..A^B, then A^{2B}..A^{TB}
+    int16_t *powers = nullptr;  // B + T slots of `slot` entries: A^1..A^B, then (A^{tB})^T
+    size_t slot = 0;            // N*N rounded up to 8 entries (16-byte aligned slots)
+    std::vector<int32_t> diag;  // min diag A^m, m = 1..B
     std::atomic<int> built{0};  // set by the builder thread (1 ok, -1 failed)
     int build_err = 0;
     std::thread builder;
@@ -128,6 +156,7 @@ struct PathState {
 
 struct Batch {
     std::vector<Query> qs;
+    int64_t ctas = 0;
     std::vector<std::pair<int, int>> uses;  // path orders touched (n, count)
     int32_t *d_out = nullptr;
     int32_t *h_out = nullptr;
@@ -175,8 +204,10 @@ namespace mp {
 
 namespace {
 
+size_t slot_of(int64_t N) { return ((size_t)N * (size_t)N + 7) & ~(size_t)7; }
+
 size_t footprint(const mp_server *sv, int64_t N) {
-    return (size_t)(sv->B + sv->T - 1) * (size_t)N * (size_t)N * 2;
+    return (size_t)(sv->B + sv->T) * slot_of(N) * 2;
 }
 
 int64_t words_count(int n) {
@@ -185,26 +216,54 @@ int64_t words_count(int n) {
     return (int64_t)w.size();
 }
 
-// Builder thread body: baby steps by the sparse chain, giant steps by
-// dense products, all on a private stream.
+// Builder thread body, on a private stream: baby steps by the sparse chain
+// (with their min-diagonals), giant steps by dense products in padded
+// scratch, each stored transposed.
 void build_path(mp_server *sv, PathState *ps) {
     cudaSetDevice(sv->device);
     cudaStream_t s = nullptr;
     int rc = MP_OK;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = MP_ECUDA;
     const int64_t N = ps->N;
-    const size_t mat = (size_t)N * (size_t)N;
+    const int64_t ld = (N + 7) & ~(int64_t)7;  // padded rows: 16-byte vector loads in the products
+    ps->slot = slot_of(N);
+    int16_t *tmp = nullptr;
+    int32_t *gd = nullptr;
     if (rc == MP_OK && cudaMallocAsync((void **)&ps->powers, footprint(sv, N), s) != cudaSuccess) {
         ps->powers = nullptr;
         rc = MP_ENOMEM;
     }
-    if (rc == MP_OK) rc = mp_transfer_power_sequence(ps->n, sv->B, ps->powers, nullptr, s);
-    const int16_t *AB = ps->powers + (size_t)(sv->B - 1) * mat;
-    for (int t = 2; rc == MP_OK && t <= sv->T; ++t) {
-        const int16_t *prev = t == 2 ? AB : ps->powers + (size_t)(sv->B + t - 3) * mat;
-        int16_t *outp = ps->powers + (size_t)(sv->B + t - 2) * mat;
-        rc = dense_minplus(prev, AB, outp, N, N, N, N, N, N, MP_I16, nullptr, s);
+    if (rc == MP_OK && (cudaMallocAsync((void **)&tmp, (size_t)3 * N * ld * 2, s) != cudaSuccess ||
+                        cudaMallocAsync((void **)&gd, sizeof(int32_t) * (size_t)sv->B, s) != cudaSuccess))
+        rc = MP_ENOMEM;
+    if (rc == MP_OK) rc = transfer_powers_strided(ps->n, sv->B, ps->powers, ps->slot, gd, s);
+    ps->diag.assign((size_t)sv->B, 0);
+    if (rc == MP_OK && cudaMemcpyAsync(ps->diag.data(), gd, sizeof(int32_t) * (size_t)sv->B,
+                                       cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        rc = MP_ECUDA;
+    int16_t *giant = ps->powers + (size_t)sv->B * ps->slot;
+    int16_t *AB = tmp, *cur = tmp + (size_t)N * ld, *nxt = tmp + (size_t)2 * N * ld;
+    const dim3 tgrid((unsigned)((N + 31) / 32), (unsigned)((N + 31) / 32)), tblock(32, 8);
+    if (rc == MP_OK &&
+        cudaMemcpy2DAsync(AB, (size_t)ld * 2, ps->powers + (size_t)(sv->B - 1) * ps->slot,
+                          (size_t)N * 2, (size_t)N * 2, (size_t)N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        rc = MP_ECUDA;
+    if (rc == MP_OK) {
+        transpose_kernel<<<tgrid, tblock, 0, s>>>(AB, ld, giant, N);  // t = 1
+        if (cudaGetLastError() != cudaSuccess) rc = MP_ECUDA;
     }
+    const int16_t *prev = AB;
+    int16_t *sbuf[2] = {cur, nxt};
+    for (int t = 2; rc == MP_OK && t <= sv->T; ++t) {
+        int16_t *dst = sbuf[t & 1];
+        rc = dense_minplus(prev, AB, dst, N, N, N, ld, ld, ld, MP_I16, nullptr, s);
+        if (rc != MP_OK) break;
+        transpose_kernel<<<tgrid, tblock, 0, s>>>(dst, ld, giant + (size_t)(t - 1) * ps->slot, N);
+        if (cudaGetLastError() != cudaSuccess) rc = MP_ECUDA;
+        prev = dst;
+    }
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (gd) cudaFreeAsync(gd, s);
     if (s) {
         if (cudaStreamSynchronize(s) != cudaSuccess && rc == MP_OK) rc = MP_ECUDA;
         cudaStreamDestroy(s);
@@ -226,19 +285,15 @@ void finish(mp_server *sv, uint64_t ticket, int err, int64_t value) {
     }
 }
 
-// Powers (x, y) with x + y = m, both resident: baby steps 1..B, giant tB.
-void split(const mp_server *sv, int64_t m, int *slot_x, int *slot_y) {
-    const int B = sv->B;
-    if (m <= B) {
-        const int x = (int)(m / 2), y = (int)(m - m / 2);
-        *slot_x = x - 1;
-        *slot_y = y - 1;
-        return;
+// A query of a resident path order: m <= B is answered from the host table
+// of min-diagonals, larger m goes to the next batch.
+void dispatch_resident(mp_server *sv, PathState *ps, const Query &q, std::vector<Query> &ready) {
+    if (q.m <= sv->B) {
+        ps->last_use = ++sv->clock;
+        finish(sv, q.ticket, MP_OK, ps->diag[(size_t)q.m - 1]);
+    } else {
+        ready.push_back(q);
     }
-    const int64_t t = (m - 1) / B;  // giant step tB < m, remainder x = m - tB in [1, B]
-    const int x = (int)(m - t * B);
-    *slot_x = x - 1;
-    *slot_y = t == 1 ? B - 1 : (int)(B + t - 2);
 }
 
 // Route incoming queries: resident -> ready; building -> waiting; absent ->
@@ -246,7 +301,7 @@ void split(const mp_server *sv, int64_t m, int *slot_x, int *slot_y) {
 void route(mp_server *sv, const Query &q, std::vector<Query> &ready) {
     auto it = sv->paths.find(q.n);
     if (it != sv->paths.end() && it->second->status == kResident) {
-        ready.push_back(q);
+        dispatch_resident(sv, it->second.get(), q, ready);
         return;
     }
     if (it != sv->paths.end() && it->second->status == kBuilding) {
@@ -301,30 +356,28 @@ int launch_batch(mp_server *sv, Batch &b, std::vector<Query> &ready) {
     b.qs.assign(ready.begin(), ready.begin() + cnt);
     ready.erase(ready.begin(), ready.begin() + cnt);
     std::map<int, int> use;
-    int64_t tiles = 0;
+    int64_t ctas = 0;
     for (int i = 0; i < cnt; ++i) {
         const Query &q = b.qs[i];
         PathState *ps = sv->paths[q.n].get();
-        const size_t mat = (size_t)ps->N * (size_t)ps->N;
-        int sx, sy;
-        split(sv, q.m, &sx, &sy);
+        const int64_t t = (q.m - 1) / sv->B;  // m = x + tB, x in [1, B], t in [1, T]
+        const int64_t x = q.m - t * sv->B;
         TraceJob &j = b.h_jobs[i];
-        j.X = ps->powers + (size_t)sx * mat;
-        j.Y = ps->powers + (size_t)sy * mat;
-        j.N = ps->N;
-        j.side = (ps->N + 31) / 32;
-        j.tile0 = tiles;
-        tiles += j.side * j.side;
+        j.X = ps->powers + (size_t)(x - 1) * ps->slot;
+        j.YT = ps->powers + (size_t)(sv->B + t - 1) * ps->slot;
+        j.count = ps->N * ps->N;
+        j.cta0 = ctas;
+        ctas += (j.count + kTraceSpan - 1) / kTraceSpan;
         ps->inflight++;
         ps->last_use = ++sv->clock;
         use[q.n]++;
     }
     b.uses.assign(use.begin(), use.end());
+    b.ctas = ctas;
     MP_CUDA_TRY(cudaMemcpyAsync(b.d_jobs, b.h_jobs, sizeof(TraceJob) * (size_t)cnt,
                                 cudaMemcpyHostToDevice, sv->compute));
     fill_inf_kernel<<<(cnt + 255) / 256, 256, 0, sv->compute>>>(b.d_out, cnt);
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sv->sms * 8));
-    batched_trace_kernel<<<(unsigned)grid, 256, 0, sv->compute>>>(b.d_jobs, cnt, tiles, b.d_out);
+    trace_stream_kernel<<<(unsigned)ctas, kTraceThreads, 0, sv->compute>>>(b.d_jobs, cnt, b.d_out);
     MP_CUDA_TRY(cudaGetLastError());
     MP_CUDA_TRY(cudaMemcpyAsync(b.h_out, b.d_out, sizeof(int32_t) * (size_t)cnt,
                                 cudaMemcpyDeviceToHost, sv->compute));
@@ -367,7 +420,7 @@ void worker_main(mp_server *sv) {
             if (ps->builder.joinable()) ps->builder.join();
             if (st > 0) {
                 ps->status = kResident;
-                for (auto &q : ps->waiting) ready.push_back(q);
+                for (auto &q : ps->waiting) dispatch_resident(sv, ps, q, ready);
             } else {
                 for (auto &q : ps->waiting) finish(sv, q.ticket, ps->build_err, 0);
                 if (ps->powers) cudaFreeAsync(ps->powers, sv->compute);
@@ -480,6 +533,22 @@ int mp_server_submit(mp_server *sv, int n, int64_t m, uint64_t *ticket) {
     }
     sv->cv.notify_one();
     *ticket = t;
+    return MP_OK;
+}
+
+int mp_server_replay(mp_server *sv, const int32_t *n, const int64_t *m, const double *t_offsets,
+                     int64_t count, uint64_t *tickets) {
+    if (!sv || !n || !m || !tickets || count < 0) return set_error(MP_EINVAL, "bad replay arguments");
+    const double base = now_s();
+    for (int64_t i = 0; i < count; ++i) {
+        if (t_offsets) {
+            const double target = base + t_offsets[i];
+            while (now_s() < target) {
+            }
+        }
+        const int rc = mp_server_submit(sv, n[i], m[i], &tickets[i]);
+        if (rc != MP_OK) return rc;
+    }
     return MP_OK;
 }
 

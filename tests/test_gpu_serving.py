@@ -29,7 +29,7 @@ def footprint(mp, n, max_m):
     B = int(np.ceil(np.sqrt(max_m)))
     T = max(2, -(-max_m // B))
     N = mp.mp_transfer_size(n)
-    return (B + T - 1) * N * N * 2
+    return (B + T) * ((N * N + 7) // 8 * 8) * 2
 
 
 def test_mixed_queries_match_oracle_and_alone(mp):
@@ -44,6 +44,11 @@ def test_mixed_queries_match_oracle_and_alone(mp):
     tables = {n: oracle.gamma2_range(n, 120, threads=THREADS) for n in range(1, 8)}
     for (n, m), g in zip(qs, got):
         assert g == tables[n][m], (n, m)
+    # the native load generator submits the same stream again
+    srv2 = mp.Server(hbm_budget=8 << 30, max_batch=64, max_m=120)
+    tk = srv2.replay([q[0] for q in qs], [q[1] for q in qs], np.linspace(0, 0.05, len(qs)))
+    assert [srv2.wait(int(t)) for t in tk] == got
+    srv2.close()
     # the same queries answered one at a time by a fresh server
     solo = mp.Server(hbm_budget=8 << 30, max_batch=64, max_m=120)
     for (n, m), g in list(zip(qs, got))[:40]:
