@@ -46,11 +46,10 @@ namespace {
 
 constexpr int kThreads = 512;                    // 16 warps
 constexpr int kWarps = kThreads / 32;
-constexpr int kGroupMax = 64;                     // rows per group: at most 4 per warp
-constexpr int kRowsPerWarp = kGroupMax / kWarps;
+constexpr int kGroupMax = 64;                     // rows per group (6-bit row indices)
 constexpr int kChunk = 64;                        // columns per work item
 constexpr int kRowBytes = kChunk * 2;
-constexpr int kBlobHeader = 32;  // words: row0, nrows, flags, ntasks, pad, task table (17)
+constexpr int kBlobHeader = 48;  // words: row0, nrows, flags, ntasks, nsegs, pad, task table (33)
 constexpr int kAccBytes = kGroupMax * kChunk * 4;  // per-row accumulators, one word per column
 constexpr int kStageRowsMax = 768;                // U rows per stage (register-staged indices)
 constexpr int kRowLoads = kStageRowsMax * (kRowBytes / 16) / kThreads;  // 12 per thread
@@ -79,7 +78,7 @@ struct RowIdx {
 };
 
 __device__ __forceinline__ void load_row_idx(const SpStepArgs &a, const UnitDesc &u, RowIdx &ri) {
-    const int pieces = (u.u1 - u.u0) * (kRowBytes / 16);
+    const int pieces = (int)(u.u1 - u.u0) * (kRowBytes / 16);
 #pragma unroll
     for (int j = 0; j < kRowLoads; ++j) {
         const int idx = threadIdx.x + j * kThreads;
@@ -87,14 +86,19 @@ __device__ __forceinline__ void load_row_idx(const SpStepArgs &a, const UnitDesc
     }
 }
 
+__device__ __forceinline__ int unit_chunk(const UnitDesc &u) { return (int)(u.meta & 0xFFFFu); }
+__device__ __forceinline__ bool unit_last(const UnitDesc &u) { return (u.meta >> 31) != 0; }
+__device__ __forceinline__ int unit_bw(const UnitDesc &u) { return (int)((u.meta >> 16) & 0x7FFFu) * 8; }
+
 // All threads stream one unit into buf: its blob, then the 64-column
 // segments of its gathered rows (indices already in registers).
 __device__ __forceinline__ void stage_in(const SpStepArgs &a, const UnitDesc &u,
                                          const RowIdx &ri, uint8_t *buf, size_t blob_bytes) {
     const int tid = threadIdx.x;
-    const uint32_t *bsrc = a.blob + u.bo;
-    for (int c = tid; c < (u.bw >> 2); c += kThreads) cp_async16(buf + (size_t)c * 16, bsrc + 4 * c);
-    const uint16_t *base = a.Bin + (int64_t)u.chunk * kChunk;
+    const uint32_t *bsrc = a.blob + (size_t)u.bo8 * 8;
+    const int bchunks = unit_bw(u) >> 2;
+    for (int c = tid; c < bchunks; c += kThreads) cp_async16(buf + (size_t)c * 16, bsrc + 4 * c);
+    const uint16_t *base = a.Bin + (int64_t)unit_chunk(u) * kChunk;
     uint8_t *rows = buf + blob_bytes;
 #pragma unroll
     for (int j = 0; j < kRowLoads; ++j) {
@@ -105,19 +109,15 @@ __device__ __forceinline__ void stage_in(const SpStepArgs &a, const UnitDesc &u,
     }
 }
 
+// Descriptor k of this CTA, or an empty one (u0 = u1 = 0xFFFFFFFF) past the end.
 __device__ __forceinline__ UnitDesc load_unit(const SpStepArgs &a, int k, int k_end) {
-    UnitDesc u;
     if (k < k_end) {
-        u = a.units[k];
-    } else {
-        u.chunk = -1;
-        u.u0 = u.u1 = u.bw = 0;
-        u.bo = 0;
-        u.last = 0;
-        u.pad = 0;
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.units) + k);
+        return UnitDesc{v.x, v.y, v.z, v.w};
     }
-    return u;
+    return UnitDesc{0u, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u};
 }
+__device__ __forceinline__ bool unit_valid(const UnitDesc &u) { return u.u0 != 0xFFFFFFFFu; }
 
 // Minima of one segment of gathered rows into the accumulators of the
 // cluster rows named by MASK (bit j = row j of the cluster): every gathered
@@ -125,7 +125,7 @@ __device__ __forceinline__ UnitDesc load_unit(const SpStepArgs &a, int k, int k_
 // two values per __vimin3_u16x2.
 template <int MASK>
 __device__ __forceinline__ void gather_min(const uint32_t *ents, const uint8_t *sb, int e0, int e1,
-                                           uint32_t (&m)[3]) {
+                                           uint32_t (&m)[4]) {
 #pragma unroll 2
     for (int e = e0; e < e1; e += 8) {
         const uint4 p = *reinterpret_cast<const uint4 *>(ents + e);
@@ -135,7 +135,7 @@ __device__ __forceinline__ void gather_min(const uint32_t *ents, const uint8_t *
         const uint32_t v4 = lds32(sb + q.x), v5 = lds32(sb + q.y);
         const uint32_t v6 = lds32(sb + q.z), v7 = lds32(sb + q.w);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
+        for (int j = 0; j < 4; ++j) {
             if (MASK & (1 << j)) {
                 m[j] = __vimin3_u16x2(m[j], v0, v1);
                 m[j] = __vimin3_u16x2(m[j], v2, v3);
@@ -172,16 +172,16 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
     stage_in(a, cur, idx, smem, blob_bytes);
     cp_async_commit();
     UnitDesc nxt = load_unit(a, k0 + 1, k_end);
-    if (nxt.chunk >= 0) load_row_idx(a, nxt, idx);
+    if (unit_valid(nxt)) load_row_idx(a, nxt, idx);
     UnitDesc nxt2 = load_unit(a, k0 + 2, k_end);
 
     int32_t dmin = (int32_t)kInf16;
     for (int k = k0; k < k_end; ++k) {
         const int b = (k - k0) & 1;
-        if (nxt.chunk >= 0) {
+        if (unit_valid(nxt)) {
             stage_in(a, nxt, idx, smem + (b ^ 1) * buf_bytes, blob_bytes);
             cp_async_commit();
-            if (nxt2.chunk >= 0) load_row_idx(a, nxt2, idx);
+            if (unit_valid(nxt2)) load_row_idx(a, nxt2, idx);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -198,12 +198,12 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
         const uint16_t *zs = reinterpret_cast<const uint16_t *>(segs + ((2 * nsegs + 7) & ~7));
         const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8;
         const uint8_t *sb = buf + blob_bytes + lane * 4;
-        const int64_t c0 = (int64_t)cur.chunk * kChunk;
+        const int64_t c0 = (int64_t)unit_chunk(cur) * kChunk;
         const int t_end = (int)blob[8 + warp + 1];
         for (int t = (int)blob[8 + warp]; t < t_end; ++t) {
             const uint32_t t0 = tasks[2 * t], t1 = tasks[2 * t + 1];
             const int nr = (int)(t0 >> 24);
-            uint32_t m[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+            uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
             for (int sg = (int)(t1 & 0xFFFFu); sg < (int)(t1 >> 16); ++sg) {
                 const uint32_t s0 = segs[2 * sg];
                 const int e0 = (int)(s0 & 0xFFFFu), mask = (int)(s0 >> 16), e1 = (int)segs[2 * sg + 1];
@@ -215,7 +215,15 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
                         case 4: gather_min<4>(ents, sb, e0, e1, m); break;
                         case 5: gather_min<5>(ents, sb, e0, e1, m); break;
                         case 6: gather_min<6>(ents, sb, e0, e1, m); break;
-                        default: gather_min<7>(ents, sb, e0, e1, m); break;
+                        case 7: gather_min<7>(ents, sb, e0, e1, m); break;
+                        case 8: gather_min<8>(ents, sb, e0, e1, m); break;
+                        case 9: gather_min<9>(ents, sb, e0, e1, m); break;
+                        case 10: gather_min<10>(ents, sb, e0, e1, m); break;
+                        case 11: gather_min<11>(ents, sb, e0, e1, m); break;
+                        case 12: gather_min<12>(ents, sb, e0, e1, m); break;
+                        case 13: gather_min<13>(ents, sb, e0, e1, m); break;
+                        case 14: gather_min<14>(ents, sb, e0, e1, m); break;
+                        default: gather_min<15>(ents, sb, e0, e1, m); break;
                     }
                 } else {
                     // two entries (offset, label pair) per 16-byte read, four per iteration
@@ -233,16 +241,16 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
+            for (int j = 0; j < 4; ++j) {
                 if (j < nr) {
-                    const int r = (int)((t0 >> (8 * j)) & 0xFFu);
+                    const int r = (int)((t0 >> (6 * j)) & 0x3Fu);
                     uint32_t *acc = accs + r * kChunk + 2 * lane;
                     atomicMin(acc, m[j] & 0xFFFFu);
                     atomicMin(acc + 1, m[j] >> 16);
                 }
             }
         }
-        if (cur.last) {
+        if (unit_last(cur)) {
             __syncthreads();
             // write the item's rows: min(INF, .) since the accumulators start at INF
             for (int r = warp; r < nrows; r += kWarps) {
@@ -357,7 +365,7 @@ __global__ void dense_csr_fill_kernel(const int16_t *__restrict__ A, int64_t N,
 // ---------------------------------------------------------------- host side
 
 int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_t> &z,
-                    int cap_rows, int blob_cap, int grid, PlanHost *out) {
+                    int cap_rows, int blob_cap, int grid, PlanHost *out, int cluster_max) {
     const int64_t N = csr.N;
     const int umax = cap_rows - 1;  // the last buffer row is the INF padding row
     if (umax < 1) return set_error(MP_EINVAL, "shared-memory buffer too small");
@@ -378,7 +386,7 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
     auto padded = [&](int64_t cnt) { return (cnt + pad_to - 1) / pad_to * pad_to; };
     auto blob_words = [&](int64_t rows, int64_t entry_words) {
         return (int64_t)kBlobHeader + ((2 * (rows + kWarps) + 7) & ~7) +
-               ((2 * (7 * rows + 2 * kWarps) + 7) & ~7) + ((rows + 15) / 16) * 8 + entry_words;
+               ((2 * (15 * rows + 2 * kWarps) + 7) & ~7) + ((rows + 15) / 16) * 8 + entry_words;
     };
 
     std::vector<int32_t> stamp((size_t)N, -1), local((size_t)N, -1);
@@ -465,7 +473,7 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
                         }
                         return c;
                     };
-                    const int kmax = colconst ? 3 : 1;
+                    const int kmax = colconst ? std::max(1, std::min(4, cluster_max)) : 1;
                     while (!rem.empty()) {
                         std::vector<int> cl{rem.front()};
                         rem.erase(rem.begin());
@@ -501,7 +509,7 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
                         for (size_t t = 0; t < rloc[cl[j]].size(); ++t)
                             all.push_back({rloc[cl[j]][t], {j, rval[cl[j]][t]}});
                     std::sort(all.begin(), all.end());
-                    std::vector<std::vector<std::pair<int32_t, uint32_t>>> bym(8);
+                    std::vector<std::vector<std::pair<int32_t, uint32_t>>> bym(16);
                     for (size_t i = 0; i < all.size();) {
                         size_t k = i;
                         int mask = 0;
@@ -509,7 +517,7 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
                         bym[mask].push_back({all[i].first, all[i].second.second});
                         i = k;
                     }
-                    for (int mask = 1; mask < 8; ++mask) {
+                    for (int mask = 1; mask < 16; ++mask) {
                         auto &v = bym[mask];
                         if (v.empty()) continue;
                         while (v.size() % pad_to) v.push_back({umax, 0u});  // padding row
@@ -580,7 +588,7 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
                         const Task &t = tasks[ti];
                         const auto &cr = cls[t.ci].rows;
                         uint32_t w0 = (uint32_t)cr.size() << 24;
-                        for (int j = 0; j < (int)cr.size(); ++j) w0 |= (uint32_t)cr[j] << (8 * j);
+                        for (int j = 0; j < (int)cr.size(); ++j) w0 |= (uint32_t)cr[j] << (6 * j);
                         ttab[2 * tcount] = w0;
                         ttab[2 * tcount + 1] = (uint32_t)scount | ((uint32_t)(scount + t.segs.size()) << 16);
                         for (auto &sr : t.segs) {
@@ -630,6 +638,8 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
     // Schedule: work items (group, chunk) dealt to the CTAs longest first,
     // each CTA's items then ordered by chunk; a unit per stage of an item.
     P.grid = std::max(1, grid);
+    if (P.nchunks > 0xFFFF || (int64_t)P.blob.size() / 8 > 0xFFFFFFFFll)
+        return set_error(MP_EINVAL, "plan too large for the packed unit descriptors");
     std::vector<int64_t> gcost((size_t)gid, 0);
     for (int gg = 0; gg < gid; ++gg)
         for (int st = P.grp_stage0[gg]; st < P.grp_stage0[gg + 1]; ++st)
@@ -668,13 +678,12 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
         for (auto &it : L)
             for (int st = P.grp_stage0[it.g]; st < P.grp_stage0[it.g + 1]; ++st) {
                 UnitDesc u;
-                u.chunk = it.chunk;
-                u.u0 = P.stage_u0[st];
-                u.u1 = P.stage_u0[st + 1];
-                u.bo = P.blob_off[st];
-                u.bw = (int32_t)(P.blob_off[st + 1] - P.blob_off[st]);
-                u.last = (st + 1 == P.grp_stage0[it.g + 1]) ? 1 : 0;
-                u.pad = 0;
+                const int64_t bw = P.blob_off[st + 1] - P.blob_off[st];
+                const bool last = st + 1 == P.grp_stage0[it.g + 1];
+                u.meta = (uint32_t)it.chunk | ((uint32_t)(bw / 8) << 16) | (last ? 0x80000000u : 0u);
+                u.u0 = (uint32_t)P.stage_u0[st];
+                u.u1 = (uint32_t)P.stage_u0[st + 1];
+                u.bo8 = (uint32_t)(P.blob_off[st] / 8);
                 P.units.push_back(u);
             }
         P.cta_unit0[(size_t)c + 1] = (int32_t)P.units.size();

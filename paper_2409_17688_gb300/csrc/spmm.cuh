@@ -18,14 +18,12 @@ struct DevCsr {
     DevBuf row_ptr, col, val;
 };
 
-// One unit of a CTA's schedule: stage s of work item (group, chunk).
+// One unit of a CTA's schedule: stage s of work item (group, chunk), packed
+// into 16 bytes: meta = chunk (bits 0-15) | blob words / 8 (bits 16-30) |
+// last stage of its item (bit 31); u0, u1 = the stage's rows in urows;
+// bo8 = blob offset in 8-word granules.
 struct UnitDesc {
-    int32_t chunk;  // column chunk (64 columns)
-    int32_t u0, u1; // the stage's rows in urows
-    int32_t bw;     // blob words
-    int64_t bo;     // blob offset (words)
-    int32_t last;   // last stage of its item
-    int32_t pad;
+    uint32_t meta, u0, u1, bo8;
 };
 
 // The gather plan of a sparse A, built once on the host (see spmm.cu).
@@ -65,7 +63,7 @@ struct SpStepArgs {
 };
 
 int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_t> &z,
-                    int cap_rows, int blob_cap, int grid, PlanHost *out);
+                    int cap_rows, int blob_cap, int grid, PlanHost *out, int cluster_max = 3);
 int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent);
 int sparse_cap_rows(int *cap_rows, int *blob_cap, int *grid);
 int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,
