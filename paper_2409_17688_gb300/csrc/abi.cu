@@ -8,6 +8,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <tuple>
 
 #include "mp_internal.cuh"
 #include "spmm.cuh"
@@ -263,16 +264,9 @@ static int transfer_recurrence(int n, int K, Recurrence *out, cudaStream_t s) {
 
 // The transfer chain with slot k-1 of the powers at powers + (k-1)*slot
 // (slot >= N*N elements; the caller may pad slots for alignment).
-int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
-                            int32_t *gdiag_opt, cudaStream_t s) {
-    if (k_max < 1) return set_error(MP_EINVAL, "k_max = %d < 1", k_max);
-    TransferEntry *te;
-    MP_TRY(transfer_entry(n, s, &te));
+static int transfer_chain_direct(TransferEntry *te, int k_max, int16_t *powers_opt, size_t slot,
+                                 int32_t *gdiag_opt, cudaStream_t s) {
     const PlanDev &plan = te->plan;
-    if (slot < (size_t)te->N * (size_t)te->N) return set_error(MP_EINVAL, "slot stride too small");
-    if (powers_opt && gdiag_opt &&
-        ranges_overlap(gdiag_opt, (size_t)k_max * 4, powers_opt, slot * 2 * (size_t)k_max))
-        return set_error(MP_EALIAS, "gdiag overlaps the powers");
     if (gdiag_opt) MP_TRY(launch_fill_i32(gdiag_opt, k_max, (int32_t)kInf16, s));
     DevBuf B;
     MP_TRY(B.alloc(2 * (size_t)plan.N * (size_t)plan.ldb * 2, s));
@@ -280,6 +274,104 @@ int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
     MP_TRY(sparse_init_from_csr(plan, te->csr.row_ptr.as<int64_t>(), te->csr.col.as<int32_t>(),
                                 te->csr.val.as<int16_t>(), B0, powers_opt, gdiag_opt, s));
     return run_sparse_chain(plan, B0, B1, k_max, powers_opt, slot, gdiag_opt, s);
+}
+
+// A chain repeated with the same arguments is captured once into a CUDA
+// graph (the second call) and replayed from then on: one launch instead of
+// k_max + 2, with the steps linked by programmatic dependencies.
+struct ChainKey {
+    int dev, n, k_max;
+    const void *powers, *gdiag;
+    size_t slot;
+    bool operator<(const ChainKey &o) const {
+        return std::tie(dev, n, k_max, powers, gdiag, slot) <
+               std::tie(o.dev, o.n, o.k_max, o.powers, o.gdiag, o.slot);
+    }
+};
+struct ChainGraph {
+    int calls = 0;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last = 0;
+};
+static std::map<ChainKey, ChainGraph> g_chain_graphs;
+static uint64_t g_chain_clock = 0;
+constexpr size_t kChainGraphCap = 32;
+
+int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
+                            int32_t *gdiag_opt, cudaStream_t s) {
+    if (k_max < 1) return set_error(MP_EINVAL, "k_max = %d < 1", k_max);
+    TransferEntry *te;
+    MP_TRY(transfer_entry(n, s, &te));
+    if (slot < (size_t)te->N * (size_t)te->N) return set_error(MP_EINVAL, "slot stride too small");
+    if (powers_opt && gdiag_opt &&
+        ranges_overlap(gdiag_opt, (size_t)k_max * 4, powers_opt, slot * 2 * (size_t)k_max))
+        return set_error(MP_EALIAS, "gdiag overlaps the powers");
+    int dev = -1;
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    const ChainKey key{dev, n, k_max, powers_opt, gdiag_opt, slot};
+    cudaGraphExec_t exec = nullptr;
+    bool capture = false;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_chain_graphs.size() > 8 * kChainGraphCap && !g_chain_graphs.count(key)) {
+            // forget the oldest chain seen once and never captured
+            auto victim = g_chain_graphs.end();
+            for (auto it = g_chain_graphs.begin(); it != g_chain_graphs.end(); ++it)
+                if (!it->second.exec && (victim == g_chain_graphs.end() || it->second.last < victim->second.last))
+                    victim = it;
+            if (victim != g_chain_graphs.end()) g_chain_graphs.erase(victim);
+        }
+        ChainGraph &cg = g_chain_graphs[key];
+        cg.last = ++g_chain_clock;
+        exec = cg.exec;
+        capture = !exec && ++cg.calls >= 2;
+    }
+    // never capture while the caller's stream is itself being captured
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MP_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return transfer_chain_direct(te, k_max, powers_opt, slot, gdiag_opt, s);
+    if (exec) {
+        MP_CUDA_TRY(cudaGraphLaunch(exec, s));
+        return MP_OK;
+    }
+    if (!capture) return transfer_chain_direct(te, k_max, powers_opt, slot, gdiag_opt, s);
+    cudaStream_t cap = nullptr;
+    MP_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    MP_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    const int rc = transfer_chain_direct(te, k_max, powers_opt, slot, gdiag_opt, cap);
+    const cudaError_t ec = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (rc != MP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ec != cudaSuccess) {
+        cudaGetLastError();
+        return transfer_chain_direct(te, k_max, powers_opt, slot, gdiag_opt, s);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        return transfer_chain_direct(te, k_max, powers_opt, slot, gdiag_opt, s);
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_chain_graphs.size() > kChainGraphCap) {
+            auto victim = g_chain_graphs.end();
+            for (auto it = g_chain_graphs.begin(); it != g_chain_graphs.end(); ++it)
+                if (it->second.exec && (victim == g_chain_graphs.end() || it->second.last < victim->second.last))
+                    victim = it;
+            if (victim != g_chain_graphs.end()) {
+                cudaGraphExecDestroy(victim->second.exec);
+                g_chain_graphs.erase(victim);
+            }
+        }
+        g_chain_graphs[key].exec = exec;
+    }
+    MP_CUDA_TRY(cudaGraphLaunch(exec, s));
+    return MP_OK;
 }
 
 static int check_n(int n) {

@@ -169,6 +169,10 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
     UnitDesc cur = load_unit(a, k0, k_end);
     RowIdx idx;
     load_row_idx(a, cur, idx);
+    // Programmatic dependent launch: everything above reads only the plan;
+    // the previous step's output (our input, and the buffer we overwrite)
+    // is touched only after its grid has completed.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     stage_in(a, cur, idx, smem, blob_bytes);
     cp_async_commit();
     UnitDesc nxt = load_unit(a, k0 + 1, k_end);
@@ -281,6 +285,8 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
         for (int o = 16; o > 0; o >>= 1) dmin = min(dmin, __shfl_xor_sync(0xFFFFFFFFu, dmin, o));
         if (lane == 0 && dmin < (int32_t)kInf16) atomicMin(a.gdiag, dmin);
     }
+    // the next step may start its prologue now
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // B0 = P_1 (+ z_row in column-constant mode) in the padded layout, padding
@@ -774,10 +780,20 @@ int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *
                                              (int)di.smem_optin));
         attr_set[kind][di.device] = true;
     }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (p.colconst)
-        sparse_step_kernel<true><<<(unsigned)grid, kThreads, smem, s>>>(a);
+        MP_CUDA_TRY(cudaLaunchKernelEx(&cfg, sparse_step_kernel<true>, a));
     else
-        sparse_step_kernel<false><<<(unsigned)grid, kThreads, smem, s>>>(a);
+        MP_CUDA_TRY(cudaLaunchKernelEx(&cfg, sparse_step_kernel<false>, a));
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

@@ -163,6 +163,26 @@ def test_transfer_chain_every_power(mp, torch, n, kmax):
         assert np.array_equal(Ph[k], Po[k]), k + 1
 
 
+def test_transfer_chain_graph_replay(mp, torch):
+    """The same chain into the same buffers runs directly, then is captured
+    into a CUDA graph, then replayed; every run gives the oracle's powers."""
+    import ctypes
+    n, kmax = 6, 40
+    N = mp.mp_transfer_size(n)
+    P = torch.empty((kmax, N, N), dtype=torch.int16, device="cuda")
+    g = torch.empty(kmax, dtype=torch.int32, device="cuda")
+    Po, go = oracle.power_sequence(oracle.build_transfer(n), kmax, threads=THREADS)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for rep in range(4):
+        P.fill_(0)
+        g.fill_(-1)
+        mp._check(mp.lib().mp_transfer_power_sequence(n, kmax, ctypes.c_void_p(P.data_ptr()),
+                                                      ctypes.c_void_p(g.data_ptr()), s))
+        torch.cuda.synchronize()
+        assert np.array_equal(host(P), Po), rep
+        assert np.array_equal(host(g), go), rep
+
+
 @pytest.mark.parametrize("n", [8, 9])
 def test_transfer_chain_sampled_rows(mp, torch, n):
     """n = 8, 9 with k_max = 200: every power on sampled rows (the oracle's own
