@@ -124,6 +124,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_ranks(ms_local: float, ops_per_step: int, steps: int, world: int):
+    """Replicas: every rank runs the same workload on its own GPU.  The job's
+    time is the slowest rank's (max over ranks) and the value counts the work
+    of all ranks (weak scaling): returns (ms_total, Gop/s)."""
+    ms_total = ms_local
+    if world > 1:
+        import torch
+        t = torch.tensor([ms_local], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    return ms_total, ops_per_step * steps * world / (ms_total * 1e-3) / 1e9
+
+
 def profiled_traffic(summary: str, source: str):
     """DRAM bytes per launch from a committed ncu summary, or None when the
     kernel's source changed since the counters were taken."""
@@ -209,13 +222,8 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
     ms_steps = [a.elapsed_time(b) for a, b in ev]
-    ms_total = sum(ms_steps)
-    if world > 1:
-        t = torch.tensor([ms_total], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total, value = aggregate_ranks(sum(ms_steps), ops_per_step, args.steps, world)
     ms_per_step = ms_total / args.steps
-    value = ops_per_step * args.steps * world / (ms_total * 1e-3) / 1e9
 
     # gamma_2 sanity on the last step (exact closed forms of Section 4, m >= n0)
     g9 = gam[9].numpy()

@@ -145,7 +145,8 @@ int mp_transfer_power_sequence(int n, int k_max, int16_t *powers_opt,
 /* ---- a6: gamma_2 of one cylinder --------------------------------------------
  * Theorem 2: gamma_2(P_n x C_m) = min_i (A^m)_ii, for n >= 1 and m >= 3.
  * Synchronous; *out is a HOST int64.  When the recurrence of n is known
- * (mp_transfer_recurrence, run automatically for n <= 11 and m > 64) the
+ * (mp_transfer_recurrence, run automatically for n <= 11 and m > 64, or
+ * mp_transfer_recurrence_stream for larger n) the
  * answer comes from Theorem 3 for any m.  Otherwise it uses the cached
  * transfer plan and either the chain or repeated squaring
  * S_j = S_{j-1} (x) S_{j-1} followed by a min-trace of the last two factors.
@@ -172,6 +173,16 @@ int mp_gamma2_cylinder(int n, int64_t m, int64_t *out);
  * m >= 3 without the int16 range limit. */
 int mp_diff_const(const int16_t *X, const int16_t *Y, int64_t count, int32_t *out, void *stream);
 int mp_transfer_recurrence(int n, int K, int32_t *out);
+
+/* NEXT f2: the same recurrence for path orders whose K powers do not fit:
+ * the chain keeps only the last `ring` powers and, after each product P_k,
+ * compares P_k with P_{k-a} for a = 1..ring-1 (smallest a first).  The first
+ * constant difference, at k = n0 + a, gives Table 4's n0 with a and b.
+ * out (HOST int32[4]) = {n0, a, b, k}; a = 0 if nothing is found by k_limit.
+ * Synchronous; needs ring*N^2*2 bytes plus two chain buffers (MP_ENOMEM
+ * otherwise).  The result is cached for mp_gamma2_cylinder, which runs this
+ * form itself (k_limit 64, ring 20) for n >= 12. */
+int mp_transfer_recurrence_stream(int n, int k_limit, int ring, int32_t *out);
 
 /* The gamma_2 table of one path order: out[m] = gamma_2(P_n x C_m) for
  * m = 3..k_max (Theorem 2 / Algorithm 5 over the chain), out[0..2] = -1.

@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
         "mp_diag_min": (I, [P, I64, I64, P, P]),
         "mp_diff_const": (I, [P, P, I64, P, P]),
         "mp_transfer_recurrence": (I, [I, I, P]),
+        "mp_transfer_recurrence_stream": (I, [I, I, I, P]),
         "mp_min_trace": (I, [P, P, I64, I64, I64, P, P]),
         "mp_minplus_mul_batched": (I, [P, I, I, P]),
         "mp_batch_prepare": (I, [P, I, P]),
@@ -306,6 +307,13 @@ def mp_transfer_recurrence(n: int, K: int = 50):
     """Algorithms 3 and 4 on the device: (r0, a, b, n0) for A(D_n) over K powers."""
     out = np.zeros(4, dtype=np.int32)
     _check(lib().mp_transfer_recurrence(int(n), int(K), out.ctypes.data))
+    return tuple(int(v) for v in out)
+
+
+def mp_transfer_recurrence_stream(n: int, k_limit: int = 64, ring: int = 20):
+    """Streaming recurrence detection: (n0, a, b, k) with only `ring` powers kept."""
+    out = np.zeros(4, dtype=np.int32)
+    _check(lib().mp_transfer_recurrence_stream(int(n), int(k_limit), int(ring), out.ctypes.data))
     return tuple(int(v) for v in out)
 
 

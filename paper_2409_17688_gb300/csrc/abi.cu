@@ -374,6 +374,63 @@ int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
     return MP_OK;
 }
 
+// Streaming form of Algorithms 3 and 4 for path orders whose K stored powers
+// do not fit: the chain keeps only the last R powers in a ring and, after
+// every product P_k, compares P_k with P_{k-a} for a = 1..R-1 (smallest a
+// first).  The first constant difference, at k = n0 + a, gives the least
+// n0 of Algorithm 4 and the period a with its constant b (Lemma 1 carries
+// it to every later power).
+static int transfer_recurrence_ring(int n, int k_limit, int R, Recurrence *out, cudaStream_t s) {
+    TransferEntry *te;
+    MP_TRY(transfer_entry(n, s, &te));
+    const PlanDev &plan = te->plan;
+    const int64_t N = te->N;
+    const size_t mat = (size_t)N * (size_t)N;
+    size_t free_b = 0, total_b = 0;
+    MP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const double need = (double)mat * 2.0 * R + 4.0 * (double)N * (double)plan.ldb;
+    if (need > 0.9 * (double)free_b)
+        return set_error(MP_ENOMEM, "a ring of %d powers of N = %lld does not fit the free memory", R,
+                         (long long)N);
+    DevBuf ring, g, d, B;
+    MP_TRY(ring.alloc(mat * 2 * (size_t)R, s));
+    MP_TRY(g.alloc(sizeof(int32_t) * (size_t)k_limit, s));
+    MP_TRY(d.alloc(sizeof(int32_t) * 4, s));
+    MP_TRY(B.alloc(2 * (size_t)plan.N * (size_t)plan.ldb * 2, s));
+    uint16_t *buf[2] = {B.as<uint16_t>(), B.as<uint16_t>() + (size_t)plan.N * (size_t)plan.ldb};
+    auto slot = [&](int k) { return ring.as<int16_t>() + (size_t)((k - 1) % R) * mat; };
+    MP_TRY(launch_fill_i32(g.as<int32_t>(), k_limit, (int32_t)kInf16, s));
+    MP_TRY(sparse_init_from_csr(plan, te->csr.row_ptr.as<int64_t>(), te->csr.col.as<int32_t>(),
+                                te->csr.val.as<int16_t>(), buf[0], slot(1), g.as<int32_t>(), s));
+    Recurrence r;
+    bool found = false;
+    for (int k = 2; k <= k_limit && !found; ++k) {
+        MP_TRY(sparse_step(plan, buf[(k - 2) & 1], buf[(k - 1) & 1], slot(k), g.as<int32_t>() + (k - 1), s));
+        for (int a = 1; a < R && a < k; ++a) {
+            bool c;
+            int32_t b;
+            MP_TRY(diff_constant(slot(k), slot(k - a), (int64_t)mat, d.as<int32_t>(), s, &c, &b));
+            if (c) {
+                r.a = a;
+                r.b = b;
+                r.n0 = k - a;
+                r.r0 = k - a;
+                r.K = k;
+                found = true;
+                break;
+            }
+        }
+    }
+    if (found) {
+        r.gdiag.resize((size_t)r.K);
+        MP_CUDA_TRY(cudaMemcpyAsync(r.gdiag.data(), g.p, sizeof(int32_t) * (size_t)r.K,
+                                    cudaMemcpyDeviceToHost, s));
+    }
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = r;
+    return MP_OK;
+}
+
 static int check_n(int n) {
     if (n < 1 || n > MP_MAX_PATH_ORDER)
         return set_error(MP_EINVAL, "path order n = %d outside [1, %d]", n, MP_MAX_PATH_ORDER);
@@ -569,6 +626,29 @@ int mp_transfer_recurrence(int n, int K, int32_t *out) {
     return MP_OK;
 }
 
+int mp_transfer_recurrence_stream(int n, int k_limit, int ring, int32_t *out) {
+    MP_TRY(check_n(n));
+    if (k_limit < 2 || ring < 2 || !out)
+        return set_error(MP_EINVAL, "need k_limit >= 2, ring >= 2 and an output array");
+    if ((int64_t)k_limit * n >= (int64_t)kInf16)
+        return set_error(MP_ERANGE, "k_limit * n reaches the int16 INF code");
+    DeviceState *st;
+    MP_TRY(device_state(&st));
+    Recurrence r;
+    MP_TRY(transfer_recurrence_ring(n, k_limit, ring, &r, st->sync_stream));
+    if (r.a > 0) {
+        int dev = -1;
+        MP_CUDA_TRY(cudaGetDevice(&dev));
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_rec[{dev, n}] = r;
+    }
+    out[0] = r.n0;
+    out[1] = r.a;
+    out[2] = r.b;
+    out[3] = r.K;
+    return MP_OK;
+}
+
 int mp_diag_min(const int16_t *P, int64_t N, int64_t ld, int32_t *out, void *stream) {
     if (!P || !out || N < 0 || ld < N) return set_error(MP_EINVAL, "bad diag_min arguments");
     return launch_diag_min(P, N, ld, out, true, (cudaStream_t)stream);
@@ -603,9 +683,11 @@ int mp_gamma2_cylinder(int n, int64_t m, int64_t *out) {
                 have = true;
             }
         }
-        if (!have && m > 64 && n <= 11) {
+        if (!have && m > 64) {
             int32_t tmp[4];
-            if (mp_transfer_recurrence(n, 50, tmp) == MP_OK) {
+            const int rc = n <= 11 ? mp_transfer_recurrence(n, 50, tmp)
+                                   : mp_transfer_recurrence_stream(n, 64, 20, tmp);
+            if (rc == MP_OK) {
                 std::lock_guard<std::mutex> lk(g_mu);
                 auto it = g_rec.find({dev, n});
                 if (it != g_rec.end()) {

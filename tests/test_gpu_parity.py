@@ -333,6 +333,22 @@ def test_recurrence_tables_3_4(mp, torch, n):
     assert n0 == T4_N0[n]
 
 
+@pytest.mark.parametrize("n", [3, 5, 7, 9, 11, 12])
+def test_recurrence_streaming_table_4(mp, torch, n):
+    """The ring-buffer form finds Table 4's (n0, a, b) keeping only 20
+    powers; for n = 12 (N = 52929, 5.6 GB per power) that is the paper's
+    printed row, which its own GPU reached only through 50 stored powers."""
+    T4 = {3: (7, 6, 8), 5: (31, 7, 15), 7: (23, 18, 53), 9: (22, 3, 11), 11: (24, 3, 13),
+          12: (26, 3, 14)}
+    N = mp.mp_transfer_size(n)
+    free, _ = torch.cuda.mem_get_info()
+    if 23 * N * N * 2 * 1.1 > free:
+        pytest.skip("not enough device memory for the ring")
+    n0, a, b, k = mp.mp_transfer_recurrence_stream(n, 64, 20)
+    assert (n0, a, b) == T4[n]
+    assert k == n0 + a
+
+
 def test_gamma2_any_m_by_recurrence(mp):
     """Theorem 3 answers every m, past the int16 range too: the closed form
     of Section 4 with Table 5's alpha, m from n0 to 10^5."""
