@@ -212,16 +212,22 @@ static int diff_constant(const int16_t *X, const int16_t *Y, int64_t count, int3
 }
 
 // Algorithm 3 over K stored powers of A(D_n), then Algorithm 4.
+static int64_t words_of(int n) {
+    std::vector<uint32_t> w;
+    enumerate_words(n, &w);
+    return (int64_t)w.size();
+}
+
 static int transfer_recurrence(int n, int K, Recurrence *out, cudaStream_t s) {
-    TransferEntry *te;
-    MP_TRY(transfer_entry(n, s, &te));
-    const int64_t N = te->N;
+    const int64_t N = words_of(n);
     const size_t mat = (size_t)N * (size_t)N;
     size_t free_b = 0, total_b = 0;
     MP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     if ((double)mat * 2.0 * (K + 3) > 0.9 * (double)free_b)
         return set_error(MP_ENOMEM, "%d powers of N = %lld do not fit the free device memory", K,
                          (long long)N);
+    TransferEntry *te;
+    MP_TRY(transfer_entry(n, s, &te));
     DevBuf P, g, d;
     MP_TRY(P.alloc(mat * 2 * (size_t)K, s));
     MP_TRY(g.alloc(sizeof(int32_t) * (size_t)K, s));
@@ -381,17 +387,17 @@ int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
 // n0 of Algorithm 4 and the period a with its constant b (Lemma 1 carries
 // it to every later power).
 static int transfer_recurrence_ring(int n, int k_limit, int R, Recurrence *out, cudaStream_t s) {
-    TransferEntry *te;
-    MP_TRY(transfer_entry(n, s, &te));
-    const PlanDev &plan = te->plan;
-    const int64_t N = te->N;
+    const int64_t N = words_of(n);
     const size_t mat = (size_t)N * (size_t)N;
     size_t free_b = 0, total_b = 0;
     MP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    const double need = (double)mat * 2.0 * R + 4.0 * (double)N * (double)plan.ldb;
+    const double need = (double)mat * 2.0 * R + 4.0 * (double)N * (double)(N + 64);
     if (need > 0.9 * (double)free_b)
         return set_error(MP_ENOMEM, "a ring of %d powers of N = %lld does not fit the free memory", R,
                          (long long)N);
+    TransferEntry *te;
+    MP_TRY(transfer_entry(n, s, &te));
+    const PlanDev &plan = te->plan;
     DevBuf ring, g, d, B;
     MP_TRY(ring.alloc(mat * 2 * (size_t)R, s));
     MP_TRY(g.alloc(sizeof(int32_t) * (size_t)k_limit, s));

@@ -450,6 +450,30 @@ def test_autotune_installs_a_valid_table(mp):
         mp.mp_tuning_set(saved)
 
 
+# ----------------------------------------------- failures made on the host
+
+def test_allocation_failures_are_reported(mp, torch):
+    """Requests that cannot fit the device come back as MP_ENOMEM, checked
+    before any kernel runs; the context stays usable afterwards."""
+    free, _ = torch.cuda.mem_get_info()
+    with pytest.raises(mp.MinplusError) as e:
+        mp.mp_transfer_recurrence(12, 200)  # 200 powers of 5.6 GB
+    assert e.value.code in (-3, -4)
+    with pytest.raises(mp.MinplusError) as e:
+        mp.mp_transfer_recurrence_stream(12, 60, int(free // (52929 * 52929 * 2)) + 8)
+    assert e.value.code == -3
+    # a server whose budget cannot hold the path order refuses it
+    srv = mp.Server(hbm_budget=1 << 20, max_batch=8, max_m=100)
+    t = srv.submit(8, 50)
+    with pytest.raises(mp.MinplusError) as e:
+        srv.wait(t)
+    assert e.value.code == -3
+    srv.close()
+    # the device still works
+    assert mp.mp_gamma2_cylinder(4, 5) == 10
+    assert mp.mp_device_status() == 0
+
+
 # --------------------------------------------------------------- misc
 
 def test_dpx_peak_positive(mp):
