@@ -49,7 +49,8 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kGroupMax = 64;                     // rows per group (6-bit row indices)
 constexpr int kChunk = 64;                        // columns per work item
 constexpr int kRowBytes = kChunk * 2;
-constexpr int kBlobHeader = 48;  // words: row0, nrows, flags, ntasks, nsegs, pad, task table (33)
+constexpr int kBlobHeader = 48;  // words: row0, nrows, flags, ntasks, nsegs, 3 pad, per-warp task
+                                 // starts (kWarps + 1), per-warp stream starts (kWarps + 1)
 constexpr int kAccBytes = kGroupMax * kChunk * 4;  // per-row accumulators, one word per column
 constexpr int kStageRowsMax = 768;                // U rows per stage (register-staged indices)
 constexpr int kRowLoads = kStageRowsMax * (kRowBytes / 16) / kThreads;  // 12 per thread
@@ -119,30 +120,67 @@ __device__ __forceinline__ UnitDesc load_unit(const SpStepArgs &a, int k, int k_
 }
 __device__ __forceinline__ bool unit_valid(const UnitDesc &u) { return u.u0 != 0xFFFFFFFFu; }
 
-// Minima of one segment of gathered rows into the accumulators of the
-// cluster rows named by MASK (bit j = row j of the cluster): every gathered
-// value is read once from shared memory and folded into each of those rows,
-// two values per __vimin3_u16x2.
-template <int MASK>
-__device__ __forceinline__ void gather_min(const uint32_t *ents, const uint8_t *sb, int e0, int e1,
-                                           uint32_t (&m)[4]) {
-#pragma unroll 2
-    for (int e = e0; e < e1; e += 8) {
-        const uint4 p = *reinterpret_cast<const uint4 *>(ents + e);
-        const uint4 q = *reinterpret_cast<const uint4 *>(ents + e + 4);
-        const uint32_t v0 = lds32(sb + p.x), v1 = lds32(sb + p.y);
-        const uint32_t v2 = lds32(sb + p.z), v3 = lds32(sb + p.w);
-        const uint32_t v4 = lds32(sb + q.x), v5 = lds32(sb + q.y);
-        const uint32_t v6 = lds32(sb + q.z), v7 = lds32(sb + q.w);
+// Entry words of the column-constant stream: bits 0..16 the byte offset of
+// the gathered row in the row buffer; on the last entry of a segment bit 31
+// is set and bits 17..20 hold the segment's cluster mask; on the last entry
+// of a task bit 30 is set as well.
+constexpr uint32_t kEntOffset = 0x1FFFFu;
+constexpr uint32_t kEntSegEnd = 0x80000000u;
+constexpr uint32_t kEntTaskEnd = 0x40000000u;
+constexpr int kEntMaskShift = 17;
+constexpr int kStreamStart = 8 + kWarps + 1;  // header words: per-warp stream starts
+static_assert(kStreamStart + kWarps < kBlobHeader, "blob header too small");
+
+// Min-folds of the accumulated segment minimum s into the rows the mask names,
+// and at a task end the cluster rows into the shared accumulators.
+__device__ __forceinline__ void seg_end(uint32_t w, uint32_t &s, uint32_t (&m)[4], uint32_t *accs,
+                                        const uint32_t *tasks, int &t, int lane) {
+    const uint32_t mask = w >> kEntMaskShift;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (mask & (1u << j)) m[j] = __vminu2(m[j], s);
+    s = 0xFFFFFFFFu;
+    if (w & kEntTaskEnd) {
+        const uint32_t t0 = tasks[t++];
+        const int nr = (int)(t0 >> 24);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (MASK & (1 << j)) {
-                m[j] = __vimin3_u16x2(m[j], v0, v1);
-                m[j] = __vimin3_u16x2(m[j], v2, v3);
-                m[j] = __vimin3_u16x2(m[j], v4, v5);
-                m[j] = __vimin3_u16x2(m[j], v6, v7);
+            if (j < nr) {
+                uint32_t *acc = accs + (int)((t0 >> (6 * j)) & 0x3Fu) * kChunk + 2 * lane;
+                atomicMin(acc, m[j] & 0xFFFFu);
+                atomicMin(acc + 1, m[j] >> 16);
             }
+            m[j] = 0xFFFFFFFFu;
         }
+    }
+}
+
+// One warp's share of a unit, as one stream of entries [e, e_end) in blocks
+// of eight.  Every entry of a segment feeds the same cluster rows, so the
+// segment is reduced once (__vimin3_u16x2, two values each) and folded into
+// its rows at the segment end: the DPX work per entry does not grow with the
+// rows that share it.  The next block's offsets are read while the current
+// block's rows are loaded.
+__device__ __forceinline__ void warp_stream(uint32_t *accs, const uint32_t *ents, const uint8_t *sb,
+                                            const uint32_t *tasks, int e, int e_end, int t, int lane) {
+    if (e >= e_end) return;
+    const uint4 *e4 = reinterpret_cast<const uint4 *>(ents);
+    uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+    uint32_t s = 0xFFFFFFFFu;
+    uint4 p = e4[e >> 2], q = e4[(e >> 2) + 1];
+    for (; e < e_end; e += 8) {
+        const uint32_t v0 = lds32(sb + p.x), v1 = lds32(sb + p.y), v2 = lds32(sb + p.z);
+        const uint32_t v3 = lds32(sb + (p.w & kEntOffset));
+        const uint32_t v4 = lds32(sb + q.x), v5 = lds32(sb + q.y), v6 = lds32(sb + q.z);
+        const uint32_t v7 = lds32(sb + (q.w & kEntOffset));
+        const uint32_t pw = p.w, qw = q.w;
+        const int en = min(e + 8, e_end - 8);  // the last block re-reads itself
+        p = e4[en >> 2];
+        q = e4[(en >> 2) + 1];
+        s = __vimin3_u16x2(s, __vimin3_u16x2(v0, v1, v2), v3);
+        if (pw & kEntSegEnd) seg_end(pw, s, m, accs, tasks, t, lane);
+        s = __vimin3_u16x2(s, __vimin3_u16x2(v4, v5, v6), v7);
+        if (qw & kEntSegEnd) seg_end(qw, s, m, accs, tasks, t, lane);
     }
 }
 
@@ -198,40 +236,27 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
         const int row0 = (int)blob[0], nrows = (int)blob[1];
         const int ntasks = (int)blob[3], nsegs = (int)blob[4];
         const uint32_t *tasks = blob + kBlobHeader;
-        const uint32_t *segs = tasks + ((2 * ntasks + 7) & ~7);
-        const uint16_t *zs = reinterpret_cast<const uint16_t *>(segs + ((2 * nsegs + 7) & ~7));
-        const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8;
         const uint8_t *sb = buf + blob_bytes + lane * 4;
         const int64_t c0 = (int64_t)unit_chunk(cur) * kChunk;
-        const int t_end = (int)blob[8 + warp + 1];
-        for (int t = (int)blob[8 + warp]; t < t_end; ++t) {
-            const uint32_t t0 = tasks[2 * t], t1 = tasks[2 * t + 1];
-            const int nr = (int)(t0 >> 24);
-            uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-            for (int sg = (int)(t1 & 0xFFFFu); sg < (int)(t1 >> 16); ++sg) {
-                const uint32_t s0 = segs[2 * sg];
-                const int e0 = (int)(s0 & 0xFFFFu), mask = (int)(s0 >> 16), e1 = (int)segs[2 * sg + 1];
-                if (kColConst) {
-                    switch (mask) {
-                        case 1: gather_min<1>(ents, sb, e0, e1, m); break;
-                        case 2: gather_min<2>(ents, sb, e0, e1, m); break;
-                        case 3: gather_min<3>(ents, sb, e0, e1, m); break;
-                        case 4: gather_min<4>(ents, sb, e0, e1, m); break;
-                        case 5: gather_min<5>(ents, sb, e0, e1, m); break;
-                        case 6: gather_min<6>(ents, sb, e0, e1, m); break;
-                        case 7: gather_min<7>(ents, sb, e0, e1, m); break;
-                        case 8: gather_min<8>(ents, sb, e0, e1, m); break;
-                        case 9: gather_min<9>(ents, sb, e0, e1, m); break;
-                        case 10: gather_min<10>(ents, sb, e0, e1, m); break;
-                        case 11: gather_min<11>(ents, sb, e0, e1, m); break;
-                        case 12: gather_min<12>(ents, sb, e0, e1, m); break;
-                        case 13: gather_min<13>(ents, sb, e0, e1, m); break;
-                        case 14: gather_min<14>(ents, sb, e0, e1, m); break;
-                        default: gather_min<15>(ents, sb, e0, e1, m); break;
-                    }
-                } else {
+        const uint16_t *zs;
+        if (kColConst) {
+            // one task word per task, the labels, then every warp's entry
+            // stream (sixteen-byte aligned, a whole number of 8-entry blocks)
+            zs = reinterpret_cast<const uint16_t *>(tasks + ((ntasks + 7) & ~7));
+            const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8;
+            warp_stream(accs, ents, sb, tasks, (int)blob[kStreamStart + warp],
+                        (int)blob[kStreamStart + warp + 1], (int)blob[8 + warp], lane);
+        } else {
+            const uint32_t *segs = tasks + ((2 * ntasks + 7) & ~7);
+            zs = reinterpret_cast<const uint16_t *>(segs + ((2 * nsegs + 7) & ~7));
+            const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8;
+            const int t_end = (int)blob[8 + warp + 1];
+            for (int t = (int)blob[8 + warp]; t < t_end; ++t) {
+                const uint32_t t0 = tasks[2 * t], t1 = tasks[2 * t + 1];
+                uint32_t mm = 0xFFFFFFFFu;
+                for (int sg = (int)(t1 & 0xFFFFu); sg < (int)(t1 >> 16); ++sg) {
+                    const int e0 = (int)(segs[2 * sg] & 0xFFFFu), e1 = (int)segs[2 * sg + 1];
                     // two entries (offset, label pair) per 16-byte read, four per iteration
-                    uint32_t mm = m[0];
 #pragma unroll 2
                     for (int e = e0; e < e1; e += 8) {
                         const uint4 p = *reinterpret_cast<const uint4 *>(ents + e);
@@ -241,17 +266,10 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
                         mm = __viaddmin_u16x2(lds32(sb + q.x), q.y, mm);
                         mm = __viaddmin_u16x2(lds32(sb + q.z), q.w, mm);
                     }
-                    m[0] = mm;
                 }
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (j < nr) {
-                    const int r = (int)((t0 >> (6 * j)) & 0x3Fu);
-                    uint32_t *acc = accs + r * kChunk + 2 * lane;
-                    atomicMin(acc, m[j] & 0xFFFFu);
-                    atomicMin(acc + 1, m[j] >> 16);
-                }
+                uint32_t *acc = accs + (int)(t0 & 0x3Fu) * kChunk + 2 * lane;
+                atomicMin(acc, mm & 0xFFFFu);
+                atomicMin(acc + 1, mm >> 16);
             }
         }
         if (unit_last(cur)) {
@@ -375,6 +393,8 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
     const int64_t N = csr.N;
     const int umax = cap_rows - 1;  // the last buffer row is the INF padding row
     if (umax < 1) return set_error(MP_EINVAL, "shared-memory buffer too small");
+    if ((int64_t)cap_rows * kRowBytes > (int64_t)kEntOffset + 1)
+        return set_error(MP_EINVAL, "%d buffer rows exceed the entry offset field", cap_rows);
     PlanHost &P = *out;
     P = PlanHost();
     P.N = N;
@@ -388,7 +408,8 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
     P.nnz = csr.row_ptr[N];
 
     const int per_entry = colconst ? 1 : 2;  // 32-bit words per entry
-    const int pad_to = colconst ? 8 : 4;     // entries per unrolled iteration
+    const int pad_to = 4;                    // entries per 16-byte index read (or two)
+    const int gran = pad_to * per_entry;     // words a segment's length is a multiple of
     auto padded = [&](int64_t cnt) { return (cnt + pad_to - 1) / pad_to * pad_to; };
     auto blob_words = [&](int64_t rows, int64_t entry_words) {
         return (int64_t)kBlobHeader + ((2 * (rows + kWarps) + 7) & ~7) +
@@ -464,7 +485,8 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
                 }
                 // clusters: with one label per gathered row (column-constant A)
                 // rows whose gather lists overlap share the reads; greedy clusters
-                // of up to 3 rows, each next row the one overlapping most
+                // of up to cluster_max (at most 4) rows, each next row the one
+                // overlapping most
                 std::vector<std::vector<int>> clusters;
                 {
                     std::vector<int> rem;
@@ -554,11 +576,11 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
                         ents.insert(ents.end(), sg.words.begin(), sg.words.end());
                         const int64_t end = (int64_t)ents.size();
                         while (e < end) {
-                            const int64_t take = std::min<int64_t>(end - e, std::max<int64_t>(8, share - cur.len));
-                            const int64_t take8 = (take + 7) / 8 * 8;
-                            cur.segs.push_back({sg.mask, e, std::min(end, e + take8)});
-                            cur.len += std::min(end, e + take8) - e;
-                            e += take8;
+                            const int64_t take = std::min<int64_t>(end - e, std::max<int64_t>(gran, share - cur.len));
+                            const int64_t takeg = (take + gran - 1) / gran * gran;
+                            cur.segs.push_back({sg.mask, e, std::min(end, e + takeg)});
+                            cur.len += std::min(end, e + takeg) - e;
+                            e += takeg;
                             if (cur.len >= share) {
                                 tasks.push_back(cur);
                                 cur = Task{ci, {}, 0};
@@ -585,35 +607,69 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
                 blob[2] = (st == 0 ? 1u : 0u) | (st == nst - 1 ? 2u : 0u);
                 blob[3] = (uint32_t)ntasks;
                 blob[4] = (uint32_t)nsegs;
-                std::vector<uint32_t> ttab((size_t)((2 * ntasks + 7) & ~7), 0u);
-                std::vector<uint32_t> stab((size_t)((2 * nsegs + 7) & ~7), 0u);
-                int tcount = 0, scount = 0;
-                for (int wv = 0; wv < kWarps; ++wv) {
-                    blob[8 + wv] = (uint32_t)tcount;
-                    for (int ti : per_warp[wv]) {
-                        const Task &t = tasks[ti];
-                        const auto &cr = cls[t.ci].rows;
-                        uint32_t w0 = (uint32_t)cr.size() << 24;
-                        for (int j = 0; j < (int)cr.size(); ++j) w0 |= (uint32_t)cr[j] << (6 * j);
-                        ttab[2 * tcount] = w0;
-                        ttab[2 * tcount + 1] = (uint32_t)scount | ((uint32_t)(scount + t.segs.size()) << 16);
-                        for (auto &sr : t.segs) {
-                            stab[2 * scount] = (uint32_t)sr.e0 | ((uint32_t)sr.mask << 16);
-                            stab[2 * scount + 1] = (uint32_t)sr.e1;
-                            ++scount;
-                        }
-                        ++tcount;
-                    }
-                }
-                blob[8 + kWarps] = (uint32_t)tcount;
-                blob.insert(blob.end(), ttab.begin(), ttab.end());
-                blob.insert(blob.end(), stab.begin(), stab.end());
+                auto task_word = [&](const Task &t) {
+                    const auto &cr = cls[t.ci].rows;
+                    uint32_t w0 = (uint32_t)cr.size() << 24;
+                    for (int j = 0; j < (int)cr.size(); ++j) w0 |= (uint32_t)cr[j] << (6 * j);
+                    return w0;
+                };
                 // labels of the group's rows (16-bit), added when a row is written
                 std::vector<uint32_t> zw((size_t)((rows + 15) / 16) * 8, 0u);
                 for (int64_t r = 0; r < rows; ++r)
                     zw[(size_t)(r >> 1)] |= (uint32_t)P.z[(size_t)(g0 + r)] << (16 * (r & 1));
-                blob.insert(blob.end(), zw.begin(), zw.end());
-                blob.insert(blob.end(), ents.begin(), ents.end());
+                int tcount = 0;
+                if (colconst) {
+                    // per warp: its tasks' entries back to back, segment and task
+                    // ends flagged in the last entry word, padded to 8-entry blocks
+                    std::vector<uint32_t> ttab, stream;
+                    for (int wv = 0; wv < kWarps; ++wv) {
+                        blob[8 + wv] = (uint32_t)tcount;
+                        blob[kStreamStart + wv] = (uint32_t)stream.size();
+                        for (int ti : per_warp[wv]) {
+                            const Task &t = tasks[ti];
+                            ttab.push_back(task_word(t));
+                            ++tcount;
+                            for (size_t k = 0; k < t.segs.size(); ++k) {
+                                const SegRef &sr = t.segs[k];
+                                stream.insert(stream.end(), ents.begin() + sr.e0, ents.begin() + sr.e1);
+                                stream.back() |= kEntSegEnd | ((uint32_t)sr.mask << kEntMaskShift) |
+                                                 (k + 1 == t.segs.size() ? kEntTaskEnd : 0u);
+                            }
+                        }
+                        const size_t len = stream.size() - blob[kStreamStart + wv];
+                        if (len % 8) stream.insert(stream.end(), 8 - len % 8, (uint32_t)umax * kRowBytes);
+                    }
+                    blob[8 + kWarps] = (uint32_t)tcount;
+                    blob[kStreamStart + kWarps] = (uint32_t)stream.size();
+                    ttab.resize((size_t)((ntasks + 7) & ~7), 0u);
+                    blob.insert(blob.end(), ttab.begin(), ttab.end());
+                    blob.insert(blob.end(), zw.begin(), zw.end());
+                    blob.insert(blob.end(), stream.begin(), stream.end());
+                } else {
+                    std::vector<uint32_t> ttab((size_t)((2 * ntasks + 7) & ~7), 0u);
+                    std::vector<uint32_t> stab((size_t)((2 * nsegs + 7) & ~7), 0u);
+                    int scount = 0;
+                    for (int wv = 0; wv < kWarps; ++wv) {
+                        blob[8 + wv] = (uint32_t)tcount;
+                        for (int ti : per_warp[wv]) {
+                            const Task &t = tasks[ti];
+                            ttab[2 * tcount] = task_word(t);
+                            ttab[2 * tcount + 1] =
+                                (uint32_t)scount | ((uint32_t)(scount + t.segs.size()) << 16);
+                            for (auto &sr : t.segs) {
+                                stab[2 * scount] = (uint32_t)sr.e0 | ((uint32_t)sr.mask << 16);
+                                stab[2 * scount + 1] = (uint32_t)sr.e1;
+                                ++scount;
+                            }
+                            ++tcount;
+                        }
+                    }
+                    blob[8 + kWarps] = (uint32_t)tcount;
+                    blob.insert(blob.end(), ttab.begin(), ttab.end());
+                    blob.insert(blob.end(), stab.begin(), stab.end());
+                    blob.insert(blob.end(), zw.begin(), zw.end());
+                    blob.insert(blob.end(), ents.begin(), ents.end());
+                }
                 while (blob.size() % 8) blob.push_back(0u);  // 32-byte granules for the copy
                 if ((int64_t)ents.size() > 0xFFFF || nsegs > 0xFFFF)
                     return set_error(MP_EINVAL, "stage entry list of %zu words too long", ents.size());

@@ -63,7 +63,7 @@ struct SpStepArgs {
 };
 
 int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_t> &z,
-                    int cap_rows, int blob_cap, int grid, PlanHost *out, int cluster_max = 3);
+                    int cap_rows, int blob_cap, int grid, PlanHost *out, int cluster_max = 4);
 int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent);
 int sparse_cap_rows(int *cap_rows, int *blob_cap, int *grid);
 int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,

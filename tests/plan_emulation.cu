@@ -1,8 +1,9 @@
 // CPU check of the sparse transfer-step plan (host logic only, no GPU).
 // Builds the plan of A(D_n) with the library's own host code and carries out
-// the kernel's semantics on the CPU: for every unit of every CTA, the tasks
-// of its stage fold the minima of their segments' gathered rows into the
-// row accumulators, and the last stage of an item writes the rows.  The
+// the kernel's semantics on the CPU: for every unit of every CTA, each warp's
+// entry stream is reduced segment by segment, the segment minima are folded
+// into the rows of their cluster masks, finished tasks fold into the row
+// accumulators, and the last stage of an item writes the rows.  The
 // powers P_1..P_k are written to stdout as raw int16 (row-major) so the test
 // can compare them with the oracle.
 //
@@ -95,33 +96,37 @@ int main(int argc, char **argv) {
             const uint32_t *blob = P.blob.data() + (size_t)u.bo8 * 8;
             const int row0 = (int)blob[0], nrows = (int)blob[1], ntasks = (int)blob[3], nsegs = (int)blob[4];
             const uint32_t *tasks = blob + kBlobHeader;
-            const uint32_t *segs = tasks + ((2 * ntasks + 7) & ~7);
-            const uint16_t *zs = reinterpret_cast<const uint16_t *>(segs + ((2 * nsegs + 7) & ~7));
+            const uint16_t *zs = reinterpret_cast<const uint16_t *>(tasks + ((ntasks + 7) & ~7));
             const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8;
-            for (int w = 0; w < kWarps; ++w)
-                for (int t = (int)blob[8 + w]; t < (int)blob[8 + w + 1]; ++t) {
-                    const uint32_t t0 = tasks[2 * t], t1 = tasks[2 * t + 1];
-                    const int nr = (int)(t0 >> 24);
-                    for (int c = 0; c < kChunk; ++c) {
-                        uint32_t m[4] = {0xFFFFu, 0xFFFFu, 0xFFFFu, 0xFFFFu};
-                        for (int sg = (int)(t1 & 0xFFFF); sg < (int)(t1 >> 16); ++sg) {
-                            const uint32_t s0 = segs[2 * sg];
-                            const int e0 = (int)(s0 & 0xFFFF), mask = (int)(s0 >> 16), e1 = (int)segs[2 * sg + 1];
-                            for (int e = e0; e < e1; ++e) {
-                                const int urow = (int)(ents[e] / kRowBytes);
-                                const uint32_t v = urow == P.cap_rows - 1
-                                                       ? 0xFFFFu
-                                                       : B[(int64_t)P.urows[u.u0 + urow] * ldb + chunk * kChunk + c];
-                                for (int j = 0; j < 4; ++j)
-                                    if (mask & (1 << j)) m[j] = std::min(m[j], v);
-                            }
-                        }
-                        for (int j = 0; j < nr; ++j) {
+            (void)nsegs;
+            for (int w = 0; w < kWarps; ++w) {
+                const int e0 = (int)blob[kStreamStart + w], e1 = (int)blob[kStreamStart + w + 1];
+                if ((e1 - e0) % 8 != 0 || (e0 % 4) != 0) return 5;  // whole blocks, 16-byte aligned
+                for (int c = 0; c < kChunk; ++c) {
+                    int t = (int)blob[8 + w];
+                    uint32_t m[4] = {0xFFFFu, 0xFFFFu, 0xFFFFu, 0xFFFFu}, s = 0xFFFFu;
+                    for (int e = e0; e < e1; ++e) {
+                        const uint32_t word = ents[e];
+                        const int urow = (int)((word & kEntOffset) / kRowBytes);
+                        s = std::min(s, urow == P.cap_rows - 1
+                                            ? 0xFFFFu
+                                            : B[(int64_t)P.urows[u.u0 + urow] * ldb + chunk * kChunk + c]);
+                        if (!(word & kEntSegEnd)) continue;
+                        if (e % 4 != 3) return 6;  // ends fall on the last entry of a 16-byte read
+                        for (int j = 0; j < 4; ++j)
+                            if ((word >> kEntMaskShift) & (1u << j)) m[j] = std::min(m[j], s);
+                        s = 0xFFFFu;
+                        if (!(word & kEntTaskEnd)) continue;
+                        const uint32_t t0 = tasks[t++];
+                        for (int j = 0; j < (int)(t0 >> 24); ++j) {
                             const int r = (int)((t0 >> (6 * j)) & 0x3F);
                             acc[(size_t)r * kChunk + c] = std::min(acc[(size_t)r * kChunk + c], m[j]);
+                            m[j] = 0xFFFFu;
                         }
                     }
+                    if (t != (int)blob[8 + w + 1]) return 7;  // every task of the warp ended
                 }
+            }
             if (last)
                 for (int r = 0; r < nrows; ++r)
                     for (int c = 0; c < kChunk; ++c) {
