@@ -73,18 +73,35 @@ __device__ __forceinline__ uint32_t lds32(const uint8_t *p) {
     return *reinterpret_cast<const uint32_t *>(p);
 }
 
-// Row indices of one unit, one register per 16-byte piece this thread copies.
+__device__ __forceinline__ void cp_async16_sh(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint4 lds_v4(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
+// Row offsets of one unit (in 16-byte units of the input power), one
+// register per 16-byte piece this thread copies; ~0u where there is none.
 struct RowIdx {
-    int32_t r[kRowLoads];
+    uint32_t r[kRowLoads];
 };
 
 __device__ __forceinline__ void load_row_idx(const SpStepArgs &a, const UnitDesc &u, RowIdx &ri) {
-    const int pieces = (int)(u.u1 - u.u0) * (kRowBytes / 16);
+    const int nu = (int)(u.u1 - u.u0);
+    const uint32_t *src = a.uoff16 + u.u0 + (threadIdx.x >> 3);
 #pragma unroll
-    for (int j = 0; j < kRowLoads; ++j) {
-        const int idx = threadIdx.x + j * kThreads;
-        ri.r[j] = idx < pieces ? __ldg(a.urows + u.u0 + (idx >> 3)) : -1;
-    }
+    for (int j = 0; j < kRowLoads; ++j)
+        ri.r[j] = (int)(threadIdx.x >> 3) + j * (kThreads / 8) < nu ? __ldg(src + j * (kThreads / 8))
+                                                                     : 0xFFFFFFFFu;
 }
 
 __device__ __forceinline__ int unit_chunk(const UnitDesc &u) { return (int)(u.meta & 0xFFFFu); }
@@ -92,22 +109,20 @@ __device__ __forceinline__ bool unit_last(const UnitDesc &u) { return (u.meta >>
 __device__ __forceinline__ int unit_bw(const UnitDesc &u) { return (int)((u.meta >> 16) & 0x7FFFu) * 8; }
 
 // All threads stream one unit into buf: its blob, then the 64-column
-// segments of its gathered rows (indices already in registers).
+// segments of its gathered rows (offsets already in registers).  Thread t
+// copies piece t % 8 of rows t / 8, t / 8 + 64, ...
 __device__ __forceinline__ void stage_in(const SpStepArgs &a, const UnitDesc &u,
                                          const RowIdx &ri, uint8_t *buf, size_t blob_bytes) {
     const int tid = threadIdx.x;
     const uint32_t *bsrc = a.blob + (size_t)u.bo8 * 8;
     const int bchunks = unit_bw(u) >> 2;
     for (int c = tid; c < bchunks; c += kThreads) cp_async16(buf + (size_t)c * 16, bsrc + 4 * c);
-    const uint16_t *base = a.Bin + (int64_t)unit_chunk(u) * kChunk;
-    uint8_t *rows = buf + blob_bytes;
+    const uint4 *base = reinterpret_cast<const uint4 *>(a.Bin + (int64_t)unit_chunk(u) * kChunk) + (tid & 7);
+    const uint32_t dst = smem_u32(buf + blob_bytes) + (uint32_t)(tid >> 3) * kRowBytes + (tid & 7) * 16;
 #pragma unroll
-    for (int j = 0; j < kRowLoads; ++j) {
-        const int idx = tid + j * kThreads;
-        if (ri.r[j] >= 0)
-            cp_async16(rows + (size_t)(idx >> 3) * kRowBytes + (idx & 7) * 16,
-                       base + (int64_t)ri.r[j] * a.ldb + (idx & 7) * 8);
-    }
+    for (int j = 0; j < kRowLoads; ++j)
+        if (ri.r[j] != 0xFFFFFFFFu)
+            cp_async16_sh(dst + (uint32_t)j * (kThreads / 8) * kRowBytes, base + ri.r[j]);
 }
 
 // Descriptor k of this CTA, or an empty one (u0 = u1 = 0xFFFFFFFF) past the end.
@@ -121,9 +136,10 @@ __device__ __forceinline__ UnitDesc load_unit(const SpStepArgs &a, int k, int k_
 __device__ __forceinline__ bool unit_valid(const UnitDesc &u) { return u.u0 != 0xFFFFFFFFu; }
 
 // Entry words of the column-constant stream: bits 0..16 the byte offset of
-// the gathered row in the row buffer; on the last entry of a segment bit 31
-// is set and bits 17..20 hold the segment's cluster mask; on the last entry
-// of a task bit 30 is set as well.
+// the gathered row in the row buffer.  A segment is a whole number of 8-entry
+// pairs of 4-entry blocks; every entry of its last block has bit 31 set and
+// bits 17..20 = the segment's cluster mask, and bit 30 too when the block
+// also ends a task.
 constexpr uint32_t kEntOffset = 0x1FFFFu;
 constexpr uint32_t kEntSegEnd = 0x80000000u;
 constexpr uint32_t kEntTaskEnd = 0x40000000u;
@@ -131,57 +147,97 @@ constexpr int kEntMaskShift = 17;
 constexpr int kStreamStart = 8 + kWarps + 1;  // header words: per-warp stream starts
 static_assert(kStreamStart + kWarps < kBlobHeader, "blob header too small");
 
-// Min-folds of the accumulated segment minimum s into the rows the mask names,
-// and at a task end the cluster rows into the shared accumulators.
-__device__ __forceinline__ void seg_end(uint32_t w, uint32_t &s, uint32_t (&m)[4], uint32_t *accs,
-                                        const uint32_t *tasks, int &t, int lane) {
+// Lane layout of the stream: quarter qd = lane / 8 takes entry qd of every
+// 4-entry block, and lane l8 = lane % 8 of the quarter holds bytes
+// 16 l8 .. 16 l8 + 15 of the gathered row (columns 8 l8 .. 8 l8 + 7, two per
+// 32-bit word).  One 16-byte shared load per lane reads four gathered rows.
+
+// The four quarters' minima of one cluster row, reduced and scattered so
+// that lane (qd, l8) ends with word qd: columns 8 l8 + 2 qd and + 1.
+__device__ __forceinline__ uint32_t quarter_reduce(const uint32_t (&x)[4], int qd) {
+    const bool hi = qd >= 2;
+    uint32_t k0 = hi ? x[2] : x[0], k1 = hi ? x[3] : x[1];
+    const uint32_t y0 = hi ? x[0] : x[2], y1 = hi ? x[1] : x[3];
+    k0 = __vminu2(k0, __shfl_xor_sync(0xFFFFFFFFu, y0, 16));
+    k1 = __vminu2(k1, __shfl_xor_sync(0xFFFFFFFFu, y1, 16));
+    const bool odd = qd & 1;
+    const uint32_t k = odd ? k1 : k0, y = odd ? k0 : k1;
+    return __vminu2(k, __shfl_xor_sync(0xFFFFFFFFu, y, 8));
+}
+
+// At a segment end: fold the segment minimum s into the cluster rows its mask
+// names; at a task end also fold the cluster rows into the shared
+// accumulators.  Flags and masks are the same in all four entries of a
+// block, so every branch here is warp-uniform.
+__device__ __forceinline__ void seg_end(uint32_t w, uint32_t (&s)[4], uint32_t (&m)[4][4],
+                                        uint32_t *accs, const uint32_t *tasks, int &t, int qd,
+                                        int l8) {
     const uint32_t mask = w >> kEntMaskShift;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-        if (mask & (1u << j)) m[j] = __vminu2(m[j], s);
-    s = 0xFFFFFFFFu;
+        if (mask & (1u << j)) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) m[j][k] = __vminu2(m[j][k], s[k]);
+        }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s[k] = 0xFFFFFFFFu;
     if (w & kEntTaskEnd) {
         const uint32_t t0 = tasks[t++];
         const int nr = (int)(t0 >> 24);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (j < nr) {
-                uint32_t *acc = accs + (int)((t0 >> (6 * j)) & 0x3Fu) * kChunk + 2 * lane;
-                atomicMin(acc, m[j] & 0xFFFFu);
-                atomicMin(acc + 1, m[j] >> 16);
+                const uint32_t x = quarter_reduce(m[j], qd);
+                uint32_t *acc = accs + (int)((t0 >> (6 * j)) & 0x3Fu) * kChunk + 8 * l8 + 2 * qd;
+                atomicMin(acc, x & 0xFFFFu);
+                atomicMin(acc + 1, x >> 16);
             }
-            m[j] = 0xFFFFFFFFu;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) m[j][k] = 0xFFFFFFFFu;
         }
     }
 }
 
-// One warp's share of a unit, as one stream of entries [e, e_end) in blocks
-// of eight.  Every entry of a segment feeds the same cluster rows, so the
-// segment is reduced once (__vimin3_u16x2, two values each) and folded into
-// its rows at the segment end: the DPX work per entry does not grow with the
-// rows that share it.  The next block's offsets are read while the current
-// block's rows are loaded.
-__device__ __forceinline__ void warp_stream(uint32_t *accs, const uint32_t *ents, const uint8_t *sb,
-                                            const uint32_t *tasks, int e, int e_end, int t, int lane) {
+// One warp's share of a unit, as one stream of entries [e, e_end).  A
+// segment is a whole number of 8-entry pairs of blocks and only the second
+// block of a pair can end one, so the inner loop is a tight pass over pairs
+// that exits on that flag.  Every entry of a segment feeds the same cluster
+// rows, so the segment is reduced once (__vimin3_u16x2, two blocks per
+// instruction) and folded into its rows at the segment end: the DPX work per
+// entry does not grow with the rows that share it.  The next pair's entry
+// words are read while the current pair's rows are loaded.
+__device__ __forceinline__ void warp_stream(uint32_t *accs, uint32_t ents_sh, uint32_t rows_sh,
+                                            const uint32_t *tasks, int e, int e_end, int t,
+                                            int lane) {
     if (e >= e_end) return;
-    const uint4 *e4 = reinterpret_cast<const uint4 *>(ents);
-    uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-    uint32_t s = 0xFFFFFFFFu;
-    uint4 p = e4[e >> 2], q = e4[(e >> 2) + 1];
-    for (; e < e_end; e += 8) {
-        const uint32_t v0 = lds32(sb + p.x), v1 = lds32(sb + p.y), v2 = lds32(sb + p.z);
-        const uint32_t v3 = lds32(sb + (p.w & kEntOffset));
-        const uint32_t v4 = lds32(sb + q.x), v5 = lds32(sb + q.y), v6 = lds32(sb + q.z);
-        const uint32_t v7 = lds32(sb + (q.w & kEntOffset));
-        const uint32_t pw = p.w, qw = q.w;
-        const int en = min(e + 8, e_end - 8);  // the last block re-reads itself
-        p = e4[en >> 2];
-        q = e4[(en >> 2) + 1];
-        s = __vimin3_u16x2(s, __vimin3_u16x2(v0, v1, v2), v3);
-        if (pw & kEntSegEnd) seg_end(pw, s, m, accs, tasks, t, lane);
-        s = __vimin3_u16x2(s, __vimin3_u16x2(v4, v5, v6), v7);
-        if (qw & kEntSegEnd) seg_end(qw, s, m, accs, tasks, t, lane);
+    const int qd = lane >> 3, l8 = lane & 7;
+    const uint32_t ib = ents_sh + 4 * qd;  // this quarter's entry of a block
+    const uint32_t rb = rows_sh + 16 * l8;  // this lane's 16 bytes of a gathered row
+    uint32_t m[4][4], s[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        s[k] = 0xFFFFFFFFu;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m[j][k] = 0xFFFFFFFFu;
     }
+    uint32_t w0 = lds_u32(ib + 4 * e), w1 = lds_u32(ib + 4 * e + 16);
+    do {
+        uint32_t f;
+        do {
+            const uint4 d0 = lds_v4(rb + w0);  // first blocks of pairs carry no flags
+            const uint4 d1 = lds_v4(rb + (w1 & kEntOffset));
+            f = w1;
+            e += 8;
+            const int en = min(e, e_end - 8);  // past the end: re-read the last pair
+            w0 = lds_u32(ib + 4 * en);
+            w1 = lds_u32(ib + 4 * en + 16);
+            s[0] = __vimin3_u16x2(s[0], d0.x, d1.x);
+            s[1] = __vimin3_u16x2(s[1], d0.y, d1.y);
+            s[2] = __vimin3_u16x2(s[2], d0.z, d1.z);
+            s[3] = __vimin3_u16x2(s[3], d0.w, d1.w);
+        } while (!(f & kEntSegEnd));
+        seg_end(f, s, m, accs, tasks, t, qd, l8);
+    } while (e < e_end);
 }
 
 template <bool kColConst>
@@ -244,8 +300,9 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
             // stream (sixteen-byte aligned, a whole number of 8-entry blocks)
             zs = reinterpret_cast<const uint16_t *>(tasks + ((ntasks + 7) & ~7));
             const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8;
-            warp_stream(accs, ents, sb, tasks, (int)blob[kStreamStart + warp],
-                        (int)blob[kStreamStart + warp + 1], (int)blob[8 + warp], lane);
+            warp_stream(accs, smem_u32(ents), smem_u32(buf + blob_bytes), tasks,
+                        (int)blob[kStreamStart + warp], (int)blob[kStreamStart + warp + 1],
+                        (int)blob[8 + warp], lane);
         } else {
             const uint32_t *segs = tasks + ((2 * ntasks + 7) & ~7);
             zs = reinterpret_cast<const uint16_t *>(segs + ((2 * nsegs + 7) & ~7));
@@ -275,22 +332,24 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
         if (unit_last(cur)) {
             __syncthreads();
             // write the item's rows: min(INF, .) since the accumulators start at INF
+            const bool diag = a.gdiag != nullptr;
             for (int r = warp; r < nrows; r += kWarps) {
-                uint32_t *acc = accs + r * kChunk + 2 * lane;
-                const uint32_t v = acc[0] | (acc[1] << 16);
-                acc[0] = kInf16;
-                acc[1] = kInf16;
+                uint2 *acc = reinterpret_cast<uint2 *>(accs + r * kChunk + 2 * lane);
+                const uint2 av = *acc;
+                *acc = make_uint2(kInf16, kInf16);
+                const uint32_t v = av.x | (av.y << 16);
                 const int64_t q = row0 + r;
                 const uint32_t keep = kColConst ? v + (uint32_t)zs[r] * 0x10001u : v;
-                *reinterpret_cast<uint32_t *>(a.Bout + q * a.ldb + c0 + 2 * lane) = keep;
-                const int64_t c = c0 + 2 * lane;
+                uint16_t *brow = a.Bout + q * a.ldb + c0;
+                reinterpret_cast<uint32_t *>(brow)[lane] = keep;
                 if (a.user_out) {
+                    const int64_t c = c0 + 2 * lane;
                     int16_t *orow = a.user_out + q * a.N;
                     if (c < a.N) orow[c] = (int16_t)(v & 0xFFFFu);
                     if (c + 1 < a.N) orow[c + 1] = (int16_t)(v >> 16);
                 }
-                if (c == q) dmin = min(dmin, (int32_t)(v & 0xFFFFu));
-                if (c + 1 == q) dmin = min(dmin, (int32_t)(v >> 16));
+                if (diag && q >= c0 && q < c0 + kChunk && (int)(q - c0) >> 1 == lane)
+                    dmin = min(dmin, (int32_t)((q - c0) & 1 ? v >> 16 : v & 0xFFFFu));
             }
         }
         __syncthreads();  // everyone is done with buffer b before it is refilled
@@ -408,7 +467,7 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
     P.nnz = csr.row_ptr[N];
 
     const int per_entry = colconst ? 1 : 2;  // 32-bit words per entry
-    const int pad_to = 4;                    // entries per 16-byte index read (or two)
+    const int pad_to = colconst ? 8 : 4;     // entries per pass of the gather loop
     const int gran = pad_to * per_entry;     // words a segment's length is a multiple of
     auto padded = [&](int64_t cnt) { return (cnt + pad_to - 1) / pad_to * pad_to; };
     auto blob_words = [&](int64_t rows, int64_t entry_words) {
@@ -632,12 +691,11 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
                             for (size_t k = 0; k < t.segs.size(); ++k) {
                                 const SegRef &sr = t.segs[k];
                                 stream.insert(stream.end(), ents.begin() + sr.e0, ents.begin() + sr.e1);
-                                stream.back() |= kEntSegEnd | ((uint32_t)sr.mask << kEntMaskShift) |
-                                                 (k + 1 == t.segs.size() ? kEntTaskEnd : 0u);
+                                const uint32_t f = kEntSegEnd | ((uint32_t)sr.mask << kEntMaskShift) |
+                                                   (k + 1 == t.segs.size() ? kEntTaskEnd : 0u);
+                                for (size_t i = stream.size() - 4; i < stream.size(); ++i) stream[i] |= f;
                             }
                         }
-                        const size_t len = stream.size() - blob[kStreamStart + wv];
-                        if (len % 8) stream.insert(stream.end(), 8 - len % 8, (uint32_t)umax * kRowBytes);
                     }
                     blob[8 + kWarps] = (uint32_t)tcount;
                     blob[kStreamStart + kWarps] = (uint32_t)stream.size();
@@ -772,7 +830,12 @@ int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent) 
     MP_TRY(up(d->stage_u0, h.stage_u0.data(), h.stage_u0.size() * 4));
     MP_TRY(up(d->blob_off, h.blob_off.data(), h.blob_off.size() * 8));
     MP_TRY(up(d->blob, h.blob.data(), h.blob.size() * 4));
-    MP_TRY(up(d->urows, h.urows.data(), h.urows.size() * 4));
+    // the gathered rows as offsets into the padded power, in 16-byte units
+    if ((double)h.N * (double)h.ldb / 8.0 >= 4294967295.0)
+        return set_error(MP_EINVAL, "N = %lld too large for 32-bit row offsets", (long long)h.N);
+    std::vector<uint32_t> uoff(h.urows.size());
+    for (size_t i = 0; i < uoff.size(); ++i) uoff[i] = (uint32_t)((int64_t)h.urows[i] * (h.ldb / 8));
+    MP_TRY(up(d->uoff16, uoff.data(), uoff.size() * 4));
     MP_TRY(up(d->z, h.z.data(), h.z.size() * 2));
     MP_TRY(up(d->units, h.units.data(), h.units.size() * sizeof(UnitDesc)));
     MP_TRY(up(d->cta_unit0, h.cta_unit0.data(), h.cta_unit0.size() * 4));
@@ -807,7 +870,7 @@ int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *
     MP_TRY(device_status_ptr(&status));
     SpStepArgs a;
     memset(&a, 0, sizeof(a));
-    a.urows = p.urows.as<int32_t>();
+    a.uoff16 = p.uoff16.as<uint32_t>();
     a.blob = p.blob.as<uint32_t>();
     a.units = p.units.as<UnitDesc>();
     a.cta_unit0 = p.cta_unit0.as<int32_t>();

@@ -45,11 +45,11 @@ struct PlanDev {
     bool colconst = false;
     size_t h2d_bytes = 0;
     int grid = 0;
-    DevBuf grp_row0, grp_stage0, stage_u0, blob_off, blob, urows, z, units, cta_unit0;
+    DevBuf grp_row0, grp_stage0, stage_u0, blob_off, blob, uoff16, z, units, cta_unit0;
 };
 
 struct SpStepArgs {
-    const int32_t *urows;
+    const uint32_t *uoff16;  // gathered rows: offsets into Bin in 16-byte units
     const uint32_t *blob;
     const UnitDesc *units;
     const int32_t *cta_unit0;

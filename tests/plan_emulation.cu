@@ -105,14 +105,17 @@ int main(int argc, char **argv) {
                 for (int c = 0; c < kChunk; ++c) {
                     int t = (int)blob[8 + w];
                     uint32_t m[4] = {0xFFFFu, 0xFFFFu, 0xFFFFu, 0xFFFFu}, s = 0xFFFFu;
-                    for (int e = e0; e < e1; ++e) {
-                        const uint32_t word = ents[e];
-                        const int urow = (int)((word & kEntOffset) / kRowBytes);
-                        s = std::min(s, urow == P.cap_rows - 1
-                                            ? 0xFFFFu
-                                            : B[(int64_t)P.urows[u.u0 + urow] * ldb + chunk * kChunk + c]);
+                    for (int e = e0; e < e1; e += 4) {  // one 4-entry block per pass
+                        const uint32_t word = ents[e + 3];
+                        for (int i = 0; i < 4; ++i) {
+                            if ((ents[e + i] & ~kEntOffset) != (word & ~kEntOffset)) return 6;
+                            const int urow = (int)((ents[e + i] & kEntOffset) / kRowBytes);
+                            s = std::min(s, urow == P.cap_rows - 1
+                                                ? 0xFFFFu
+                                                : B[(int64_t)P.urows[u.u0 + urow] * ldb + chunk * kChunk + c]);
+                        }
                         if (!(word & kEntSegEnd)) continue;
-                        if (e % 4 != 3) return 6;  // ends fall on the last entry of a 16-byte read
+                        if ((e - e0) % 8 != 4) return 8;  // only the second block of a pair ends a segment
                         for (int j = 0; j < 4; ++j)
                             if ((word >> kEntMaskShift) & (1u << j)) m[j] = std::min(m[j], s);
                         s = 0xFFFFu;
