@@ -165,6 +165,22 @@ __device__ __forceinline__ uint32_t quarter_reduce(const uint32_t (&x)[4], int q
     return __vminu2(k, __shfl_xor_sync(0xFFFFFFFFu, y, 8));
 }
 
+// Cluster rows of a finished task into the shared accumulators: the four
+// quarters' minima are reduced, then two 16-bit atomic minima per lane.
+template <int NR>
+__device__ __forceinline__ void task_flush(uint32_t t0, uint32_t (&m)[4][4], uint32_t *accs,
+                                           int qd, int l8) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const uint32_t x = quarter_reduce(m[j], qd);
+        uint32_t *acc = accs + (int)((t0 >> (6 * j)) & 0x3Fu) * kChunk + 8 * l8 + 2 * qd;
+        atomicMin(acc, x & 0xFFFFu);
+        atomicMin(acc + 1, x >> 16);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) m[j][k] = 0xFFFFFFFFu;
+    }
+}
+
 // At a segment end: fold the segment minimum s into the cluster rows its mask
 // names; at a task end also fold the cluster rows into the shared
 // accumulators.  Flags and masks are the same in all four entries of a
@@ -183,18 +199,11 @@ __device__ __forceinline__ void seg_end(uint32_t w, uint32_t (&s)[4], uint32_t (
     for (int k = 0; k < 4; ++k) s[k] = 0xFFFFFFFFu;
     if (w & kEntTaskEnd) {
         const uint32_t t0 = tasks[t++];
-        const int nr = (int)(t0 >> 24);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (j < nr) {
-                const uint32_t x = quarter_reduce(m[j], qd);
-                uint32_t *acc = accs + (int)((t0 >> (6 * j)) & 0x3Fu) * kChunk + 8 * l8 + 2 * qd;
-                atomicMin(acc, x & 0xFFFFu);
-                atomicMin(acc + 1, x >> 16);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) m[j][k] = 0xFFFFFFFFu;
-        }
+        const uint32_t nr = t0 >> 24;
+        if (nr == 1) task_flush<1>(t0, m, accs, qd, l8);
+        else if (nr == 2) task_flush<2>(t0, m, accs, qd, l8);
+        else if (nr == 3) task_flush<3>(t0, m, accs, qd, l8);
+        else task_flush<4>(t0, m, accs, qd, l8);
     }
 }
 
