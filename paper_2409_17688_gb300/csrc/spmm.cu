@@ -11,28 +11,37 @@
 // __vimin3_u16x2.  Any other sparse A takes per-entry __viaddmin_u16x2.
 //
 // Work decomposition.  Output rows are grouped greedily (consecutive rows,
-// at most 64) so that the union U of the rows they gather stays small; the
-// columns are cut into chunks of 64.  A work item is (group, chunk); a U
-// list longer than one buffer is cut into stages whose per-row minima carry
-// over in registers.  A persistent CTA (one per SM, 16 warps) walks its
-// items through two shared-memory buffers.  While it computes one stage,
-// all its threads stream the next stage into the other buffer with 16-byte
-// cp.async copies: the 128-byte segments (64 columns) of the U rows, and
-// one contiguous "blob" holding the stage's row range and per-row entry
-// lists (32-bit shared-memory byte offsets of the gathered rows).  The plan
-// cuts every stage into tasks -- a row, or a segment of a long row -- and
-// deals them to the 16 warps longest first, so no warp carries much more
-// than its share (row lengths range from 8 to 2^n entries).  A task folds
-// its minimum into the row's accumulator in shared memory with 32-bit
-// shared-memory atomicMin; after the last stage of an item one pass writes
-// the rows out.  The 32 lanes of a warp own the 64 columns as 16-bit
-// pairs, so every read of a gathered row is one conflict-free 128-byte
-// wavefront and every entry read is a broadcast.
+// at most 64) so that the union U of the rows they gather fits one shared
+// buffer; the columns are cut into chunks of 64.  A work item is (group,
+// chunk); a U list longer than one buffer is cut into stages whose per-row
+// minima carry over in shared accumulators.  A persistent CTA (one per SM,
+// 16 warps) walks its schedule of units (a stage of an item) through two
+// shared-memory buffers: while it computes one unit, all threads stream the
+// next into the other buffer with 16-byte cp.async copies -- the 128-byte
+// segments of the U rows (from 32-bit row offsets precomputed on the host)
+// and one "blob" with the unit's task table, row labels and entry streams.
+//
+// Column-constant A (the transfer matrix).  Rows of a group are clustered
+// (up to four rows whose gather lists overlap most); a cluster's union is
+// split by membership mask into segments, so every gathered row of a
+// segment feeds the same cluster rows.  A segment is reduced once and its
+// minimum folded into the rows its mask names: rows that share a gathered
+// row share its read and its min.  The unit's clusters, laid out one after
+// another, are cut into 16 contiguous ranges of equal modelled cost, one per
+// warp; a cluster cut in two becomes two tasks.  Each warp walks its range as
+// one stream of entry words (row offset plus segment and task flags); its
+// four quarter-warps take one entry each, so one 16-byte shared load per
+// lane reads four gathered rows.  At a task end the quarters' minima are
+// combined with shuffles and folded into the rows' shared accumulators with
+// atomicMin; after the last stage of an item one pass writes the rows out.
+// A general sparse A keeps one row per task and per-entry labels.
 // (1-D TMA bulk copies were tried first for the row segments: at 128 bytes
 // each they issued far too slowly to feed the arithmetic.)
 // Rows of the next power go to a padded internal buffer (and, when asked,
 // to the caller's power array); the diagonal entries are min-reduced in
-// registers and folded into g[k] with one atomicMin per warp.
+// registers and folded into g[k] with one atomicMin per warp.  Steps are
+// chained with programmatic dependent launch: a step's prologue (reading
+// only the plan) overlaps the previous step's tail.
 #include <algorithm>
 #include <cstring>
 #include <iterator>
@@ -480,6 +489,9 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
     const int gran = pad_to * per_entry;     // words a segment's length is a multiple of
     auto padded = [&](int64_t cnt) { return (cnt + pad_to - 1) / pad_to * pad_to; };
     auto blob_words = [&](int64_t rows, int64_t entry_words) {
+        if (colconst)  // task words, labels, entry streams
+            return (int64_t)kBlobHeader + ((rows + kWarps + 7) & ~7) + ((rows + 15) / 16) * 8 +
+                   entry_words;
         return (int64_t)kBlobHeader + ((2 * (rows + kWarps) + 7) & ~7) +
                ((2 * (15 * rows + 2 * kWarps) + 7) & ~7) + ((rows + 15) / 16) * 8 + entry_words;
     };
@@ -628,43 +640,56 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
                     }
                     cls.push_back(std::move(c));
                 }
-                // entries laid out cluster by cluster; tasks = clusters, long ones cut
-                // into pieces of about a warp's share, dealt to warps longest first
-                int64_t words = 0;
-                for (auto &c : cls) words += c.words;
-                const int64_t share = std::max<int64_t>(8, (words / kWarps + 7) / 8 * 8);
+                // Entries laid out cluster by cluster, and that sequence cut into
+                // at most kWarps contiguous ranges of equal cost, one per warp: a
+                // cluster that straddles a cut becomes two tasks.  A range's cost counts, besides its entry words, the
+                // work at each segment end and at each task end, in entry words.
+                const int64_t seg_cost = 12 * per_entry, task_cost = 32 * per_entry;
+                int64_t total = 0;
+                for (auto &c : cls) total += c.words + seg_cost * (int64_t)c.segs.size() + task_cost;
                 struct SegRef { int mask; int64_t e0, e1; };
                 struct Task { int ci; std::vector<SegRef> segs; int64_t len; };
                 std::vector<Task> tasks;
                 std::vector<uint32_t> ents;
+                std::vector<std::vector<int>> per_warp(kWarps);
+                // each cut adds a task end and a segment end; small units use
+                // fewer warps so that a range costs at least twice that
+                const int64_t cut_cost = task_cost + seg_cost;
+                int nw = kWarps;
+                while (nw > 1 && total + (nw - 1) * cut_cost < 2 * cut_cost * nw) --nw;
+                const int64_t whole = total + (nw - 1) * cut_cost;
+                int cw = 0;
+                int64_t spent = 0;
+                auto bound = [&](int w) { return (w + 1) * whole / nw; };
                 for (int ci = 0; ci < (int)cls.size(); ++ci) {
                     Task cur{ci, {}, 0};
+                    spent += task_cost;
                     for (auto &sg : cls[ci].segs) {
                         int64_t e = (int64_t)ents.size();
                         ents.insert(ents.end(), sg.words.begin(), sg.words.end());
                         const int64_t end = (int64_t)ents.size();
                         while (e < end) {
-                            const int64_t take = std::min<int64_t>(end - e, std::max<int64_t>(gran, share - cur.len));
-                            const int64_t takeg = (take + gran - 1) / gran * gran;
-                            cur.segs.push_back({sg.mask, e, std::min(end, e + takeg)});
-                            cur.len += std::min(end, e + takeg) - e;
-                            e += takeg;
-                            if (cur.len >= share) {
+                            int64_t take = end - e;
+                            if (cw < nw - 1) {
+                                const int64_t room = bound(cw) - spent - seg_cost;
+                                take = std::min(take, std::max<int64_t>(gran, (room + gran - 1) / gran * gran));
+                            }
+                            cur.segs.push_back({sg.mask, e, e + take});
+                            cur.len += take;
+                            spent += take + seg_cost;
+                            e += take;
+                            if (cw < nw - 1 && spent >= bound(cw)) {
                                 tasks.push_back(cur);
+                                per_warp[cw++].push_back((int)tasks.size() - 1);
                                 cur = Task{ci, {}, 0};
+                                spent += task_cost;
                             }
                         }
                     }
-                    if (!cur.segs.empty()) tasks.push_back(cur);
-                }
-                std::stable_sort(tasks.begin(), tasks.end(),
-                                 [](const Task &x, const Task &y) { return x.len > y.len; });
-                std::vector<std::vector<int>> per_warp(kWarps);
-                std::vector<int64_t> load(kWarps, 0);
-                for (int ti = 0; ti < (int)tasks.size(); ++ti) {
-                    const int wsel = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-                    per_warp[wsel].push_back(ti);
-                    load[wsel] += tasks[ti].len;
+                    if (!cur.segs.empty()) {
+                        tasks.push_back(cur);
+                        per_warp[cw].push_back((int)tasks.size() - 1);
+                    }
                 }
                 int nsegs = 0;
                 for (auto &t : tasks) nsegs += (int)t.segs.size();
@@ -858,10 +883,10 @@ int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent) 
 int sparse_cap_rows(int *cap_rows, int *blob_cap, int *grid) {
     DeviceInfo di;
     MP_TRY(device_info(&di));
-    // one CTA per SM; two buffers, each a 24 KiB blob region plus cap_rows
+    // one CTA per SM; two buffers, each a 16 KiB blob region plus cap_rows
     // gathered row segments of 128 B (at most kStageRowsMax + the padding
     // row), and the 16 KiB of per-row accumulators
-    const int blob = 6144;
+    const int blob = 4096;
     const size_t budget = di.smem_optin - 1024 - kAccBytes - 2 * (size_t)blob * 4;
     int cap = (int)(budget / (2 * (size_t)kRowBytes));
     if (cap > kStageRowsMax + 1) cap = kStageRowsMax + 1;
