@@ -107,6 +107,53 @@ def test_example1_p4_c5(brute):
     assert g == brute(4, 5) == 10
 
 
+def _subset_pair_gamma2(n, mmax):
+    """gamma_2(P_n x C_m), m = 3..mmax, from a second transfer construction
+    that shares nothing with the paper's words: a state is the pair
+    (D_prev, D_cur) of column subsets in the dominating set, a step to
+    (D_cur, D_next) is allowed when every vertex of the current column outside
+    D_cur has at least two neighbours in D (up and down in D_cur, left in
+    D_prev, right in D_next), and it costs |D_next|.  A 2-dominating set of
+    the cylinder is a closed walk of m steps, so gamma_2 is the least diagonal
+    entry of the m-th (min,+) power."""
+    S = 1 << n
+    big = 1 << 20
+    pop = np.array([bin(d).count("1") for d in range(S)], dtype=np.int64)
+    cover_ok = np.zeros((S, S, S), dtype=bool)  # [prev, cur, next]
+    for prev, cur, nxt in itertools.product(range(S), repeat=3):
+        ok = True
+        for r in range(n):
+            if cur >> r & 1:
+                continue
+            cnt = (prev >> r & 1) + (nxt >> r & 1)
+            cnt += (r > 0 and cur >> (r - 1) & 1) + (r < n - 1 and cur >> (r + 1) & 1)
+            if cnt < 2:
+                ok = False
+                break
+        cover_ok[prev, cur, nxt] = ok
+    B = np.full((S * S, S * S), big, dtype=np.int64)
+    for prev, cur, nxt in zip(*np.nonzero(cover_ok)):
+        B[prev * S + cur, cur * S + nxt] = pop[nxt]
+    out, P = {}, B.copy()
+    for m in range(2, mmax + 1):
+        P = np.min(P[:, :, None] + B[None, :, :], axis=1) if S <= 8 else \
+            np.stack([np.min(P[i][:, None] + B, axis=0) for i in range(S * S)])
+        np.minimum(P, big, out=P)
+        if m >= 3:
+            out[m] = int(P.diagonal().min())
+    return out
+
+
+@pytest.mark.parametrize("n,mmax", [(1, 12), (2, 12), (3, 12), (4, 10), (5, 6)])
+def test_subset_pair_construction(n, mmax):
+    """The oracle's gamma_2 (the paper's correct words and arc rules, Section
+    2.2, with Theorem 2) equals the subset-pair transfer construction."""
+    want = _subset_pair_gamma2(n, mmax)
+    got = oracle.gamma2_range(n, mmax)
+    for m in range(3, mmax + 1):
+        assert got[m] == want[m], (n, m)
+
+
 def test_cycle_closed_form():
     """Path order 1 is the cycle C_m, whose 2-domination number is ceil(m/2)."""
     g = oracle.gamma2_range(1, 60)
