@@ -153,6 +153,18 @@ def profiled_traffic(summary: str, source: str):
     return int(fields["traffic_bytes_per_launch"])
 
 
+def hbm_frac(bytes_per_s: float):
+    """Algorithmic bytes/s of a launch against the measured copy bandwidth:
+    the memory side of the roofline, reported to show that it does not bind."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["hbm_gbs"]) * 1e9
+    except (OSError, ValueError, KeyError):
+        return None
+    return {"achieved_gbs": round(bytes_per_s / 1e9, 1), "peak_gbs": round(peak / 1e9, 1),
+            "frac": round(bytes_per_s / peak, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -266,6 +278,7 @@ def run_ours(args):
                                             "paper_2409_17688_gb300/csrc/spmm.cu"),
                 "traffic_unit": "bytes per launch (ncu dram read+write, cold cache)",
                 "algorithmic_bytes": 4 * Ns[9] * Ns[9],
+                "hbm_frac": hbm_frac(4 * Ns[9] * Ns[9] / (step_ms * 1e-3)),
                 "peak_source": "K6 __vimin3_u16x2 rate measured in this run (4 terms/instr)",
                 "launch_us": round(step_ms * 1e3, 2)}
 
