@@ -143,6 +143,12 @@ def mp_build_transfer_matrix(n: int, A=None, words: bool = False, stream=None):
 
 # --------------------------------------------------------------- products
 
+def _ld(t) -> int:
+    """Leading dimension (elements) of a row-major 2-D tensor; an empty
+    tensor reports stride 0, so its row length stands in."""
+    return int(t.stride(0)) if t.numel() else max(int(t.shape[1]), 1)
+
+
 def mp_minplus_mul(X, Y, Z=None, stream=None):
     """Z = X (x) Y, exact and saturating; int16 (INF 0x7FFF) or uint8 (INF 255)."""
     import torch
@@ -154,8 +160,8 @@ def mp_minplus_mul(X, Y, Z=None, stream=None):
     if Z is None:
         Z = torch.empty((M, N), dtype=X.dtype, device=X.device)
     assert Z.dtype == X.dtype and Z.stride(1) == 1
-    _check(lib().mp_minplus_mul(_dev(X), _dev(Y), _dev(Z), M, N, K, max(X.stride(0), 1),
-                                max(Y.stride(0), 1), max(Z.stride(0), 1), dtype, _stream(stream)))
+    _check(lib().mp_minplus_mul(_dev(X), _dev(Y), _dev(Z), M, N, K, _ld(X), _ld(Y), _ld(Z),
+                                dtype, _stream(stream)))
     return Z
 
 
@@ -166,8 +172,7 @@ def mp_minplus_mul_batched(problems, mode: int = 0, stream=None):
     for i, (X, Y, Z) in enumerate(problems):
         dtype = {torch.int16: MP_I16, torch.uint8: MP_U8}[X.dtype]
         arr[i] = mp_problem(X.data_ptr(), Y.data_ptr(), Z.data_ptr(), X.shape[0], Y.shape[1],
-                            X.shape[1], max(X.stride(0), 1), max(Y.stride(0), 1),
-                            max(Z.stride(0), 1), dtype, 0)
+                            X.shape[1], _ld(X), _ld(Y), _ld(Z), dtype, 0)
     _check(lib().mp_minplus_mul_batched(ctypes.cast(arr, ctypes.c_void_p), len(problems),
                                         int(mode), _stream(stream)))
 
@@ -182,8 +187,7 @@ class Batch:
         for i, (X, Y, Z) in enumerate(problems):
             dtype = {torch.int16: MP_I16, torch.uint8: MP_U8}[X.dtype]
             arr[i] = mp_problem(X.data_ptr(), Y.data_ptr(), Z.data_ptr(), X.shape[0], Y.shape[1],
-                                X.shape[1], max(X.stride(0), 1), max(Y.stride(0), 1),
-                                max(Z.stride(0), 1), dtype, 0)
+                                X.shape[1], _ld(X), _ld(Y), _ld(Z), dtype, 0)
         h = ctypes.c_void_p()
         _check(lib().mp_batch_prepare(ctypes.cast(arr, ctypes.c_void_p), len(problems),
                                       ctypes.byref(h)))

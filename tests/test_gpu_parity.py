@@ -384,6 +384,70 @@ def test_batched_matches_single(mp, torch, mode):
         assert np.array_equal(host(Zd), w)
 
 
+def test_batched_empty_and_rectangular(mp, torch):
+    """Degenerate and rectangular products in one persistent launch: M = 0
+    (nothing written), K = 0 (all INF), 1 x 1, and non-square shapes that
+    leave ragged tiles in every dimension; an empty batch is a no-op."""
+    mp.mp_minplus_mul_batched([])
+    shapes = [(0, 5, 7, np.int16), (6, 0, 9, np.int16), (1, 1, 1, np.uint8),
+              (130, 70, 300, np.int16), (257, 129, 65, np.uint8), (64, 1000, 3, np.int16)]
+    probs, want = [], []
+    for i, (M, K, N, dt) in enumerate(shapes):
+        X = synth.entry_inf_matrix(M, K, 300 + i, dt, inf_frac=0.2)
+        Y = synth.entry_inf_matrix(K, N, 400 + i, dt, inf_frac=0.2)
+        Zd = torch.full((M, N), 7, dtype=torch.int16 if dt == np.int16 else torch.uint8,
+                        device="cuda")
+        probs.append((to_dev(torch, X), to_dev(torch, Y), Zd))
+        want.append(oracle.minplus_mul(X, Y, threads=THREADS) if M and N else None)
+    for mode in (0, 1):
+        for _, _, Zd in probs:
+            Zd.fill_(7)
+        mp.mp_minplus_mul_batched(probs, mode=mode)
+        torch.cuda.synchronize()
+        for (_, _, Zd), w in zip(probs, want):
+            if w is not None:
+                assert np.array_equal(host(Zd), w), (mode, Zd.shape)
+    assert np.all(host(probs[1][2]) == INF)  # K = 0: every entry is an empty minimum
+
+
+@pytest.mark.slow
+def test_batched_full_workload_sampled(mp, torch):
+    """The bench's batched workload at full size (96 square products, N
+    log-uniform in [64, 8192], 30% INF 128-blocks, the same seeds), run the
+    way it is timed: autotuned tile table, one persistent launch captured in
+    a CUDA graph and replayed.  Three rows of every product (first, last and
+    one drawn) equal the oracle's product of those rows with Y."""
+    sizes = synth.batch_sizes(96, 64, 8192, seed=7)
+    probs, hosts = [], []
+    for i, N in enumerate(sizes):
+        X = synth.block_inf_matrix(N, N, 1000 + 2 * i, np.int16, inf_frac=0.3)
+        Y = synth.block_inf_matrix(N, N, 1001 + 2 * i, np.int16, inf_frac=0.3)
+        Xd = to_dev(torch, X)
+        probs.append((Xd, to_dev(torch, Y), torch.full_like(Xd, 5)))
+        hosts.append((X, Y))
+    mp.mp_autotune()
+    batch = mp.Batch(probs)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        batch.run(0)
+    torch.cuda.synchronize()
+    for _, _, Zd in probs:
+        Zd.fill_(5)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        batch.run(0, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    rng = np.random.Generator(np.random.PCG64(99))
+    for (X, Y), (_, _, Zd) in zip(hosts, probs):
+        N = X.shape[0]
+        rows = sorted({0, N - 1, int(rng.integers(0, N))})
+        got = host(Zd[rows])
+        for j, r in enumerate(rows):
+            assert np.array_equal(got[j], oracle.minplus_mul(X[r:r + 1], Y, threads=THREADS)[0]), (N, r)
+    del batch
+
+
 def test_batched_alias_rejected(mp, torch):
     X = torch.zeros((64, 64), dtype=torch.int16, device="cuda")
     Z = torch.zeros((64, 64), dtype=torch.int16, device="cuda")
