@@ -218,11 +218,26 @@ static int64_t words_of(int n) {
     return (int64_t)w.size();
 }
 
+// Free device memory for a large request: buffers of earlier calls were
+// released stream-ordered into the device's memory pool, which keeps them
+// reserved until it is trimmed, so wait for the stream and trim first.
+static int device_free_bytes(cudaStream_t s, size_t *free_b) {
+    int dev = 0;
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    MP_CUDA_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool = nullptr;
+    MP_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    MP_CUDA_TRY(cudaMemPoolTrimTo(pool, 0));
+    size_t total_b = 0;
+    MP_CUDA_TRY(cudaMemGetInfo(free_b, &total_b));
+    return MP_OK;
+}
+
 static int transfer_recurrence(int n, int K, Recurrence *out, cudaStream_t s) {
     const int64_t N = words_of(n);
     const size_t mat = (size_t)N * (size_t)N;
-    size_t free_b = 0, total_b = 0;
-    MP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    size_t free_b = 0;
+    MP_TRY(device_free_bytes(s, &free_b));
     if ((double)mat * 2.0 * (K + 3) > 0.9 * (double)free_b)
         return set_error(MP_ENOMEM, "%d powers of N = %lld do not fit the free device memory", K,
                          (long long)N);
@@ -389,8 +404,8 @@ int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
 static int transfer_recurrence_ring(int n, int k_limit, int R, Recurrence *out, cudaStream_t s) {
     const int64_t N = words_of(n);
     const size_t mat = (size_t)N * (size_t)N;
-    size_t free_b = 0, total_b = 0;
-    MP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    size_t free_b = 0;
+    MP_TRY(device_free_bytes(s, &free_b));
     const double need = (double)mat * 2.0 * R + 4.0 * (double)N * (double)(N + 64);
     if (need > 0.9 * (double)free_b)
         return set_error(MP_ENOMEM, "a ring of %d powers of N = %lld does not fit the free memory", R,

@@ -349,6 +349,44 @@ def test_recurrence_streaming_table_4(mp, torch, n):
     assert k == n0 + a
 
 
+def test_recurrence_stream_twice_with_large_ring(mp, torch):
+    """Two streaming detections back to back whose ring takes most of the
+    free memory: the first call's buffers go back to the device's memory pool
+    and must not make the second call's memory check fail."""
+    N = mp.mp_transfer_size(12)
+    free, _ = torch.cuda.mem_get_info()
+    R = int(0.6 * free / (N * N * 2))
+    if R < 4:
+        pytest.skip("not enough device memory")
+    for _ in range(2):
+        n0, a, b, k = mp.mp_transfer_recurrence_stream(12, 40, R)
+        assert (n0, a, b) == (26, 3, 14)
+
+
+@pytest.mark.slow
+def test_path_order_13_conjecture(mp, torch):
+    """Path order 13 (N = 131562, 34.6 GB per power), which the paper could
+    not fit: the ring-buffer detector keeps four powers and the two chain
+    buffers (about 208 GB).  Pins are the paper's statements: its conjecture
+    (Section 5) gamma_2(P_n x C_m) = (n + 2) m / 3 for n >= 8 and m = 0 mod 3,
+    the C_5 formula 2n + 1 for odd n (Section 4), and so the period's slope
+    b / a = (n + 2) / 3.  About three minutes; runs with MP_PATH_ORDER_13=1."""
+    if os.environ.get("MP_PATH_ORDER_13") != "1":
+        pytest.skip("set MP_PATH_ORDER_13=1 to run the path-order-13 detection")
+    torch.cuda.empty_cache()
+    try:
+        n0, a, b, k = mp.mp_transfer_recurrence_stream(13, 64, 4)
+    except mp.MinplusError as e:
+        if e.code == -3:
+            pytest.skip("not enough free device memory for four powers of N = 131562")
+        raise
+    assert a > 0 and k == n0 + a
+    assert 3 * b == 15 * a
+    assert mp.mp_gamma2_cylinder(13, 5) == 27
+    for m in range(3, 3001, 3):
+        assert mp.mp_gamma2_cylinder(13, m) == 5 * m, m
+
+
 def test_gamma2_any_m_by_recurrence(mp):
     """Theorem 3 answers every m, past the int16 range too: the closed form
     of Section 4 with Table 5's alpha, m from n0 to 10^5."""
