@@ -42,15 +42,23 @@ __device__ __forceinline__ uint32_t dup16(uint32_t v) { return v | (v << 16); }
 
 // Occupancy mask: mask[bi * nbc + bj] = 1 when the 128 x 128 block (bi, bj)
 // holds at least one finite entry.
+// When dst is given the block is also copied there (leading dimension ldd):
+// operands whose rows are not 16-byte aligned are repacked once so the
+// product's tile loads can use 16-byte vectors.
 template <typename T>
 __global__ void block_mask_kernel(const T *__restrict__ A, int64_t rows, int64_t cols,
-                                  int64_t ld, uint8_t *__restrict__ mask, int64_t nbc) {
+                                  int64_t ld, uint8_t *__restrict__ mask, int64_t nbc,
+                                  T *__restrict__ dst, int64_t ldd) {
     int64_t bi = blockIdx.y, bj = blockIdx.x;
     int64_t r0 = bi * MASK_BLOCK, c0 = bj * MASK_BLOCK;
     int found = 0;
-    for (int t = threadIdx.x; t < MASK_BLOCK * MASK_BLOCK && !found; t += blockDim.x) {
+    for (int t = threadIdx.x; t < MASK_BLOCK * MASK_BLOCK && (dst || !found); t += blockDim.x) {
         int64_t r = r0 + t / MASK_BLOCK, c = c0 + t % MASK_BLOCK;
-        if (r < rows && c < cols && (uint32_t)A[r * ld + c] < Elem<T>::inf) found = 1;
+        if (r < rows && c < cols) {
+            const T v = A[r * ld + c];
+            if ((uint32_t)v < Elem<T>::inf) found = 1;
+            if (dst) dst[r * ldd + c] = v;
+        }
     }
     found = __syncthreads_or(found);
     if (threadIdx.x == 0) mask[bi * nbc + bj] = (uint8_t)(found ? 1 : 0);
@@ -330,6 +338,13 @@ int choose_cfg(int dtype, int64_t M, int64_t N, int *cfg) {
     return MP_OK;
 }
 
+// Rows start on 8-element boundaries (what the 8-element vector loads of a
+// tile need).
+template <typename T>
+bool rows_aligned(const T *A, int64_t ld) {
+    return (uintptr_t)A % (8 * sizeof(T)) == 0 && ld % 8 == 0;
+}
+
 template <typename T>
 TileArgs<T> make_args(const T *X, const T *Y, T *Z, int64_t M, int64_t N, int64_t K, int64_t ldx,
                       int64_t ldy, int64_t ldz, const uint8_t *xm, const uint8_t *ym,
@@ -341,8 +356,8 @@ TileArgs<T> make_args(const T *X, const T *Y, T *Z, int64_t M, int64_t N, int64_
     ta.M = M; ta.N = N; ta.K = K; ta.ldx = ldx; ta.ldy = ldy; ta.ldz = ldz;
     ta.xmask = xm; ta.ymask = ym; ta.kblocks = kb; ta.nblocks = nb128;
     // vector loads of 8 elements need 8-element-aligned rows
-    ta.vecx = ((uintptr_t)X % (8 * sizeof(T)) == 0) && (ldx % 8 == 0);
-    ta.vecy = ((uintptr_t)Y % (8 * sizeof(T)) == 0) && (ldy % 8 == 0);
+    ta.vecx = rows_aligned(X, ldx);
+    ta.vecy = rows_aligned(Y, ldy);
     // the epilogue stores up to 8 outputs of a row at once
     ta.vecz = ((uintptr_t)Z % 16 == 0) && (ldz % 8 == 0);
     ta.gdiag = gdiag;
@@ -366,16 +381,37 @@ int run_dense(const T *X, const T *Y, T *Z, int64_t M, int64_t N, int64_t K, int
               int64_t ldy, int64_t ldz, int32_t *gdiag, int cfg, cudaStream_t s) {
     const int64_t mb = (M + MASK_BLOCK - 1) / MASK_BLOCK, nb = (N + MASK_BLOCK - 1) / MASK_BLOCK;
     const int64_t kb = (K + MASK_BLOCK - 1) / MASK_BLOCK;
-    DevBuf masks;
+    DevBuf masks, xpad, ypad;
     const uint8_t *xm = nullptr, *ym = nullptr;
     if (K > 0) {
         MP_TRY(masks.alloc((size_t)(mb * kb + kb * nb), s));
         uint8_t *xmw = masks.as<uint8_t>(), *ymw = xmw + mb * kb;
-        block_mask_kernel<T><<<dim3((unsigned)kb, (unsigned)mb), 256, 0, s>>>(X, M, K, ldx, xmw, kb);
-        block_mask_kernel<T><<<dim3((unsigned)nb, (unsigned)kb), 256, 0, s>>>(Y, K, N, ldy, ymw, nb);
+        // operands with rows off the 16-byte grid are repacked while masked
+        T *xd = nullptr, *yd = nullptr;
+        const int64_t ldxp = (K + 7) / 8 * 8, ldyp = (N + 7) / 8 * 8;
+        if (!rows_aligned(X, ldx)) {
+            MP_TRY(xpad.alloc((size_t)M * (size_t)ldxp * sizeof(T), s));
+            xd = xpad.as<T>();
+        }
+        if (!rows_aligned(Y, ldy)) {
+            MP_TRY(ypad.alloc((size_t)K * (size_t)ldyp * sizeof(T), s));
+            yd = ypad.as<T>();
+        }
+        block_mask_kernel<T><<<dim3((unsigned)kb, (unsigned)mb), 256, 0, s>>>(X, M, K, ldx, xmw, kb,
+                                                                           xd, ldxp);
+        block_mask_kernel<T><<<dim3((unsigned)nb, (unsigned)kb), 256, 0, s>>>(Y, K, N, ldy, ymw, nb,
+                                                                           yd, ldyp);
         MP_CUDA_TRY(cudaGetLastError());
         xm = xmw;
         ym = ymw;
+        if (xd) {
+            X = xd;
+            ldx = ldxp;
+        }
+        if (yd) {
+            Y = yd;
+            ldy = ldyp;
+        }
     }
     return launch_product<T>(make_args<T>(X, Y, Z, M, N, K, ldx, ldy, ldz, xm, ym, gdiag), cfg, s);
 }
@@ -425,21 +461,27 @@ struct MaskJob {
     const void *A;
     int64_t rows, cols, ld, bi, bj, nbc;
     uint8_t *mask;
+    void *dst;    // repacked copy of the block (leading dimension ldd), or NULL
+    int64_t ldd;
     int32_t dtype, pad;
 };
 
 __global__ void batched_mask_kernel(const MaskJob *__restrict__ jobs) {
     const MaskJob j = jobs[blockIdx.x];
     const int64_t r0 = j.bi * MASK_BLOCK, c0 = j.bj * MASK_BLOCK;
-    const uint32_t inf = j.dtype == MP_I16 ? 0x7FFFu : 0xFFu;
+    const bool i16 = j.dtype == MP_I16;
+    const uint32_t inf = i16 ? 0x7FFFu : 0xFFu;
     int found = 0;
-    for (int t = threadIdx.x; t < MASK_BLOCK * MASK_BLOCK && !found; t += blockDim.x) {
+    for (int t = threadIdx.x; t < MASK_BLOCK * MASK_BLOCK && (j.dst || !found); t += blockDim.x) {
         const int64_t r = r0 + t / MASK_BLOCK, c = c0 + t % MASK_BLOCK;
         if (r < j.rows && c < j.cols) {
-            const uint32_t v = j.dtype == MP_I16
-                                   ? (uint32_t)((const uint16_t *)j.A)[r * j.ld + c]
+            const uint32_t v = i16 ? (uint32_t)((const uint16_t *)j.A)[r * j.ld + c]
                                    : (uint32_t)((const uint8_t *)j.A)[r * j.ld + c];
             if (v < inf) found = 1;
+            if (j.dst) {
+                if (i16) ((uint16_t *)j.dst)[r * j.ldd + c] = (uint16_t)v;
+                else ((uint8_t *)j.dst)[r * j.ldd + c] = (uint8_t)v;
+            }
         }
     }
     found = __syncthreads_or(found);
@@ -485,6 +527,7 @@ struct mp_batch {
     int ntiles16 = 0;  // the int16 tiles come first in the list, then the uint8 ones
     std::vector<mp::BatchProb> host_probs;
     mp::DevBuf masks, probs, tiles, jobs, counter;
+    mp::DevBuf pads;   // repacked copies of operands whose rows are off the 8-element grid
 };
 
 namespace mp {
@@ -540,6 +583,28 @@ int batch_prepare(const mp_problem *probs, int count, mp_batch **out) {
     }
     MP_TRY(b->masks.alloc(std::max<size_t>(mask_bytes, 16), nullptr, true));
     uint8_t *mbase = b->masks.as<uint8_t>();
+    // operands whose rows are not on the 8-element grid get a repacked copy
+    // (written by the mask pass of every run) so their tiles load 16 bytes
+    auto aligned8 = [](const void *A, int64_t ld, size_t e) {
+        return (uintptr_t)A % (8 * e) == 0 && ld % 8 == 0;
+    };
+    std::vector<size_t> xpo((size_t)count, SIZE_MAX), ypo((size_t)count, SIZE_MAX);
+    size_t pad_bytes = 0;
+    for (int i = 0; i < count; ++i) {
+        const mp_problem &p = probs[i];
+        if (p.M == 0 || p.N == 0 || p.K == 0) continue;
+        const size_t e = p.dtype == MP_I16 ? 2 : 1;
+        if (!aligned8(p.X, p.ldx, e)) {
+            xpo[i] = pad_bytes;
+            pad_bytes += ((size_t)p.M * (size_t)((p.K + 7) / 8 * 8) * e + 255) / 256 * 256;
+        }
+        if (!aligned8(p.Y, p.ldy, e)) {
+            ypo[i] = pad_bytes;
+            pad_bytes += ((size_t)p.K * (size_t)((p.N + 7) / 8 * 8) * e + 255) / 256 * 256;
+        }
+    }
+    if (pad_bytes) MP_TRY(b->pads.alloc(pad_bytes, nullptr, true));
+    uint8_t *pbase = b->pads.as<uint8_t>();
     for (int i = 0; i < count; ++i) {
         const mp_problem &p = probs[i];
         const int64_t mb = (p.M + MASK_BLOCK - 1) / MASK_BLOCK, nb = (p.N + MASK_BLOCK - 1) / MASK_BLOCK;
@@ -547,11 +612,16 @@ int batch_prepare(const mp_problem *probs, int count, mp_batch **out) {
         const int cfg = tune.cfg[p.dtype == MP_U8 ? 1 : 0][size_class(p.M, p.N)];
         BatchProb &q = b->host_probs[i];
         const size_t e = p.dtype == MP_I16 ? 2 : 1;
-        q.X = p.X; q.Y = p.Y; q.Z = p.Z;
-        q.M = p.M; q.N = p.N; q.K = p.K; q.ldx = p.ldx; q.ldy = p.ldy; q.ldz = p.ldz;
+        void *xd = xpo[i] != SIZE_MAX ? pbase + xpo[i] : nullptr;
+        void *yd = ypo[i] != SIZE_MAX ? pbase + ypo[i] : nullptr;
+        const int64_t ldxp = (p.K + 7) / 8 * 8, ldyp = (p.N + 7) / 8 * 8;
+        q.X = xd ? xd : p.X; q.Y = yd ? yd : p.Y; q.Z = p.Z;
+        q.M = p.M; q.N = p.N; q.K = p.K; q.ldz = p.ldz;
+        q.ldx = xd ? ldxp : p.ldx;
+        q.ldy = yd ? ldyp : p.ldy;
         q.kblocks = kb; q.nblocks = nb; q.dtype = p.dtype; q.cfg = cfg;
-        q.vecx = ((uintptr_t)p.X % (8 * e) == 0) && (p.ldx % 8 == 0);
-        q.vecy = ((uintptr_t)p.Y % (8 * e) == 0) && (p.ldy % 8 == 0);
+        q.vecx = aligned8(q.X, q.ldx, e);
+        q.vecy = aligned8(q.Y, q.ldy, e);
         q.vecz = ((uintptr_t)p.Z % 16 == 0) && (p.ldz % 8 == 0);
         q.xmask = p.K > 0 ? mbase + xoff[i] : nullptr;
         q.ymask = p.K > 0 ? mbase + yoff[i] : nullptr;
@@ -559,10 +629,10 @@ int batch_prepare(const mp_problem *probs, int count, mp_batch **out) {
         if (p.M > 0 && p.N > 0 && p.K > 0) {
             for (int64_t bi = 0; bi < mb; ++bi)
                 for (int64_t bk = 0; bk < kb; ++bk)
-                    jobs.push_back({p.X, p.M, p.K, p.ldx, bi, bk, kb, mbase + xoff[i], p.dtype, 0});
+                    jobs.push_back({p.X, p.M, p.K, p.ldx, bi, bk, kb, mbase + xoff[i], xd, ldxp, p.dtype, 0});
             for (int64_t bk = 0; bk < kb; ++bk)
                 for (int64_t bj = 0; bj < nb; ++bj)
-                    jobs.push_back({p.Y, p.K, p.N, p.ldy, bk, bj, nb, mbase + yoff[i], p.dtype, 0});
+                    jobs.push_back({p.Y, p.K, p.N, p.ldy, bk, bj, nb, mbase + yoff[i], yd, ldyp, p.dtype, 0});
         }
         q.job1 = (int32_t)jobs.size();
         q.pad = 0;
@@ -812,8 +882,10 @@ int run_dense_noalloc(const T *X, const T *Y, T *Z, int64_t M, int64_t N, int64_
         // every mask byte the product reads is written here first, so stale
         // contents of an earlier call never matter
         uint8_t *xmw = base, *ymw = base + mb * kb;
-        block_mask_kernel<T><<<dim3((unsigned)kb, (unsigned)mb), 256, 0, s>>>(X, M, K, ldx, xmw, kb);
-        block_mask_kernel<T><<<dim3((unsigned)nb, (unsigned)kb), 256, 0, s>>>(Y, K, N, ldy, ymw, nb);
+        block_mask_kernel<T><<<dim3((unsigned)kb, (unsigned)mb), 256, 0, s>>>(X, M, K, ldx, xmw, kb,
+                                                                           nullptr, 0);
+        block_mask_kernel<T><<<dim3((unsigned)nb, (unsigned)kb), 256, 0, s>>>(Y, K, N, ldy, ymw, nb,
+                                                                           nullptr, 0);
         MP_CUDA_TRY(cudaGetLastError());
         xm = xmw;
         ym = ymw;
