@@ -92,6 +92,10 @@ int mp_build_transfer_matrix(int n, int16_t *A, int64_t lda, uint32_t *words_opt
  * (ldz >= N), all of element type dtype (MP_I16 or MP_U8).  K = 0 gives an
  * all-INF Z (X and Y may then be NULL).  M = 0 or N = 0 is a no-op.  Blocks of 128 x 128 that are
  * entirely INF in X or Y are skipped (their terms cannot lower a minimum).
+ * An operand whose rows do not start on 8-element boundaries (base address
+ * or leading dimension) is repacked into temporary library-owned device
+ * memory (M x K or K x N, rows padded to 8) during the mask pass, so every
+ * tile is read with 16-byte loads; the caller's arrays are only read.
  * Errors: MP_EINVAL (negative sizes, ld too small, dtype), MP_EALIAS (Z
  * overlaps X or Y), MP_ENOMEM, MP_ECUDA.  Asynchronous.
  */
@@ -227,7 +231,9 @@ int mp_minplus_mul_batched(const mp_problem *probs, int count, int mode, void *s
  * in the tile shape the tuning table gives its size class, most expensive
  * first), the problem descriptors and the mask-block list are uploaded once
  * (synchronously) and owned by the opaque handle, together with the mask
- * buffer.  mp_batch_run only enqueues kernels and one memset on stream, so
+ * buffer and, for operands whose rows are off the 8-element grid, buffers
+ * for their repacked copies (refreshed by every run's mask pass).
+ * mp_batch_run only enqueues kernels and one memset on stream, so
  * it may be captured in a CUDA graph and replayed; the operands may change
  * between runs but not their addresses or shapes.  One batch must not run
  * concurrently with itself.  mp_batch_destroy frees the handle (the caller
