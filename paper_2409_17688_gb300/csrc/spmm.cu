@@ -62,6 +62,7 @@ constexpr int kBlobHeader = 48;  // words: row0, nrows, flags, ntasks, nsegs, 3 
                                  // starts (kWarps + 1), per-warp stream starts (kWarps + 1)
 constexpr int kAccBytes = kGroupMax * kChunk * 4;  // per-row accumulators, one word per column
 constexpr int kStageRowsMax = 768;                // U rows per stage (register-staged indices)
+constexpr int kStagesMax = 3;                     // stages per group when rows are long
 constexpr int kRowLoads = kStageRowsMax * (kRowBytes / 16) / kThreads;  // 12 per thread
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -502,10 +503,19 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
     P.stage_u0.push_back(0);
     P.blob_off.push_back(0);
     int32_t gid = 0, attempt = 0;
+    // When rows are long against the buffer (mean length above a quarter of
+    // it) a one-buffer union holds only a few rows and every gathered row is
+    // staged again for each of those small groups.  Such matrices get groups
+    // whose union spans up to kStagesMax buffers: more rows share each staged
+    // row, and the stages' minima carry over in the shared accumulators.
+    const bool long_rows = N > 0 && 4 * csr.row_ptr[N] > (int64_t)umax * N;
+    const int64_t u_limit = long_rows ? (int64_t)kStagesMax * umax : umax;
     int64_t q = 0;
     while (q < N) {
-        // grow the group while the union of gathered rows fits one buffer and
-        // the stage's entry blob fits the blob region
+        // grow the group while the union of gathered rows fits its stages and
+        // a stage's entry blob fits the blob region (estimated from the rows'
+        // lengths shared out over the stages; a stage that still overflows is
+        // rebuilt with fewer rows below)
         const int64_t g0 = q;
         int64_t ucount = 0, ewords = 0;
         while (q < N && q - g0 < kGroupMax) {
@@ -513,8 +523,9 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
             for (int64_t e = csr.row_ptr[q]; e < csr.row_ptr[q + 1]; ++e)
                 if (stamp[csr.col[e]] != gid) ++add;
             const int64_t ew = padded(csr.row_ptr[q + 1] - csr.row_ptr[q]) * per_entry;
-            if (q > g0 && (ucount + add > umax ||
-                           blob_words(q - g0 + 1, ewords + ew) > blob_cap))
+            const int64_t nst = std::max<int64_t>(1, (ucount + add + umax - 1) / umax);
+            if (q > g0 && (ucount + add > u_limit ||
+                           blob_words(q - g0 + 1, (ewords + ew) / nst) > blob_cap))
                 break;
             for (int64_t e = csr.row_ptr[q]; e < csr.row_ptr[q + 1]; ++e) stamp[csr.col[e]] = gid;
             ucount += add;
