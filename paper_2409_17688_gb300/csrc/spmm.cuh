@@ -7,6 +7,32 @@
 
 namespace mp {
 
+// Shape of the sparse step shared by the kernel (spmm.cu) and the host plan
+// builder (spmm_plan.cu).
+constexpr int kThreads = 512;                    // 16 warps
+constexpr int kWarps = kThreads / 32;
+constexpr int kGroupMax = 64;                     // rows per group (6-bit row indices)
+constexpr int kChunk = 64;                        // columns per work item
+constexpr int kRowBytes = kChunk * 2;
+constexpr int kBlobHeader = 48;  // words: row0, nrows, flags, ntasks, nsegs, 3 pad, per-warp task
+                                 // starts (kWarps + 1), per-warp stream starts (kWarps + 1)
+constexpr int kAccBytes = kGroupMax * kChunk * 4;  // per-row accumulators, one word per column
+constexpr int kStageRowsMax = 768;                // U rows per stage (register-staged indices)
+constexpr int kStagesMax = 3;                     // stages per group when rows are long
+constexpr int kRowLoads = kStageRowsMax * (kRowBytes / 16) / kThreads;  // 12 per thread
+
+// Entry words of the column-constant stream: bits 0..16 the byte offset of
+// the gathered row in the row buffer.  A segment is a whole number of 8-entry
+// pairs of 4-entry blocks; every entry of its last block has bit 31 set and
+// bits 17..20 = the segment's cluster mask, and bit 30 too when the block
+// also ends a task.
+constexpr uint32_t kEntOffset = 0x1FFFFu;
+constexpr uint32_t kEntSegEnd = 0x80000000u;
+constexpr uint32_t kEntTaskEnd = 0x40000000u;
+constexpr int kEntMaskShift = 17;
+constexpr int kStreamStart = 8 + kWarps + 1;  // header words: per-warp stream starts
+static_assert(kStreamStart + kWarps < kBlobHeader, "blob header too small");
+
 // CSR of a sparse N x N int16 matrix: the finite entries of each row.
 struct HostCsr {
     int64_t N = 0;
@@ -26,7 +52,7 @@ struct UnitDesc {
     uint32_t meta, u0, u1, bo8;
 };
 
-// The gather plan of a sparse A, built once on the host (see spmm.cu).
+// The gather plan of a sparse A, built once on the host (spmm_plan.cu).
 struct PlanHost {
     int64_t N = 0, ldb = 0, nnz = 0;
     int ngroups = 0, nchunks = 0, cap_rows = 0, blob_cap = 0;

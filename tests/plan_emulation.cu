@@ -11,7 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 
-#include "../paper_2409_17688_gb300/csrc/spmm.cu"
+#include "../paper_2409_17688_gb300/csrc/spmm_plan.cu"
 
 namespace mp {
 int set_error(int code, const char *fmt, ...) {
@@ -21,17 +21,6 @@ int set_error(int code, const char *fmt, ...) {
     va_end(ap);
     fputc('\n', stderr);
     return code;
-}
-// the plan is built for a fixed grid here; no device is queried
-int device_info(DeviceInfo *o) {
-    o->sms = 152;
-    o->smem_optin = 232448;
-    o->device = 0;
-    return MP_OK;
-}
-int device_status_ptr(int **p) {
-    *p = nullptr;
-    return MP_OK;
 }
 }  // namespace mp
 
