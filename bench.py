@@ -153,6 +153,24 @@ def profiled_traffic(summary: str, source: str):
     return int(fields["traffic_bytes_per_launch"])
 
 
+def profiled_shared(summary: str, source: str):
+    """The shared-memory pipe (what binds the sparse step) from the committed
+    ncu summary: wavefronts per launch and their share of the pipe's peak, or
+    None when the kernel's source changed since the counters were taken."""
+    if profiled_traffic(summary, source) is None:
+        return None
+    text = open(os.path.join(ROOT, summary)).read()
+    vals = {}
+    for line in text.splitlines():
+        cells = [c.strip() for c in line.split("|")]
+        if len(cells) > 3 and cells[1].startswith("shared-memory wavefronts"):
+            vals["pct" if "% of peak" in cells[1] else "n"] = float(cells[2])
+    if len(vals) != 2:
+        return None
+    return {"wavefronts_per_launch": int(vals["n"]), "frac_of_pipe_peak": round(vals["pct"] / 100, 4),
+            "source": summary + " (ncu, one launch)"}
+
+
 def hbm_frac(bytes_per_s: float):
     """Algorithmic bytes/s of a launch against the measured copy bandwidth:
     the memory side of the roofline, reported to show that it does not bind."""
@@ -279,6 +297,8 @@ def run_ours(args):
                 "traffic_unit": "bytes per launch (ncu dram read+write, cold cache)",
                 "algorithmic_bytes": 4 * Ns[9] * Ns[9],
                 "hbm_frac": hbm_frac(4 * Ns[9] * Ns[9] / (step_ms * 1e-3)),
+                "shared_memory": profiled_shared("profiles/k2_transfer_step_n9.md",
+                                                 "paper_2409_17688_gb300/csrc/spmm.cu"),
                 "peak_source": "K6 __vimin3_u16x2 rate measured in this run (4 terms/instr)",
                 "launch_us": round(step_ms * 1e3, 2)}
 
