@@ -30,6 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = ("min-plus Gop/s and % of DPX peak on A^k for P_n□C_m; time-to-γ2; "
+WORKLOAD = ("transfer power chains P_n x C_m, n=6,7,8,9 (N=225,558,1386,3447), "
+            "A^1..A^200 exact int16, gamma_2 for m=3..200")
           "p50/p99 served")
 PATH_ORDERS = (6, 7, 8, 9)
 K_MAX = 200
@@ -332,8 +334,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int16",
         "data": "synthetic: transfer matrices A(D_n) built from the paper's word and arc rules",
-        "config": {"workload": "transfer power chains P_n x C_m, n=6,7,8,9 (N=225,558,1386,3447), "
-                               "A^1..A^200 exact int16, gamma_2 for m=3..200",
+        "config": {"workload": WORKLOAD,
                    "ops_per_step_algorithmic": ops_per_step,
                    "ops_per_step_dense_equiv": dense_per_step,
                    "l2": "flushed between steps (256 MiB write); within a step each power "
@@ -582,8 +583,8 @@ def run_reference(args):
             "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32 accumulate of int16",
             "data": "synthetic: transfer matrices A(D_n)",
-            "config": {"workload": "transfer power chains P_n x C_m, n=6,7,8,9 (bounded sample)",
-                       "parallelism": "cpu"},
+            "config": {"workload": WORKLOAD,
+                       "parallelism": "cpu (oracle), a bounded sample of the workload per step"},
             "cpu_baseline": {"value": round(value, 2), "unit": "Gop/s", "cores": threads,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 2), "unit": "Gop/s", "h2d_bytes_per_step": 0,
