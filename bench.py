@@ -30,9 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = ("min-plus Gop/s and % of DPX peak on A^k for P_n□C_m; time-to-γ2; "
+          "p50/p99 served")
 WORKLOAD = ("transfer power chains P_n x C_m, n=6,7,8,9 (N=225,558,1386,3447), "
             "A^1..A^200 exact int16, gamma_2 for m=3..200")
-          "p50/p99 served")
 PATH_ORDERS = (6, 7, 8, 9)
 K_MAX = 200
 
