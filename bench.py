@@ -546,10 +546,16 @@ def cpu_baseline_sample(target_s: float = 12.0):
     oracle.power_sequence(A, k, keep_powers=False, threads=threads)
     dt = time.perf_counter() - t0
     ops = N * nnz * (k - 1)
+    # the plain loop on one thread as well, on the first two products
+    t0 = time.perf_counter()
+    oracle.power_sequence(A, 3, keep_powers=False, threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": round(ops / dt / 1e9, 2), "unit": "Gop/s", "cores": threads,
             "kind": "oracle",
+            "single_thread_value": round(N * nnz * 2 / dt1 / 1e9, 2),
             "sample": f"n=9 (N={N}) chain A^1..A^{k} ({k - 1} products of N*nnz terms) "
-                      f"in {dt:.1f} s"}
+                      f"in {dt:.1f} s on {threads} threads; single thread: A^1..A^3 "
+                      f"in {dt1:.1f} s"}
 
 
 def run_reference(args):
