@@ -144,14 +144,67 @@ static int transfer_entry(int n, cudaStream_t s, TransferEntry **out) {
     for (int64_t p = 0; p < N; ++p) z[p] = (uint16_t)__builtin_popcount(masks[p].zero);
     csr.val.resize((size_t)nnz);
     for (int64_t t = 0; t < nnz; ++t) csr.val[t] = (int16_t)z[csr.col[t]];
+    // The chain keeps its rows in an order of its own: words sorted by the
+    // positions of their 1s, then of their 0s.  Rows with equal 1-positions
+    // gather largely the same rows, so row groups of the gather plan come out
+    // larger and fewer rows are staged per output row (at n = 9: 16% fewer
+    // units, 14% fewer staged rows).  Row i of the internal buffers is word
+    // canon[i]; columns keep the words' order, and every value written to
+    // the caller (powers, diagonal minima) is placed by canon.
+    std::vector<int32_t> canon((size_t)N), inv((size_t)N);
+    for (int64_t i = 0; i < N; ++i) canon[i] = (int32_t)i;
+    std::stable_sort(canon.begin(), canon.end(), [&](int32_t a, int32_t b) {
+        return masks[a].one != masks[b].one ? masks[a].one < masks[b].one
+                                            : masks[a].zero < masks[b].zero;
+    });
+    for (int64_t i = 0; i < N; ++i) inv[canon[i]] = (int32_t)i;
+    // CSR with rows in the internal order: caller columns for the initial
+    // power on the device, internal columns (gathered rows) for the plan
+    HostCsr pcsr;
+    pcsr.N = N;
+    pcsr.row_ptr.assign((size_t)N + 1, 0);
+    for (int64_t i = 0; i < N; ++i)
+        pcsr.row_ptr[i + 1] = pcsr.row_ptr[i] + (csr.row_ptr[canon[i] + 1] - csr.row_ptr[canon[i]]);
+    pcsr.col.resize((size_t)nnz);
+    pcsr.val.resize((size_t)nnz);
+    std::vector<int32_t> dcol((size_t)nnz);
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t o = pcsr.row_ptr[i];
+        for (int64_t t = csr.row_ptr[canon[i]]; t < csr.row_ptr[canon[i] + 1]; ++t, ++o) {
+            dcol[o] = csr.col[t];
+            pcsr.col[o] = inv[csr.col[t]];
+            pcsr.val[o] = csr.val[t];
+        }
+    }
+    // internal columns ascend within a row, as the plan expects
+    for (int64_t i = 0; i < N; ++i) {
+        const int64_t b = pcsr.row_ptr[i], f = pcsr.row_ptr[i + 1];
+        std::vector<std::pair<int32_t, int32_t>> tmp;
+        tmp.reserve((size_t)(f - b));
+        for (int64_t t = b; t < f; ++t) tmp.push_back({pcsr.col[t], dcol[t]});
+        std::sort(tmp.begin(), tmp.end());
+        for (int64_t t = b; t < f; ++t) {
+            pcsr.col[t] = tmp[(size_t)(t - b)].first;
+            dcol[t] = tmp[(size_t)(t - b)].second;
+            pcsr.val[t] = (int16_t)z[dcol[t]];
+        }
+    }
+    std::vector<uint16_t> pz((size_t)N);
+    for (int64_t i = 0; i < N; ++i) pz[i] = z[canon[i]];
+    MP_CUDA_TRY(cudaMemcpyAsync(d_rp, pcsr.row_ptr.data(), (size_t)(N + 1) * 8,
+                                cudaMemcpyHostToDevice, s));
+    if (nnz)
+        MP_CUDA_TRY(cudaMemcpyAsync(e->csr.col.p, dcol.data(), (size_t)nnz * 4,
+                                    cudaMemcpyHostToDevice, s));
     MP_TRY(e->csr.val.alloc((size_t)std::max<int64_t>(nnz, 1) * 2, s, true));
     if (nnz)
-        MP_CUDA_TRY(cudaMemcpyAsync(e->csr.val.p, csr.val.data(), (size_t)nnz * 2,
+        MP_CUDA_TRY(cudaMemcpyAsync(e->csr.val.p, pcsr.val.data(), (size_t)nnz * 2,
                                     cudaMemcpyHostToDevice, s));
     int cap = 0, blob_cap = 0, grid = 0;
     MP_TRY(sparse_cap_rows(&cap, &blob_cap, &grid));
     PlanHost ph;
-    MP_TRY(plan_build_host(csr, true, z, cap, blob_cap, grid, &ph));
+    MP_TRY(plan_build_host(pcsr, true, pz, &canon, cap, blob_cap, grid, &ph));
+    ph.canon = canon;
     MP_TRY(plan_upload(ph, &e->plan, s, true));
     MP_CUDA_TRY(cudaStreamSynchronize(s));
     e->h2d_bytes = masks.size() * sizeof(WordMasks) + (size_t)(N + 1) * 8 + (size_t)nnz * 2 +
@@ -577,7 +630,7 @@ int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max, int16_t *p
     int cap = 0, blob_cap = 0, grid = 0;
     MP_TRY(sparse_cap_rows(&cap, &blob_cap, &grid));
     PlanHost ph;
-    MP_TRY(plan_build_host(csr, colconst, z, cap, blob_cap, grid, &ph));
+    MP_TRY(plan_build_host(csr, colconst, z, nullptr, cap, blob_cap, grid, &ph));
     PlanDev plan;
     MP_TRY(plan_upload(ph, &plan, s, false));
     DevBuf B;

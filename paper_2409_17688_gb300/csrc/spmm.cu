@@ -294,14 +294,16 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
             // one task word per task, the labels, then every warp's entry
             // stream (sixteen-byte aligned, a whole number of 8-entry blocks)
             zs = reinterpret_cast<const uint16_t *>(tasks + ((ntasks + 7) & ~7));
-            const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8;
+            const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8 +
+                                   ((nrows + 7) & ~7);
             warp_stream(accs, smem_u32(ents), smem_u32(buf + blob_bytes), tasks,
                         (int)blob[kStreamStart + warp], (int)blob[kStreamStart + warp + 1],
                         (int)blob[8 + warp], lane);
         } else {
             const uint32_t *segs = tasks + ((2 * ntasks + 7) & ~7);
             zs = reinterpret_cast<const uint16_t *>(segs + ((2 * nsegs + 7) & ~7));
-            const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8;
+            const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8 +
+                                   ((nrows + 7) & ~7);
             const int t_end = (int)blob[8 + warp + 1];
             for (int t = (int)blob[8 + warp]; t < t_end; ++t) {
                 const uint32_t t0 = tasks[2 * t], t1 = tasks[2 * t + 1];
@@ -337,14 +339,17 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
                 const uint32_t keep = kColConst ? v + (uint32_t)zs[r] * 0x10001u : v;
                 uint16_t *brow = a.Bout + q * a.ldb + c0;
                 reinterpret_cast<uint32_t *>(brow)[lane] = keep;
+                // the caller's row (and diagonal column) of internal row q,
+                // from the blob (after the labels)
+                const int64_t qc = (int64_t)reinterpret_cast<const uint32_t *>(zs)[((nrows + 15) / 16) * 8 + r];
                 if (a.user_out) {
                     const int64_t c = c0 + 2 * lane;
-                    int16_t *orow = a.user_out + q * a.N;
+                    int16_t *orow = a.user_out + qc * a.N;
                     if (c < a.N) orow[c] = (int16_t)(v & 0xFFFFu);
                     if (c + 1 < a.N) orow[c + 1] = (int16_t)(v >> 16);
                 }
-                if (diag && q >= c0 && q < c0 + kChunk && (int)(q - c0) >> 1 == lane)
-                    dmin = min(dmin, (int32_t)((q - c0) & 1 ? v >> 16 : v & 0xFFFFu));
+                if (diag && qc >= c0 && qc < c0 + kChunk && (int)(qc - c0) >> 1 == lane)
+                    dmin = min(dmin, (int32_t)((qc - c0) & 1 ? v >> 16 : v & 0xFFFFu));
             }
         }
         __syncthreads();  // everyone is done with buffer b before it is refilled
@@ -381,24 +386,27 @@ __global__ void init_from_dense_kernel(const int16_t *__restrict__ A, int64_t N,
 }
 
 // The same from CSR (transfer matrices are never formed densely here).
+// Rows are in the chain's internal order (row q of the CSR is internal row
+// q, whose caller row is canon[q]); columns are the caller's.
 __global__ void init_from_csr_kernel(const int64_t *__restrict__ row_ptr,
                                      const int32_t *__restrict__ col, const int16_t *__restrict__ val,
                                      int64_t N, int64_t ldb, const uint16_t *__restrict__ z,
-                                     uint16_t *__restrict__ B, int16_t *__restrict__ user0,
-                                     int32_t *__restrict__ g0) {
+                                     const int32_t *__restrict__ canon, uint16_t *__restrict__ B,
+                                     int16_t *__restrict__ user0, int32_t *__restrict__ g0) {
     const int64_t q = blockIdx.x;
+    const int64_t qc = canon ? (int64_t)canon[q] : q;
     const uint16_t zq = z ? z[q] : 0;
     for (int64_t c = threadIdx.x; c < ldb; c += blockDim.x) {
         B[q * ldb + c] = (uint16_t)(kInf16 + zq);
-        if (user0 && c < N) user0[q * N + c] = (int16_t)kInf16;
+        if (user0 && c < N) user0[qc * N + c] = (int16_t)kInf16;
     }
     __syncthreads();  // the whole row is INF before the arcs land (one block per row)
     for (int64_t e = row_ptr[q] + threadIdx.x; e < row_ptr[q + 1]; e += blockDim.x) {
         const int64_t p = col[e];
         const uint32_t v = (uint32_t)(uint16_t)val[e];
         B[q * ldb + p] = (uint16_t)(v + zq);
-        if (user0) user0[q * N + p] = (int16_t)v;
-        if (g0 && p == q) atomicMin(g0, (int32_t)v);
+        if (user0) user0[qc * N + p] = (int16_t)v;
+        if (g0 && p == qc) atomicMin(g0, (int32_t)v);
     }
 }
 
@@ -471,10 +479,15 @@ int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent) 
     MP_TRY(up(d->z, h.z.data(), h.z.size() * 2));
     MP_TRY(up(d->units, h.units.data(), h.units.size() * sizeof(UnitDesc)));
     MP_TRY(up(d->cta_unit0, h.cta_unit0.data(), h.cta_unit0.size() * 4));
+    d->permuted = !h.canon.empty();
+    if (d->permuted) {
+        if ((int64_t)h.canon.size() != h.N) return set_error(MP_EINVAL, "row order of the wrong length");
+        MP_TRY(up(d->canon, h.canon.data(), h.canon.size() * 4));
+    }
     d->grid = h.grid;
     d->h2d_bytes = (h.grp_row0.size() + h.grp_stage0.size() + h.stage_u0.size() + h.blob.size() +
                     h.urows.size() + h.cta_unit0.size()) * 4 + h.blob_off.size() * 8 +
-                   h.z.size() * 2 + h.units.size() * sizeof(UnitDesc);
+                   h.z.size() * 2 + h.units.size() * sizeof(UnitDesc) + h.canon.size() * 4;
     return MP_OK;
 }
 
@@ -551,6 +564,7 @@ int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *
 
 int sparse_init_from_dense(const PlanDev &p, const int16_t *A, uint16_t *B0, int16_t *user0,
                            int32_t *g0, cudaStream_t s) {
+    if (p.permuted) return set_error(MP_EINVAL, "dense initialisation of a reordered plan");
     dim3 grid((unsigned)p.N, (unsigned)std::min<int64_t>((p.ldb + 255) / 256, 64));
     init_from_dense_kernel<<<grid, 256, 0, s>>>(A, p.N, p.ldb, p.colconst ? p.z.as<uint16_t>() : nullptr,
                                                 B0, user0, g0);
@@ -564,7 +578,9 @@ int sparse_init_from_csr(const PlanDev &p, const int64_t *row_ptr, const int32_t
     // one block per row so the INF fill precedes the arc scatter within the block
     dim3 grid((unsigned)p.N, 1);
     init_from_csr_kernel<<<grid, 256, 0, s>>>(row_ptr, col, val, p.N, p.ldb,
-                                              p.colconst ? p.z.as<uint16_t>() : nullptr, B0, user0, g0);
+                                              p.colconst ? p.z.as<uint16_t>() : nullptr,
+                                              p.permuted ? p.canon.as<int32_t>() : nullptr, B0,
+                                              user0, g0);
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

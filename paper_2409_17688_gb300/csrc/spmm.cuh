@@ -64,6 +64,11 @@ struct PlanHost {
     int grid = 0;                         // CTAs the schedule is made for
     std::vector<UnitDesc> units;          // every CTA's units, back to back
     std::vector<int32_t> cta_unit0;       // [grid + 1] offsets into units
+    // The chain may keep the rows of its powers in an order of its own
+    // (rows of the plan = rows of the internal buffers): canon[i] is the row
+    // (and diagonal column) of the caller's matrices that internal row i
+    // holds.  Empty: the identity.  Columns are never reordered.
+    std::vector<int32_t> canon;
 };
 struct PlanDev {
     int64_t N = 0, ldb = 0, nnz = 0;
@@ -72,6 +77,8 @@ struct PlanDev {
     size_t h2d_bytes = 0;
     int grid = 0;
     DevBuf grp_row0, grp_stage0, stage_u0, blob_off, blob, uoff16, z, units, cta_unit0;
+    DevBuf canon;          // empty: identity row order
+    bool permuted = false;
 };
 
 struct SpStepArgs {
@@ -89,7 +96,7 @@ struct SpStepArgs {
 };
 
 int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_t> &z,
-                    int cap_rows, int blob_cap, int grid, PlanHost *out, int cluster_max = 4);
+                    const std::vector<int32_t> *canon, int cap_rows, int blob_cap, int grid, PlanHost *out, int cluster_max = 4);
 int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent);
 int sparse_cap_rows(int *cap_rows, int *blob_cap, int *grid);
 int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,

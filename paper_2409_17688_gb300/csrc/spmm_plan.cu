@@ -12,6 +12,7 @@
 namespace mp {
 
 int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_t> &z,
+                    const std::vector<int32_t> *canon,
                     int cap_rows, int blob_cap, int grid, PlanHost *out, int cluster_max) {
     const int64_t N = csr.N;
     const int umax = cap_rows - 1;  // the last buffer row is the INF padding row
@@ -35,11 +36,11 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
     const int gran = pad_to * per_entry;     // words a segment's length is a multiple of
     auto padded = [&](int64_t cnt) { return (cnt + pad_to - 1) / pad_to * pad_to; };
     auto blob_words = [&](int64_t rows, int64_t entry_words) {
+        const int64_t labels = ((rows + 15) / 16) * 8 + ((rows + 7) & ~7);  // z, caller rows
         if (colconst)  // task words, labels, entry streams
-            return (int64_t)kBlobHeader + ((rows + kWarps + 7) & ~7) + ((rows + 15) / 16) * 8 +
-                   entry_words;
+            return (int64_t)kBlobHeader + ((rows + kWarps + 7) & ~7) + labels + entry_words;
         return (int64_t)kBlobHeader + ((2 * (rows + kWarps) + 7) & ~7) +
-               ((2 * (15 * rows + 2 * kWarps) + 7) & ~7) + ((rows + 15) / 16) * 8 + entry_words;
+               ((2 * (15 * rows + 2 * kWarps) + 7) & ~7) + labels + entry_words;
     };
 
     std::vector<int32_t> stamp((size_t)N, -1), local((size_t)N, -1);
@@ -266,6 +267,10 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
                 std::vector<uint32_t> zw((size_t)((rows + 15) / 16) * 8, 0u);
                 for (int64_t r = 0; r < rows; ++r)
                     zw[(size_t)(r >> 1)] |= (uint32_t)P.z[(size_t)(g0 + r)] << (16 * (r & 1));
+                // then the caller's row of each group row (where its values and
+                // diagonal entry go), 32-bit, padded to 8 words
+                for (int64_t r = 0; r < ((rows + 7) & ~7); ++r)
+                    zw.push_back(r < rows ? (uint32_t)(canon ? (*canon)[(size_t)(g0 + r)] : g0 + r) : 0u);
                 int tcount = 0;
                 if (colconst) {
                     // per warp: its tasks' entries back to back, segment and task

@@ -59,7 +59,7 @@ int main(int argc, char **argv) {
         csr.row_ptr.push_back((int64_t)csr.col.size());
     }
     PlanHost P;
-    if (plan_build_host(csr, true, z, cap, 6144, 7, &P, cl) != MP_OK) return 3;
+    if (plan_build_host(csr, true, z, nullptr, cap, 6144, 7, &P, cl) != MP_OK) return 3;
     fprintf(stderr, "groups %d stages %zu units %zu\n", P.ngroups, P.stage_u0.size() - 1,
             P.units.size());
     const int INF = 0x7FFF;
@@ -86,7 +86,8 @@ int main(int argc, char **argv) {
             const int row0 = (int)blob[0], nrows = (int)blob[1], ntasks = (int)blob[3], nsegs = (int)blob[4];
             const uint32_t *tasks = blob + kBlobHeader;
             const uint16_t *zs = reinterpret_cast<const uint16_t *>(tasks + ((ntasks + 7) & ~7));
-            const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8;
+            const uint32_t *ents = reinterpret_cast<const uint32_t *>(zs) + ((nrows + 15) / 16) * 8 +
+                                   ((nrows + 7) & ~7);
             (void)nsegs;
             for (int w = 0; w < kWarps; ++w) {
                 const int e0 = (int)blob[kStreamStart + w], e1 = (int)blob[kStreamStart + w + 1];
