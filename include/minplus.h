@@ -195,6 +195,24 @@ int mp_transfer_recurrence_stream(int n, int k_limit, int ring, int32_t *out);
  * (k_max * n >= 32767), MP_ENOMEM, MP_ECUDA. */
 int mp_gamma2_table(int n, int k_max, int64_t *out);
 
+/* Several transfer chains at once (Algorithm 2 and Theorem 2 for each path
+ * order ns[i], i < count, distinct): gdiag (DEVICE int32, count x k_max,
+ * row i for ns[i]) receives min diag A^k for k = 1..k_max as in
+ * mp_transfer_power_sequence with powers_opt NULL.  The chains run side by
+ * side on library-owned streams forked from and joined back into stream, so
+ * the work is asynchronous on stream and the short chains' per-step latency
+ * overlaps the long ones.  Errors: MP_EINVAL (count < 0, NULL arrays,
+ * k_max < 1, an n out of range or repeated), MP_ENOMEM, MP_ECUDA. */
+int mp_transfer_power_sequences(const int *ns, int count, int k_max, int32_t *gdiag,
+                                void *stream);
+
+/* The gamma_2 tables of several path orders (HOST int32 ns[count], distinct):
+ * out (HOST int64, count x (k_max + 1)) row i holds mp_gamma2_table(ns[i]).
+ * Synchronous; the chains run side by side as in mp_transfer_power_sequences.
+ * Errors: MP_EINVAL (count < 0, NULL arrays, k_max < 3, an n out of range or
+ * repeated), MP_ERANGE (k_max * n >= 32767 for some n), MP_ENOMEM, MP_ECUDA. */
+int mp_gamma2_tables(const int *ns, int count, int k_max, int64_t *out);
+
 /* ---- K3: reductions -----------------------------------------------------
  * mp_diag_min: *out = min_i P[i][i] over an N x N DEVICE int16 matrix
  * (leading dimension ld), written to DEVICE int32 out.  Theorem 2.

@@ -61,6 +61,8 @@ def lib() -> ctypes.CDLL:
         "mp_transfer_power_sequence": (I, [I, I, P, P, P]),
         "mp_gamma2_cylinder": (I, [I, I64, P]),
         "mp_gamma2_table": (I, [I, I, P]),
+        "mp_transfer_power_sequences": (I, [P, I, I, P, P]),
+        "mp_gamma2_tables": (I, [P, I, I, P]),
         "mp_diag_min": (I, [P, I64, I64, P, P]),
         "mp_diff_const": (I, [P, P, I64, P, P]),
         "mp_transfer_recurrence": (I, [I, I, P]),
@@ -294,6 +296,25 @@ def mp_gamma2_table(n: int, k_max: int) -> np.ndarray:
     """gamma_2(P_n x C_m) for m = 0..k_max (entries m < 3 are -1), synchronous."""
     out = np.zeros(k_max + 1, dtype=np.int64)
     _check(lib().mp_gamma2_table(int(n), int(k_max), out.ctypes.data))
+    return out
+
+
+def mp_transfer_power_sequences(ns, k_max: int, stream=None):
+    """min diag A^k, k = 1..k_max, of several path orders at once (device
+    int32 [len(ns), k_max]); the chains run side by side on library streams."""
+    import torch
+    ns_arr = (ctypes.c_int * len(ns))(*[int(n) for n in ns])
+    g = torch.empty((len(ns), int(k_max)), dtype=torch.int32, device="cuda")
+    _check(lib().mp_transfer_power_sequences(ns_arr, len(ns), int(k_max), _dev(g),
+                                             _stream(stream)))
+    return g
+
+
+def mp_gamma2_tables(ns, k_max: int) -> np.ndarray:
+    """gamma_2 tables of several path orders, [len(ns), k_max + 1], synchronous."""
+    ns_arr = (ctypes.c_int * len(ns))(*[int(n) for n in ns])
+    out = np.zeros((len(ns), int(k_max) + 1), dtype=np.int64)
+    _check(lib().mp_gamma2_tables(ns_arr, len(ns), int(k_max), out.ctypes.data))
     return out
 
 

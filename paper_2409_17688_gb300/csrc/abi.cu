@@ -42,10 +42,13 @@ const char *last_error() { return g_err; }
 // ------------------------------------------------------- per-device state
 static std::mutex g_mu;
 
+constexpr int kChainStreams = 8;  // streams on which several chains run side by side
+
 struct DeviceState {
     DeviceInfo info;
     int *status = nullptr;            // device-side error latch
     cudaStream_t sync_stream = nullptr;  // for the synchronous entry points
+    cudaStream_t chain_streams[kChainStreams] = {};
 };
 static std::map<int, DeviceState> g_dev;
 
@@ -64,6 +67,8 @@ static int device_state(DeviceState **out) {
         MP_CUDA_TRY(cudaMalloc(&st.status, sizeof(int)));
         MP_CUDA_TRY(cudaMemset(st.status, 0, sizeof(int)));
         MP_CUDA_TRY(cudaStreamCreateWithFlags(&st.sync_stream, cudaStreamNonBlocking));
+        for (cudaStream_t &cs : st.chain_streams)
+            MP_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         it = g_dev.emplace(dev, st).first;
     }
     *out = &it->second;
@@ -651,6 +656,81 @@ int mp_transfer_power_sequence(int n, int k_max, int16_t *powers_opt, int32_t *g
     enumerate_words(n, &w);
     const size_t N = w.size();
     return transfer_powers_strided(n, k_max, powers_opt, N * N, gdiag_opt, (cudaStream_t)stream);
+}
+
+// Several transfer chains at once: each runs on a library stream of its own,
+// forked from and joined back into the caller's stream, so the small chains'
+// per-step latency overlaps the large ones' work.
+int mp_transfer_power_sequences(const int *ns, int count, int k_max, int32_t *gdiag,
+                                void *stream) {
+    if (count < 0 || (count > 0 && (!ns || !gdiag)) || k_max < 1)
+        return set_error(MP_EINVAL, "need count >= 0, the path orders, gdiag and k_max >= 1");
+    for (int i = 0; i < count; ++i) MP_TRY(check_n(ns[i]));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (count == 1) return mp_transfer_power_sequence(ns[0], k_max, nullptr, gdiag, s);
+    for (int i = 0; i < count; ++i)
+        for (int j = 0; j < i; ++j)
+            if (ns[i] == ns[j])
+                return set_error(MP_EINVAL, "path order %d appears twice", ns[i]);
+    DeviceState *st;
+    MP_TRY(device_state(&st));
+    // largest chains first, so they take their SMs before the small ones
+    std::vector<int> order((size_t)count);
+    for (int i = 0; i < count; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ns[a] > ns[b]; });
+    cudaEvent_t fork = nullptr;
+    MP_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    int rc = MP_OK;
+    if (cudaEventRecord(fork, s) != cudaSuccess) rc = set_error(MP_ECUDA, "event record failed");
+    std::vector<cudaEvent_t> joins;
+    for (int k = 0; k < count && rc == MP_OK; ++k) {
+        const int i = order[(size_t)k];
+        cudaStream_t cs = st->chain_streams[k % kChainStreams];
+        if (cudaStreamWaitEvent(cs, fork, 0) != cudaSuccess) {
+            rc = set_error(MP_ECUDA, "stream wait failed");
+            break;
+        }
+        rc = mp_transfer_power_sequence(ns[i], k_max, nullptr, gdiag + (size_t)i * (size_t)k_max, cs);
+        cudaEvent_t j = nullptr;
+        if (cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess) {
+            rc = set_error(MP_ECUDA, "event create failed");
+            break;
+        }
+        joins.push_back(j);
+        // join even after a failed launch, so the caller's stream stays ordered
+        if (cudaEventRecord(j, cs) != cudaSuccess || cudaStreamWaitEvent(s, j, 0) != cudaSuccess)
+            rc = rc != MP_OK ? rc : set_error(MP_ECUDA, "stream join failed");
+    }
+    for (cudaEvent_t j : joins) cudaEventDestroy(j);
+    cudaEventDestroy(fork);
+    return rc;
+}
+
+int mp_gamma2_tables(const int *ns, int count, int k_max, int64_t *out) {
+    if (count < 0 || (count > 0 && (!ns || !out)) || k_max < 3)
+        return set_error(MP_EINVAL, "need count >= 0, the path orders, out and k_max >= 3");
+    for (int i = 0; i < count; ++i) {
+        MP_TRY(check_n(ns[i]));
+        if ((int64_t)k_max * ns[i] >= (int64_t)kInf16)
+            return set_error(MP_ERANGE, "k_max * n = %lld reaches the int16 INF code",
+                             (long long)k_max * ns[i]);
+    }
+    if (count == 0) return MP_OK;
+    DeviceState *st;
+    MP_TRY(device_state(&st));
+    cudaStream_t s = st->sync_stream;
+    DevBuf g;
+    const size_t cells = (size_t)count * (size_t)k_max;
+    MP_TRY(g.alloc(sizeof(int32_t) * cells, s));
+    MP_TRY(mp_transfer_power_sequences(ns, count, k_max, g.as<int32_t>(), s));
+    std::vector<int32_t> h(cells);
+    MP_CUDA_TRY(cudaMemcpyAsync(h.data(), g.p, sizeof(int32_t) * cells, cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i)
+        for (int m = 0; m <= k_max; ++m)
+            out[(size_t)i * (size_t)(k_max + 1) + (size_t)m] =
+                m < 3 ? -1 : (int64_t)h[(size_t)i * (size_t)k_max + (size_t)m - 1];
+    return MP_OK;
 }
 
 int mp_gamma2_table(int n, int k_max, int64_t *out) {

@@ -591,3 +591,31 @@ def test_gamma2_table(mp):
     for n in (2, 5, 8):
         t = mp.mp_gamma2_table(n, 60)
         assert np.array_equal(t, oracle.gamma2_range(n, 60, threads=THREADS))
+
+
+def test_several_chains_side_by_side(mp, torch):
+    """Chains of several path orders run side by side on library streams give
+    the same min-diagonal sequences as one at a time, and the oracle's for
+    the small orders; the synchronous tables equal the per-order tables."""
+    ns = [9, 3, 6, 1, 8, 7]
+    g = mp.mp_transfer_power_sequences(ns, 60)
+    torch.cuda.synchronize()
+    for i, n in enumerate(ns):
+        _, gi = mp.mp_transfer_power_sequence(n, 60, keep_powers=False)
+        torch.cuda.synchronize()
+        assert torch.equal(g[i], gi), n
+        if n <= 6:
+            _, go = oracle.power_sequence(oracle.build_transfer(n), 60, keep_powers=False,
+                                          threads=THREADS)
+            assert np.array_equal(host(g[i]), go), n
+    t = mp.mp_gamma2_tables([6, 7, 8, 9], 200)
+    for i, n in enumerate([6, 7, 8, 9]):
+        assert np.array_equal(t[i], mp.mp_gamma2_table(n, 200)), n
+    assert mp.mp_gamma2_tables([], 10).shape == (0, 11)
+    with pytest.raises(mp.MinplusError) as e:
+        mp.mp_transfer_power_sequences([5, 5], 10)
+    assert e.value.code == -1
+    with pytest.raises(mp.MinplusError) as e:
+        mp.mp_gamma2_tables([5, 12], 3000)  # 12 * 3000 reaches the INF code
+    assert e.value.code == -4
+
