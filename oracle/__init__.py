@@ -78,6 +78,8 @@ def _load():
     lib.or_power_sequence.restype = I
     lib.or_power_rows.argtypes = [P, I64, P, I64, I, P, I]
     lib.or_power_rows.restype = I
+    lib.or_transfer_power_rows.argtypes = [I, P, I64, I, P, I]
+    lib.or_transfer_power_rows.restype = I64
     lib.or_diff_is_constant.argtypes = [P, P, I64, P]
     lib.or_diff_is_constant.restype = I
     lib.or_recurrence_search.argtypes = [P, I64, I, P, P, P]
@@ -183,6 +185,19 @@ def power_rows(A: np.ndarray, rows, kmax: int, threads: int = 1) -> np.ndarray:
                               _ptr(out), int(threads))
     if r != 0:
         raise MemoryError("oracle power rows failed")
+    return out
+
+
+def transfer_power_rows(n: int, rows, kmax: int, threads: int = 1) -> np.ndarray:
+    """Rows `rows` of A(D_n)^1..A(D_n)^kmax without forming A (its finite
+    entries listed from the word rule): out[t, k-1, :] = (A^k)[rows[t], :]."""
+    N = transfer_size(n)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty((rows.shape[0], kmax, N), dtype=np.int16)
+    r = _load().or_transfer_power_rows(int(n), _ptr(rows), rows.shape[0], int(kmax), _ptr(out),
+                                       int(threads))
+    if r != N:
+        raise MemoryError("oracle transfer power rows failed")
     return out
 
 

@@ -241,13 +241,46 @@ int or_power_sequence(const int16_t *A, int64_t N, int kmax, int16_t *powers,
 /* Rows of the power chain, one row at a time: with right multiplication,
  * row i of P_k = (row i of P_{k-1}) (x) A, so row i of every power follows
  * from row i of A alone.  The product r (x) A is the same triple loop
- * (one row of X), with the INF entries of A skipped by first listing, per
- * row l of A, the columns whose entry is finite.  out receives
- * nrows x kmax x N values: out[(t*kmax + k-1)*N + p] = P_k[rows[t]][p]. */
+ * (one row of X), with the INF entries of A skipped by listing, per row l
+ * of A, the columns whose entry is finite (start/col/val, row l in
+ * [start[l], start[l+1])).  out receives nrows x kmax x N values:
+ * out[(t*kmax + k-1)*N + p] = P_k[rows[t]][p]. */
+static int chain_rows(int64_t N, const int64_t *start, const int32_t *col, const int32_t *val,
+                      const int64_t *rows, int64_t nrows, int kmax, int16_t *out, int threads)
+{
+    int failed = 0;
+    (void)threads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads > 0 ? threads : 1)
+#endif
+    for (int64_t t = 0; t < nrows; ++t) {
+        int16_t *o = out + (size_t)t * (size_t)kmax * (size_t)N;
+        int32_t *acc = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+        if (!acc) { failed = 1; continue; }
+        for (int64_t p = 0; p < N; ++p) o[p] = OR_INF16;
+        for (int64_t e = start[rows[t]]; e < start[rows[t] + 1]; ++e) o[col[e]] = (int16_t)val[e];
+        for (int k = 2; k <= kmax; ++k) {
+            const int16_t *r = o + (size_t)(k - 2) * (size_t)N;
+            for (int64_t p = 0; p < N; ++p) acc[p] = OR_INF16;
+            for (int64_t l = 0; l < N; ++l) {
+                int32_t x = r[l];
+                if (x >= OR_INF16) continue;
+                for (int64_t e = start[l]; e < start[l + 1]; ++e) {
+                    int32_t s2 = x + val[e];
+                    if (s2 < acc[col[e]]) acc[col[e]] = s2;
+                }
+            }
+            int16_t *w = o + (size_t)(k - 1) * (size_t)N;
+            for (int64_t p = 0; p < N; ++p) w[p] = (int16_t)(acc[p] < OR_INF16 ? acc[p] : OR_INF16);
+        }
+        free(acc);
+    }
+    return failed ? -1 : 0;
+}
+
 int or_power_rows(const int16_t *A, int64_t N, const int64_t *rows, int64_t nrows,
                   int kmax, int16_t *out, int threads)
 {
-    (void)threads;
     int64_t *start = (int64_t *)malloc((size_t)(N + 1) * sizeof(int64_t));
     if (!start) return -1;
     int64_t nnz = 0;
@@ -256,37 +289,76 @@ int or_power_rows(const int16_t *A, int64_t N, const int64_t *rows, int64_t nrow
         for (int64_t p = 0; p < N; ++p) nnz += (A[l * N + p] < OR_INF16);
     }
     start[N] = nnz;
-    int64_t *col = (int64_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int64_t));
+    int32_t *col = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
     int32_t *val = (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
     if (!col || !val) { free(start); free(col); free(val); return -1; }
     for (int64_t l = 0, e = 0; l < N; ++l)
         for (int64_t p = 0; p < N; ++p)
-            if (A[l * N + p] < OR_INF16) { col[e] = p; val[e] = A[l * N + p]; ++e; }
-#ifdef _OPENMP
-#pragma omp parallel for schedule(dynamic, 1) num_threads(threads > 0 ? threads : 1)
-#endif
-    for (int64_t t = 0; t < nrows; ++t) {
-        int16_t *o = out + (size_t)t * (size_t)kmax * (size_t)N;
-        int32_t *acc = (int32_t *)malloc((size_t)N * sizeof(int32_t));
-        for (int64_t p = 0; p < N; ++p) o[p] = A[rows[t] * N + p];
-        for (int k = 2; k <= kmax; ++k) {
-            const int16_t *r = o + (size_t)(k - 2) * (size_t)N;
-            for (int64_t p = 0; p < N; ++p) acc[p] = OR_INF16;
-            for (int64_t l = 0; l < N; ++l) {
-                int32_t x = r[l];
-                if (x >= OR_INF16) continue;
-                for (int64_t e = start[l]; e < start[l + 1]; ++e) {
-                    int32_t s = x + val[e];
-                    if (s < acc[col[e]]) acc[col[e]] = s;
-                }
-            }
-            int16_t *w = o + (size_t)(k - 1) * (size_t)N;
-            for (int64_t p = 0; p < N; ++p) w[p] = (int16_t)(acc[p] < OR_INF16 ? acc[p] : OR_INF16);
-        }
-        free(acc);
-    }
+            if (A[l * N + p] < OR_INF16) { col[e] = (int32_t)p; val[e] = A[l * N + p]; ++e; }
+    int r = chain_rows(N, start, col, val, rows, nrows, kmax, out, threads);
     free(start); free(col); free(val);
-    return 0;
+    return r;
+}
+
+/* The same rows for A(D_n) without forming the N x N matrix (path orders
+ * whose A does not fit the host): the finite entries of every row of A are
+ * listed straight from the rule -- word p can follow word q (Section 2.2),
+ * label the zeros of p (Algorithm 1) -- then the rows follow as above.
+ * Returns N, or -1 on error. */
+int64_t or_transfer_power_rows(int n, const int64_t *rows, int64_t nrows, int kmax,
+                               int16_t *out, int threads)
+{
+    int64_t N = or_enumerate_words(n, NULL, 0);
+    if (N <= 0) return -1;
+    uint8_t *L = (uint8_t *)malloc((size_t)(N * n));
+    int64_t *deg = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
+    int32_t **lists = (int32_t **)calloc((size_t)N, sizeof(int32_t *));
+    if (!L || !deg || !lists) { free(L); free(deg); free(lists); return -1; }
+    or_enumerate_words(n, L, N);
+    int failed = 0;
+    (void)threads;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(threads > 0 ? threads : 1)
+#endif
+    {
+        int32_t *tmp = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+        if (!tmp) failed = 1;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int64_t q = 0; q < N; ++q) {
+            if (!tmp) continue;
+            int64_t c = 0;
+            for (int64_t p = 0; p < N; ++p)
+                if (or_can_follow(L + q * n, L + p * n, n)) tmp[c++] = (int32_t)p;
+            lists[q] = (int32_t *)malloc((size_t)(c > 0 ? c : 1) * sizeof(int32_t));
+            if (!lists[q]) { failed = 1; continue; }
+            memcpy(lists[q], tmp, (size_t)c * sizeof(int32_t));
+            deg[q] = c;
+        }
+        free(tmp);
+    }
+    int64_t *start = (int64_t *)malloc((size_t)(N + 1) * sizeof(int64_t));
+    int64_t nnz = 0;
+    if (start) {
+        for (int64_t q = 0; q < N; ++q) { start[q] = nnz; nnz += deg[q]; }
+        start[N] = nnz;
+    }
+    int32_t *col = start ? (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t)) : NULL;
+    int32_t *val = start ? (int32_t *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t)) : NULL;
+    int64_t r = -1;
+    if (!failed && start && col && val) {
+        for (int64_t q = 0; q < N; ++q)
+            for (int64_t e = 0; e < deg[q]; ++e) {
+                int32_t p = lists[q][e];
+                col[start[q] + e] = p;
+                val[start[q] + e] = count_zeros(L + (int64_t)p * n, n);
+            }
+        r = chain_rows(N, start, col, val, rows, nrows, kmax, out, threads) == 0 ? N : -1;
+    }
+    for (int64_t q = 0; q < N; ++q) free(lists[q]);
+    free(lists); free(deg); free(L); free(start); free(col); free(val);
+    return r;
 }
 
 /* ------------------------------------------------------------------ */

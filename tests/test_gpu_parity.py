@@ -210,6 +210,47 @@ def test_transfer_chain_sampled_rows(mp, torch, n):
     assert bool(torch.equal(P[kmax - 1].to(torch.int32), P[kmax - 1 - a].to(torch.int32) + b))
 
 
+def _large_order_rows(mp, torch, n, kmax, nsample):
+    """Powers A^1..A^kmax of a large path order on the GPU, checked on
+    sampled rows (first, last and drawn ones) against the oracle's rows,
+    which it lists from the word rule without forming A."""
+    P, _ = mp.mp_transfer_power_sequence(n, kmax)
+    torch.cuda.synchronize()
+    N = P.shape[1]
+    rng = np.random.default_rng(n)
+    rows = np.unique(np.concatenate([[0, N - 1], rng.choice(N, nsample, replace=False)]))
+    want = oracle.transfer_power_rows(n, rows, kmax, threads=THREADS)
+    for t, i in enumerate(rows):
+        assert np.array_equal(host(P[:, i, :]), want[t]), (n, i)
+    del P
+    torch.cuda.empty_cache()
+
+
+def test_path_order_12_sampled_rows(mp, torch):
+    """n = 12 (N = 52929, 5.6 GB per power): six powers, bit-exact on
+    sampled rows against the oracle."""
+    N = mp.mp_transfer_size(12)
+    free, _ = torch.cuda.mem_get_info()
+    if 8 * N * N * 2 * 1.1 > free:
+        pytest.skip("not enough device memory for six powers")
+    _large_order_rows(mp, torch, 12, 6, 6)
+
+
+@pytest.mark.slow
+def test_path_order_13_sampled_rows(mp, torch):
+    """n = 13 (N = 131562, 34.6 GB per power), the largest path order whose
+    powers fit one GPU: four powers (138 GB) bit-exact on sampled rows
+    against the oracle.  Runs with MP_PATH_ORDER_13=1."""
+    if os.environ.get("MP_PATH_ORDER_13") != "1":
+        pytest.skip("set MP_PATH_ORDER_13=1 to run the path-order-13 rows")
+    torch.cuda.empty_cache()
+    N = mp.mp_transfer_size(13)
+    free, _ = torch.cuda.mem_get_info()
+    if 6 * N * N * 2 * 1.05 > free:
+        pytest.skip("not enough device memory for four powers and the chain buffers")
+    _large_order_rows(mp, torch, 13, 4, 4)
+
+
 def test_power_sequence_generic_matches_transfer(mp, torch):
     """The generic entry point on the dense A(D_n) (it detects the
     column-constant labels) agrees with the transfer chain and the oracle."""

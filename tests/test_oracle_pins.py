@@ -257,6 +257,19 @@ def _rand(rng, shape, inf_frac, hi=31, dtype=np.int16, inf=INF):
     return X
 
 
+def test_transfer_power_rows_match_dense():
+    """The oracle's rows of A(D_n)^k listed straight from the word rule (for
+    path orders whose N x N matrix does not fit the host) equal the rows of
+    the dense oracle chain, for every row of n <= 6 and sampled rows of 7, 8."""
+    for n in range(1, 9):
+        A = oracle.build_transfer(n)
+        N = A.shape[0]
+        rows = np.arange(N) if N <= 225 else np.array(sorted({0, N // 3, N // 2, N - 1}))
+        got = oracle.transfer_power_rows(n, rows, 10, threads=os.cpu_count() or 1)
+        want = oracle.power_rows(A, rows, 10, threads=os.cpu_count() or 1)
+        assert np.array_equal(got, want), n
+
+
 def test_carre_walks():
     """Theorem 1: (A^k)_ij is the least label over walks of length k from
     i to j (INF when there is none).  Brute force over all walks."""
