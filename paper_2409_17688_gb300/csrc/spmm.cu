@@ -271,16 +271,17 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
     int32_t dmin = (int32_t)kInf16;
     for (int k = k0; k < k_end; ++k) {
         const int b = (k - k0) & 1;
+        // one barrier per unit: after it this unit's copies are visible to
+        // all threads and every warp is done with the previous unit, so its
+        // buffer takes the next unit's copies while this one is computed
+        cp_async_wait<0>();
+        __syncthreads();
         if (unit_valid(nxt)) {
             stage_in(a, nxt, idx, smem + (b ^ 1) * buf_bytes, blob_bytes);
             cp_async_commit();
             if (unit_valid(nxt2)) load_row_idx(a, nxt2, idx);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
         }
         const UnitDesc nxt3 = load_unit(a, k + 3, k_end);
-        __syncthreads();
 
         const uint8_t *buf = smem + b * buf_bytes;
         const uint32_t *blob = reinterpret_cast<const uint32_t *>(buf);
@@ -352,7 +353,6 @@ __global__ void __launch_bounds__(kThreads, 1) sparse_step_kernel(SpStepArgs a) 
                     dmin = min(dmin, (int32_t)((qc - c0) & 1 ? v >> 16 : v & 0xFFFFu));
             }
         }
-        __syncthreads();  // everyone is done with buffer b before it is refilled
         cur = nxt;
         nxt = nxt2;
         nxt2 = nxt3;
