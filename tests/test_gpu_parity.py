@@ -4,6 +4,7 @@ Every comparison is integer equality: every entry of every power, every
 product and every gamma_2.  Inputs come from paper_2409_17688_gb300.synth
 (seeded) or from the paper's construction; expected values only from oracle/.
 """
+import ctypes
 import os
 
 import numpy as np
@@ -659,4 +660,34 @@ def test_several_chains_side_by_side(mp, torch):
     with pytest.raises(mp.MinplusError) as e:
         mp.mp_gamma2_tables([5, 12], 3000)  # 12 * 3000 reaches the INF code
     assert e.value.code == -4
+
+
+def test_several_chains_in_a_cuda_graph(mp, torch):
+    """The side-by-side chains can be captured into a CUDA graph (the library
+    streams join the capture through the fork and join events) and replayed;
+    every replay gives the one-at-a-time sequences."""
+    ns = [8, 6, 7]
+    want = [mp.mp_transfer_power_sequence(n, 40, keep_powers=False)[1] for n in ns]
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.empty((len(ns), 40), dtype=torch.int32, device="cuda")
+    ns_arr = (ctypes.c_int * len(ns))(*ns)
+    L = mp.lib()
+
+    def run():
+        mp._check(L.mp_transfer_power_sequences(ns_arr, len(ns), 40, ctypes.c_void_p(g.data_ptr()),
+                                                ctypes.c_void_p(s.cuda_stream)))
+
+    with torch.cuda.stream(s):
+        run()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        run()
+    for _ in range(2):
+        g.fill_(-1)
+        graph.replay()
+        torch.cuda.synchronize()
+        for i in range(len(ns)):
+            assert torch.equal(g[i], want[i]), ns[i]
 
