@@ -319,7 +319,7 @@ def run_ours(args):
            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * K_MAX * len(PATH_ORDERS),
            "api": "mp_gamma2_tables (synchronous, host int64 output)"}
 
-    # ---- configs[1]-style dense products (K1), reported beside the chain
+    # ---- the dense N = 8192 products (K1), reported beside the chain
     dense = dense_extras(mp, torch, flush, stream, peak_viaddmin) if not args.no_dense else None
     batched = batched_extras(mp, torch, flush) if not args.no_batched else None
     serving = serving_extras(mp, torch) if not args.no_serving else None
