@@ -224,7 +224,7 @@ __device__ __forceinline__ void gemm_tile(const TileArgs<T> &a, int64_t bi, int6
             load_tile<T, Cfg>(a.X, a.Y, a.M, a.N, a.K, a.ldx, a.ldy, m0, n0, kn * BK, a.vecx, a.vecy, st);
         const uint32_t *xs = &sm.Xs[buf][0][0];
         const uint16_t *ys = &sm.Ys[buf][0][0];
-#pragma unroll 4
+#pragma unroll
         for (int k = 0; k < BK; ++k) {
             uint32_t xr[TM], yr[TW];
 #pragma unroll
