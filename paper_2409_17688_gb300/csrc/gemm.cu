@@ -38,8 +38,6 @@ template <> struct Elem<uint8_t> {
     static constexpr uint32_t inf = 0xFFu;
 };
 
-__device__ __forceinline__ uint32_t dup16(uint32_t v) { return v | (v << 16); }
-
 // Occupancy mask: mask[bi * nbc + bj] = 1 when the 128 x 128 block (bi, bj)
 // holds at least one finite entry.
 // When dst is given the block is also copied there (leading dimension ldd):
@@ -156,8 +154,9 @@ __device__ __forceinline__ void store_tile(const Stage<Cfg> &st, TileSmem &sm, i
     uint32_t *xs = &sm.Xs[buf][0][0];
 #pragma unroll
     for (int j = 0; j < Cfg::XK / 2; ++j) {
-        xs[(kb + 2 * j) * Cfg::BM + m] = dup16(st.x[j] & 0xFFFFu);
-        xs[(kb + 2 * j + 1) * Cfg::BM + m] = dup16(st.x[j] >> 16);
+        // each 16-bit value in both halves of a word (one byte permute)
+        xs[(kb + 2 * j) * Cfg::BM + m] = __byte_perm(st.x[j], 0, 0x1010);
+        xs[(kb + 2 * j + 1) * Cfg::BM + m] = __byte_perm(st.x[j], 0, 0x3232);
     }
     uint16_t *ys = &sm.Ys[buf][0][0];
 #pragma unroll
