@@ -97,8 +97,16 @@ struct TransferEntry {
     PlanDev plan;
     DevCsr csr;                // device CSR of A(D_n), labels as values
     size_t h2d_bytes = 0, d2h_bytes = 0;
+    // what the narrow plan is built from, on first use
+    HostCsr pcsr;              // rows and columns in the internal row order
+    std::vector<uint16_t> pz;
+    std::vector<int32_t> canon;
+    PlanDev plan_narrow;       // the mirror-representative columns only
+    bool have_narrow = false;
+    int64_t narrow_cols = 0;
 };
 static std::map<std::pair<int, int>, std::unique_ptr<TransferEntry>> g_transfer;
+static std::mutex g_narrow_mu;
 
 // Builds (or finds) the sparse plan of A(D_n) on the current device.  The
 // arcs come from the device arc test; the host only groups rows.
@@ -208,17 +216,64 @@ static int transfer_entry(int n, cudaStream_t s, TransferEntry **out) {
     int cap = 0, blob_cap = 0, grid = 0;
     MP_TRY(sparse_cap_rows(&cap, &blob_cap, &grid));
     PlanHost ph;
-    MP_TRY(plan_build_host(pcsr, true, pz, &canon, cap, blob_cap, grid, &ph));
+    MP_TRY(plan_build_host(pcsr, true, pz, &canon, 0, cap, blob_cap, grid, &ph));
     ph.canon = canon;
     MP_TRY(plan_upload(ph, &e->plan, s, true));
     MP_CUDA_TRY(cudaStreamSynchronize(s));
     e->h2d_bytes = masks.size() * sizeof(WordMasks) + (size_t)(N + 1) * 8 + (size_t)nnz * 2 +
                    e->plan.h2d_bytes;
+    e->pcsr = std::move(pcsr);
+    e->pz = std::move(pz);
+    e->canon = std::move(canon);
     e->d2h_bytes = (size_t)N * 8 + (size_t)nnz * 4;
     std::lock_guard<std::mutex> lk(g_mu);
     auto &slot = g_transfer[{dev, n}];
     if (!slot) slot = std::move(e);
     *out = slot.get();
+    return MP_OK;
+}
+
+// Reading each column word backwards maps correct words to correct words
+// and arcs to arcs with the same label (the path P_n is symmetric, and the
+// zero count does not change), so A[R q][R p] = A[q][p] for that reversal R,
+// every power satisfies P_k[R q][R c] = P_k[q][c], and the diagonal entry of
+// row q equals that of row R q.  With left multiplication the columns of a
+// power depend only on the same columns of the previous one, so a chain that
+// keeps one column of every pair {c, R c} (the one with c <= R c) still sees
+// every diagonal value: the narrow plan does about half the work of a full
+// one and serves every call that needs only the minimum diagonals.
+static int narrow_plan(TransferEntry *te, cudaStream_t s, const PlanDev **out) {
+    std::lock_guard<std::mutex> lk(g_narrow_mu);
+    if (!te->have_narrow) {
+        const int n = te->n;
+        const int64_t N = te->N;
+        std::map<uint32_t, int64_t> index;
+        for (int64_t c = 0; c < N; ++c) index[te->words[(size_t)c]] = c;
+        std::vector<int32_t> colpos((size_t)N, -1);
+        int64_t ncols = 0;
+        for (int64_t c = 0; c < N; ++c) {
+            const uint32_t w = te->words[(size_t)c];
+            uint32_t r = 0;
+            for (int i = 0; i < n; ++i) r |= ((w >> (2 * i)) & 3u) << (2 * (n - 1 - i));
+            auto it = index.find(r);
+            if (it == index.end()) return set_error(MP_EINVAL, "reversed word not correct (n = %d)", n);
+            if (c <= it->second) colpos[(size_t)c] = (int32_t)ncols++;
+        }
+        // per internal row, the buffer column of its diagonal entry (or none)
+        std::vector<int32_t> dcol((size_t)N);
+        for (int64_t i = 0; i < N; ++i) dcol[(size_t)i] = colpos[(size_t)te->canon[(size_t)i]];
+        int cap = 0, blob_cap = 0, grid = 0;
+        MP_TRY(sparse_cap_rows(&cap, &blob_cap, &grid));
+        PlanHost ph;
+        MP_TRY(plan_build_host(te->pcsr, true, te->pz, &dcol, ncols, cap, blob_cap, grid, &ph));
+        ph.canon = te->canon;
+        ph.colpos = colpos;
+        MP_TRY(plan_upload(ph, &te->plan_narrow, s, true));
+        MP_CUDA_TRY(cudaStreamSynchronize(s));
+        te->narrow_cols = ncols;
+        te->have_narrow = true;
+    }
+    *out = &te->plan_narrow;
     return MP_OK;
 }
 
@@ -345,7 +400,10 @@ static int transfer_recurrence(int n, int K, Recurrence *out, cudaStream_t s) {
 // (slot >= N*N elements; the caller may pad slots for alignment).
 static int transfer_chain_direct(TransferEntry *te, int k_max, int16_t *powers_opt, size_t slot,
                                  int32_t *gdiag_opt, cudaStream_t s) {
-    const PlanDev &plan = te->plan;
+    // without powers to write, the narrow chain gives the same diagonals
+    const PlanDev *pp = &te->plan;
+    if (!powers_opt) MP_TRY(narrow_plan(te, s, &pp));
+    const PlanDev &plan = *pp;
     if (gdiag_opt) MP_TRY(launch_fill_i32(gdiag_opt, k_max, (int32_t)kInf16, s));
     DevBuf B;
     MP_TRY(B.alloc(2 * (size_t)plan.N * (size_t)plan.ldb * 2, s));
@@ -635,7 +693,7 @@ int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max, int16_t *p
     int cap = 0, blob_cap = 0, grid = 0;
     MP_TRY(sparse_cap_rows(&cap, &blob_cap, &grid));
     PlanHost ph;
-    MP_TRY(plan_build_host(csr, colconst, z, nullptr, cap, blob_cap, grid, &ph));
+    MP_TRY(plan_build_host(csr, colconst, z, nullptr, 0, cap, blob_cap, grid, &ph));
     PlanDev plan;
     MP_TRY(plan_upload(ph, &plan, s, false));
     DevBuf B;

@@ -387,11 +387,13 @@ __global__ void init_from_dense_kernel(const int16_t *__restrict__ A, int64_t N,
 
 // The same from CSR (transfer matrices are never formed densely here).
 // Rows are in the chain's internal order (row q of the CSR is internal row
-// q, whose caller row is canon[q]); columns are the caller's.
+// q, whose caller row is canon[q]); columns are the caller's, placed at
+// colpos[p] in a narrow chain (dropped where it is -1).
 __global__ void init_from_csr_kernel(const int64_t *__restrict__ row_ptr,
                                      const int32_t *__restrict__ col, const int16_t *__restrict__ val,
                                      int64_t N, int64_t ldb, const uint16_t *__restrict__ z,
-                                     const int32_t *__restrict__ canon, uint16_t *__restrict__ B,
+                                     const int32_t *__restrict__ canon,
+                                     const int32_t *__restrict__ colpos, uint16_t *__restrict__ B,
                                      int16_t *__restrict__ user0, int32_t *__restrict__ g0) {
     const int64_t q = blockIdx.x;
     const int64_t qc = canon ? (int64_t)canon[q] : q;
@@ -404,7 +406,8 @@ __global__ void init_from_csr_kernel(const int64_t *__restrict__ row_ptr,
     for (int64_t e = row_ptr[q] + threadIdx.x; e < row_ptr[q + 1]; e += blockDim.x) {
         const int64_t p = col[e];
         const uint32_t v = (uint32_t)(uint16_t)val[e];
-        B[q * ldb + p] = (uint16_t)(v + zq);
+        const int64_t j = colpos ? (int64_t)colpos[p] : p;
+        if (j >= 0) B[q * ldb + j] = (uint16_t)(v + zq);
         if (user0) user0[qc * N + p] = (int16_t)v;
         if (g0 && p == qc) atomicMin(g0, (int32_t)v);
     }
@@ -484,6 +487,11 @@ int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent) 
         if ((int64_t)h.canon.size() != h.N) return set_error(MP_EINVAL, "row order of the wrong length");
         MP_TRY(up(d->canon, h.canon.data(), h.canon.size() * 4));
     }
+    d->narrow = !h.colpos.empty();
+    if (d->narrow) {
+        if ((int64_t)h.colpos.size() != h.N) return set_error(MP_EINVAL, "column map of the wrong length");
+        MP_TRY(up(d->colpos, h.colpos.data(), h.colpos.size() * 4));
+    }
     d->grid = h.grid;
     d->h2d_bytes = (h.grp_row0.size() + h.grp_stage0.size() + h.stage_u0.size() + h.blob.size() +
                     h.urows.size() + h.cta_unit0.size()) * 4 + h.blob_off.size() * 8 +
@@ -509,6 +517,7 @@ int sparse_cap_rows(int *cap_rows, int *blob_cap, int *grid) {
 
 int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,
                 int32_t *gdiag, cudaStream_t s) {
+    if (p.narrow && user_out) return set_error(MP_EINVAL, "a narrow chain has no full powers to write");
     DeviceInfo di;
     MP_TRY(device_info(&di));
     int *status = nullptr;
@@ -577,9 +586,11 @@ int sparse_init_from_csr(const PlanDev &p, const int64_t *row_ptr, const int32_t
                          cudaStream_t s) {
     // one block per row so the INF fill precedes the arc scatter within the block
     dim3 grid((unsigned)p.N, 1);
+    if (p.narrow && user0) return set_error(MP_EINVAL, "a narrow chain has no full powers to write");
     init_from_csr_kernel<<<grid, 256, 0, s>>>(row_ptr, col, val, p.N, p.ldb,
                                               p.colconst ? p.z.as<uint16_t>() : nullptr,
-                                              p.permuted ? p.canon.as<int32_t>() : nullptr, B0,
+                                              p.permuted ? p.canon.as<int32_t>() : nullptr,
+                                              p.narrow ? p.colpos.as<int32_t>() : nullptr, B0,
                                               user0, g0);
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;

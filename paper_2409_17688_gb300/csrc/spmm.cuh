@@ -69,6 +69,9 @@ struct PlanHost {
     // (and diagonal column) of the caller's matrices that internal row i
     // holds.  Empty: the identity.  Columns are never reordered.
     std::vector<int32_t> canon;
+    // A narrow chain keeps only some columns: colpos[c] is the buffer column
+    // of caller column c, or -1.  Empty: all columns, in the caller's order.
+    std::vector<int32_t> colpos;
 };
 struct PlanDev {
     int64_t N = 0, ldb = 0, nnz = 0;
@@ -79,6 +82,8 @@ struct PlanDev {
     DevBuf grp_row0, grp_stage0, stage_u0, blob_off, blob, uoff16, z, units, cta_unit0;
     DevBuf canon;          // empty: identity row order
     bool permuted = false;
+    DevBuf colpos;         // empty: all columns
+    bool narrow = false;
 };
 
 struct SpStepArgs {
@@ -95,8 +100,12 @@ struct SpStepArgs {
     int *status;
 };
 
+// canon: per row, the word written to the blob (the caller row, which is also
+// the buffer column of the row's diagonal entry), NULL for the identity;
+// ncols: columns of the chain's buffers (<= 0: N).
 int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_t> &z,
-                    const std::vector<int32_t> *canon, int cap_rows, int blob_cap, int grid, PlanHost *out, int cluster_max = 4);
+                    const std::vector<int32_t> *canon, int64_t ncols, int cap_rows, int blob_cap,
+                    int grid, PlanHost *out, int cluster_max = 4);
 int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent);
 int sparse_cap_rows(int *cap_rows, int *blob_cap, int *grid);
 int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,

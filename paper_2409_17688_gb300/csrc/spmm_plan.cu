@@ -12,9 +12,10 @@
 namespace mp {
 
 int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_t> &z,
-                    const std::vector<int32_t> *canon,
+                    const std::vector<int32_t> *canon, int64_t ncols,
                     int cap_rows, int blob_cap, int grid, PlanHost *out, int cluster_max) {
     const int64_t N = csr.N;
+    if (ncols <= 0) ncols = N;
     const int umax = cap_rows - 1;  // the last buffer row is the INF padding row
     if (umax < 1) return set_error(MP_EINVAL, "shared-memory buffer too small");
     if ((int64_t)cap_rows * kRowBytes > (int64_t)kEntOffset + 1)
@@ -27,7 +28,7 @@ int plan_build_host(const HostCsr &csr, bool colconst, const std::vector<uint16_
     P.blob_cap = blob_cap;
     P.z = z;
     if (P.z.size() != (size_t)N) P.z.assign((size_t)N, 0);
-    P.ldb = ((N + kChunk - 1) / kChunk) * kChunk;
+    P.ldb = ((ncols + kChunk - 1) / kChunk) * kChunk;
     P.nchunks = (int)(P.ldb / kChunk);
     P.nnz = csr.row_ptr[N];
 

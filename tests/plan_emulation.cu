@@ -59,7 +59,7 @@ int main(int argc, char **argv) {
         csr.row_ptr.push_back((int64_t)csr.col.size());
     }
     PlanHost P;
-    if (plan_build_host(csr, true, z, nullptr, cap, 6144, 7, &P, cl) != MP_OK) return 3;
+    if (plan_build_host(csr, true, z, nullptr, 0, cap, 6144, 7, &P, cl) != MP_OK) return 3;
     fprintf(stderr, "groups %d stages %zu units %zu\n", P.ngroups, P.stage_u0.size() - 1,
             P.units.size());
     const int INF = 0x7FFF;

@@ -691,3 +691,22 @@ def test_several_chains_in_a_cuda_graph(mp, torch):
         for i in range(len(ns)):
             assert torch.equal(g[i], want[i]), ns[i]
 
+
+@pytest.mark.parametrize("n", [2, 5, 7, 8, 9])
+def test_mirror_columns_chain_matches_full(mp, torch, n):
+    """Without powers to write, the chain keeps one column of every mirror
+    pair of words (the reversal symmetry of A(D_n)); its min-diagonals equal
+    those of the full chain, which writes every power."""
+    _, g_narrow = mp.mp_transfer_power_sequence(n, 80, keep_powers=False)
+    P, g_full = mp.mp_transfer_power_sequence(n, 80, keep_powers=True)
+    torch.cuda.synchronize()
+    assert torch.equal(g_narrow, g_full), n
+    # the symmetry itself, on the full powers: P_k[R q][R c] = P_k[q][c]
+    words = [int(w) for w in mp.mp_transfer_words(n)]
+    index = {w: i for i, w in enumerate(words)}
+    R = [index[sum(((w >> (2 * j)) & 3) << (2 * (n - 1 - j)) for j in range(n))] for w in words]
+    Rt = torch.tensor(R, device="cuda")
+    for k in (1, 7, 80):
+        Pk = P[k - 1]
+        assert torch.equal(Pk[Rt][:, Rt], Pk), (n, k)
+
