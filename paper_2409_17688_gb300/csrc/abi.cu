@@ -518,35 +518,43 @@ int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
 // n0 of Algorithm 4 and the period a with its constant b (Lemma 1 carries
 // it to every later power).
 static int transfer_recurrence_ring(int n, int k_limit, int R, Recurrence *out, cudaStream_t s) {
+    // The ring is the chain itself, narrow: slot (k - 1) % R holds the k-th
+    // buffer z + P_k on the mirror-representative columns.  Labels cancel in
+    // a difference, and a difference that is constant on those columns is
+    // constant on all of them (the dropped columns repeat kept ones), so
+    // Algorithm 3's test runs on the slots directly and no full power is
+    // ever written.
     const int64_t N = words_of(n);
-    const size_t mat = (size_t)N * (size_t)N;
+    const double cols_est = 0.5625 * (double)N + 64.0;  // a little over N / 2
     size_t free_b = 0;
     MP_TRY(device_free_bytes(s, &free_b));
-    const double need = (double)mat * 2.0 * R + 4.0 * (double)N * (double)(N + 64);
-    if (need > 0.9 * (double)free_b)
+    if ((double)N * cols_est * 2.0 * R > 0.9 * (double)free_b)
         return set_error(MP_ENOMEM, "a ring of %d powers of N = %lld does not fit the free memory", R,
                          (long long)N);
     TransferEntry *te;
     MP_TRY(transfer_entry(n, s, &te));
-    const PlanDev &plan = te->plan;
-    DevBuf ring, g, d, B;
-    MP_TRY(ring.alloc(mat * 2 * (size_t)R, s));
+    const PlanDev *pp = nullptr;
+    MP_TRY(narrow_plan(te, s, &pp));
+    const PlanDev &plan = *pp;
+    const size_t slab = (size_t)plan.N * (size_t)plan.ldb;
+    DevBuf ring, g, d;
+    MP_TRY(ring.alloc(slab * 2 * (size_t)R, s));
     MP_TRY(g.alloc(sizeof(int32_t) * (size_t)k_limit, s));
     MP_TRY(d.alloc(sizeof(int32_t) * 4, s));
-    MP_TRY(B.alloc(2 * (size_t)plan.N * (size_t)plan.ldb * 2, s));
-    uint16_t *buf[2] = {B.as<uint16_t>(), B.as<uint16_t>() + (size_t)plan.N * (size_t)plan.ldb};
-    auto slot = [&](int k) { return ring.as<int16_t>() + (size_t)((k - 1) % R) * mat; };
+    auto slot = [&](int k) { return ring.as<uint16_t>() + (size_t)((k - 1) % R) * slab; };
     MP_TRY(launch_fill_i32(g.as<int32_t>(), k_limit, (int32_t)kInf16, s));
     MP_TRY(sparse_init_from_csr(plan, te->csr.row_ptr.as<int64_t>(), te->csr.col.as<int32_t>(),
-                                te->csr.val.as<int16_t>(), buf[0], slot(1), g.as<int32_t>(), s));
+                                te->csr.val.as<int16_t>(), slot(1), nullptr, g.as<int32_t>(), s));
     Recurrence r;
     bool found = false;
     for (int k = 2; k <= k_limit && !found; ++k) {
-        MP_TRY(sparse_step(plan, buf[(k - 2) & 1], buf[(k - 1) & 1], slot(k), g.as<int32_t>() + (k - 1), s));
+        MP_TRY(sparse_step(plan, slot(k - 1), slot(k), nullptr, g.as<int32_t>() + (k - 1), s));
         for (int a = 1; a < R && a < k; ++a) {
             bool c;
             int32_t b;
-            MP_TRY(diff_constant(slot(k), slot(k - a), (int64_t)mat, d.as<int32_t>(), s, &c, &b));
+            MP_TRY(diff_constant(reinterpret_cast<const int16_t *>(slot(k)),
+                                 reinterpret_cast<const int16_t *>(slot(k - a)), (int64_t)slab,
+                                 d.as<int32_t>(), s, &c, &b));
             if (c) {
                 r.a = a;
                 r.b = b;
