@@ -142,7 +142,13 @@ int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max,
 /* The same chain for the transfer matrix A(D_n) itself, built on the device
  * from n (no dense A is formed).  The plan for n is cached per device after
  * the first call.  powers_opt / gdiag_opt as above with N = |C_n|.
- * Synchronizes the stream on the first call for a given n. */
+ * With powers_opt NULL the chain computes only one column of every pair
+ * {w, reversed w} of column words: reading words backwards is an
+ * automorphism of A(D_n), so the dropped columns repeat kept ones, every
+ * diagonal value is among the kept columns, and gdiag is the same; the work
+ * is about half (a second plan, cached likewise, is built on the first such
+ * call).  Synchronizes the stream on the first call of either kind for a
+ * given n. */
 int mp_transfer_power_sequence(int n, int k_max, int16_t *powers_opt,
                                int32_t *gdiag_opt, void *stream);
 

@@ -710,3 +710,34 @@ def test_mirror_columns_chain_matches_full(mp, torch, n):
         Pk = P[k - 1]
         assert torch.equal(Pk[Rt][:, Rt], Pk), (n, k)
 
+
+def test_threads_share_the_plan_caches(mp, torch):
+    """Host threads asking for the same path orders at once (both chain
+    kinds, plans built on first use) get the single-thread results."""
+    import threading
+    want = {n: mp.mp_gamma2_table(n, 60) for n in (4, 5, 6, 7)}
+    results, errors = {}, []
+
+    def work(i):
+        try:
+            torch.cuda.set_device(0)
+            n = 4 + i % 4
+            results[i] = mp.mp_gamma2_table(n, 60)
+            P, g = mp.mp_transfer_power_sequence(n, 20)
+            torch.cuda.synchronize()
+            results[(i, "g")] = (n, host(g))
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(8)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for i in range(8):
+        n = 4 + i % 4
+        assert np.array_equal(results[i], want[n]), n
+        n2, g = results[(i, "g")]
+        assert np.array_equal(g[2:], want[n2][3:21]), n2
+
