@@ -286,7 +286,10 @@ int mp_tuning_get(int32_t *table);
  * current device: A^1..A^B and, transposed, A^{tB} for t = 1..T, with
  * B = ceil(sqrt(max_m)) and T = ceil(max_m / B).  m <= B is answered from
  * the min-diagonals kept on the host; every larger m <= max_m is one
- * streaming min of A^x + (A^{tB})^T over two resident powers (m = x + tB).  A worker thread batches the queries whose path order is
+ * streaming min of A^x + (A^{tB})^T over two resident powers (m = x + tB),
+ * read on the rows of one word of every mirror pair only (reading a word
+ * backwards is an automorphism of A(D_n), so the other rows repeat the same
+ * terms).  A worker thread batches the queries whose path order is
  * resident into one launch (two batches may be in flight); a query for a
  * path order that is not resident admits it: its footprint
  * (B + T) * N^2 * 2 bytes (slots rounded to 8 entries) is checked against hbm_budget, idle path

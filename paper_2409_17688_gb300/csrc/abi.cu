@@ -247,18 +247,12 @@ static int narrow_plan(TransferEntry *te, cudaStream_t s, const PlanDev **out) {
     if (!te->have_narrow) {
         const int n = te->n;
         const int64_t N = te->N;
-        std::map<uint32_t, int64_t> index;
-        for (int64_t c = 0; c < N; ++c) index[te->words[(size_t)c]] = c;
+        std::vector<int64_t> partner;
+        MP_TRY(mirror_words(n, te->words, &partner));
         std::vector<int32_t> colpos((size_t)N, -1);
         int64_t ncols = 0;
-        for (int64_t c = 0; c < N; ++c) {
-            const uint32_t w = te->words[(size_t)c];
-            uint32_t r = 0;
-            for (int i = 0; i < n; ++i) r |= ((w >> (2 * i)) & 3u) << (2 * (n - 1 - i));
-            auto it = index.find(r);
-            if (it == index.end()) return set_error(MP_EINVAL, "reversed word not correct (n = %d)", n);
-            if (c <= it->second) colpos[(size_t)c] = (int32_t)ncols++;
-        }
+        for (int64_t c = 0; c < N; ++c)
+            if (c <= partner[(size_t)c]) colpos[(size_t)c] = (int32_t)ncols++;
         // per internal row, the buffer column of its diagonal entry (or none)
         std::vector<int32_t> dcol((size_t)N);
         for (int64_t i = 0; i < N; ++i) dcol[(size_t)i] = colpos[(size_t)te->canon[(size_t)i]];

@@ -110,6 +110,8 @@ struct WordMasks {
     uint16_t zero, one, two, pad;
 };
 void word_masks(int n, const std::vector<uint32_t> &words, std::vector<WordMasks> *out);
+// partner[c] = index of word c read backwards (an involution of the words).
+int mirror_words(int n, const std::vector<uint32_t> &words, std::vector<int64_t> *partner);
 
 // ------------------------------------------------------- kernels (launchers)
 int launch_build_transfer(int n, const WordMasks *d_masks, int64_t N, int16_t *A,

@@ -48,9 +48,9 @@ double now_s() {
 }
 
 struct TraceJob {
-    const int16_t *X;   // A^x, N*N entries
-    const int16_t *YT;  // (A^{tB})^T, N*N entries
-    int64_t count;      // N*N
+    const int16_t *X;   // A^x, representative rows first
+    const int16_t *YT;  // (A^{tB})^T, rows in the same order
+    int64_t count;      // representative rows x N
     int64_t cta0;       // first CTA of this job
 };
 
@@ -114,6 +114,14 @@ __global__ void transpose_kernel(const int16_t *__restrict__ in, int64_t ld_in,
     }
 }
 
+// out row r = in row rows[r] (N entries each, both packed); one CTA per row.
+__global__ void row_gather_kernel(const int16_t *__restrict__ in, const int32_t *__restrict__ rows,
+                                  int64_t N, int16_t *__restrict__ out) {
+    const int16_t *src = in + (int64_t)rows[blockIdx.x] * N;
+    int16_t *dst = out + (int64_t)blockIdx.x * N;
+    for (int64_t c = threadIdx.x; c < N; c += blockDim.x) dst[c] = src[c];
+}
+
 __global__ void fill_inf_kernel(int32_t *p, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         p[i] = (int32_t)kInf16;
@@ -145,6 +153,7 @@ struct PathState {
     size_t bytes = 0;
     int16_t *powers = nullptr;  // B + T slots of `slot` entries: A^1..A^B, then (A^{tB})^T
     size_t slot = 0;            // N*N rounded up to 8 entries (16-byte aligned slots)
+    int64_t nrep = 0;           // rows a trace reads: one word of every mirror pair
     std::vector<int32_t> diag;  // min diag A^m, m = 1..B
     std::atomic<int> built{0};  // set by the builder thread (1 ok, -1 failed)
     int build_err = 0;
@@ -218,7 +227,13 @@ int64_t words_count(int n) {
 
 // Builder thread body, on a private stream: baby steps by the sparse chain
 // (with their min-diagonals), giant steps by dense products in padded
-// scratch, each stored transposed.
+// scratch, each stored transposed.  Last, the rows of every slot are put in
+// one order that lists first one word of every mirror pair {q, R q} (R reads
+// a word backwards).  R is an automorphism of A(D_n), so P_x[R i][R l] =
+// P_x[i][l] for every power, and the trace term P_x[i][l] + P_y[l][i] of the
+// pair (i, l) equals that of (R i, R l): the minimum over the representative
+// rows and all columns is the minimum over all of them, and a trace reads
+// about half of each slot.
 void build_path(mp_server *sv, PathState *ps) {
     cudaSetDevice(sv->device);
     cudaStream_t s = nullptr;
@@ -262,6 +277,33 @@ void build_path(mp_server *sv, PathState *ps) {
         if (cudaGetLastError() != cudaSuccess) rc = MP_ECUDA;
         prev = dst;
     }
+    // representative rows (i <= R i) first; the rows after them are never read
+    int32_t *d_rows = nullptr;
+    std::vector<int32_t> reps;
+    if (rc == MP_OK) {
+        std::vector<uint32_t> w;
+        enumerate_words(ps->n, &w);
+        std::vector<int64_t> partner;
+        rc = mirror_words(ps->n, w, &partner);
+        for (int64_t i = 0; rc == MP_OK && i < N; ++i)
+            if (i <= partner[(size_t)i]) reps.push_back((int32_t)i);
+    }
+    if (rc == MP_OK && cudaMallocAsync((void **)&d_rows, sizeof(int32_t) * reps.size(), s) != cudaSuccess)
+        rc = MP_ENOMEM;
+    if (rc == MP_OK && cudaMemcpyAsync(d_rows, reps.data(), sizeof(int32_t) * reps.size(),
+                                       cudaMemcpyHostToDevice, s) != cudaSuccess)
+        rc = MP_ECUDA;
+    const int64_t nrep = (int64_t)reps.size();
+    for (int k = 0; rc == MP_OK && k < sv->B + sv->T; ++k) {
+        int16_t *slot = ps->powers + (size_t)k * ps->slot;
+        row_gather_kernel<<<(unsigned)nrep, 256, 0, s>>>(slot, d_rows, N, tmp);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(slot, tmp, sizeof(int16_t) * (size_t)(nrep * N), cudaMemcpyDeviceToDevice,
+                            s) != cudaSuccess)
+            rc = MP_ECUDA;
+    }
+    ps->nrep = nrep;
+    if (d_rows) cudaFreeAsync(d_rows, s);
     if (tmp) cudaFreeAsync(tmp, s);
     if (gd) cudaFreeAsync(gd, s);
     if (s) {
@@ -365,7 +407,7 @@ int launch_batch(mp_server *sv, Batch &b, std::vector<Query> &ready) {
         TraceJob &j = b.h_jobs[i];
         j.X = ps->powers + (size_t)(x - 1) * ps->slot;
         j.YT = ps->powers + (size_t)(sv->B + t - 1) * ps->slot;
-        j.count = ps->N * ps->N;
+        j.count = ps->nrep * ps->N;
         j.cta0 = ctas;
         ctas += (j.count + kTraceSpan - 1) / kTraceSpan;
         ps->inflight++;

@@ -10,6 +10,8 @@
 // pairs at once in bit-sliced form: for each word the positions holding 0,
 // 1 and 2 are three n-bit masks, and the "neighbours equal to 0" counts of
 // every position come from shifted masks.
+#include <map>
+
 #include "mp_internal.cuh"
 
 namespace mp {
@@ -52,6 +54,23 @@ void word_masks(int n, const std::vector<uint32_t> &words, std::vector<WordMasks
         }
         (*out)[t] = m;
     }
+}
+
+// Reading a word backwards keeps it correct (the forbidden windows and the
+// end rules are mirror images of each other), so reversal is an involution
+// on the correct words; partner[c] is the index of word c read backwards.
+int mirror_words(int n, const std::vector<uint32_t> &words, std::vector<int64_t> *partner) {
+    std::map<uint32_t, int64_t> index;
+    for (size_t c = 0; c < words.size(); ++c) index[words[c]] = (int64_t)c;
+    partner->assign(words.size(), -1);
+    for (size_t c = 0; c < words.size(); ++c) {
+        uint32_t r = 0;
+        for (int i = 0; i < n; ++i) r |= ((words[c] >> (2 * i)) & 3u) << (2 * (n - 1 - i));
+        auto it = index.find(r);
+        if (it == index.end()) return set_error(MP_EINVAL, "reversed word not correct (n = %d)", n);
+        (*partner)[c] = it->second;
+    }
+    return MP_OK;
 }
 
 // Arc q -> p ("p can follow q") in bit-sliced form.  Bit i is letter i+1.
