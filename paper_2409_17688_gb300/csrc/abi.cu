@@ -104,7 +104,16 @@ struct TransferEntry {
     PlanDev plan_narrow;       // the mirror-representative columns only
     bool have_narrow = false;
     int64_t narrow_cols = 0;
+    CircuitHost circuit;       // reuse circuit of the rows (empty: none)
 };
+
+// Steps of transfer chains run on the reuse circuit where a column chunk fits
+// shared memory; MP_SPARSE_CIRCUIT=0 in the environment keeps the gather
+// plan for every step.
+static bool circuit_enabled() {
+    const char *v = getenv("MP_SPARSE_CIRCUIT");
+    return !(v && v[0] == '0');
+}
 static std::map<std::pair<int, int>, std::unique_ptr<TransferEntry>> g_transfer;
 static std::mutex g_narrow_mu;
 
@@ -220,6 +229,27 @@ static int transfer_entry(int n, cudaStream_t s, TransferEntry **out) {
     ph.canon = canon;
     MP_TRY(plan_upload(ph, &e->plan, s, true));
     MP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (circuit_enabled() && 2 * N + 1 <= 0xFFFF) {
+        // rows are internal, and so are the gathered rows of pcsr; chunks of
+        // 8 columns (measured faster than 16 at n = 8: more CTAs, less
+        // shared memory each), 16 where asked by MP_CIRCUIT_WIDTH
+        CircuitCover cv;
+        MP_TRY(circuit_cover_host(pcsr, &cv));
+        const char *wenv = getenv("MP_CIRCUIT_WIDTH");
+        const int only = wenv ? atoi(wenv) : 0;
+        for (int w : {8, 16}) {
+            if (only && w != only) continue;
+            CircuitHost ch;
+            MP_TRY(circuit_slice_host(cv, w, &ch));
+            size_t bytes = 0;
+            MP_TRY(circuit_smem_bytes(ch, &bytes));
+            if (bytes > 0 && e->plan.ldb % w == 0) {
+                e->circuit = std::move(ch);
+                break;
+            }
+        }
+        if (e->circuit.W > 0) MP_TRY(circuit_upload(e->circuit, pz, canon, canon, &e->plan, s));
+    }
     e->h2d_bytes = masks.size() * sizeof(WordMasks) + (size_t)(N + 1) * 8 + (size_t)nnz * 2 +
                    e->plan.h2d_bytes;
     e->pcsr = std::move(pcsr);
@@ -264,6 +294,8 @@ static int narrow_plan(TransferEntry *te, cudaStream_t s, const PlanDev **out) {
         ph.colpos = colpos;
         MP_TRY(plan_upload(ph, &te->plan_narrow, s, true));
         MP_CUDA_TRY(cudaStreamSynchronize(s));
+        if (te->circuit.W > 0 && te->plan_narrow.ldb % te->circuit.W == 0)
+            MP_TRY(circuit_upload(te->circuit, te->pz, dcol, te->canon, &te->plan_narrow, s));
         te->narrow_cols = ncols;
         te->have_narrow = true;
     }

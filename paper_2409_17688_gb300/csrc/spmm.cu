@@ -517,6 +517,7 @@ int sparse_cap_rows(int *cap_rows, int *blob_cap, int *grid) {
 
 int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,
                 int32_t *gdiag, cudaStream_t s) {
+    if (p.circuit.ready) return circuit_step(p, Bin, Bout, user_out, gdiag, s);
     if (p.narrow && user_out) return set_error(MP_EINVAL, "a narrow chain has no full powers to write");
     DeviceInfo di;
     MP_TRY(device_info(&di));

@@ -73,6 +73,48 @@ struct PlanHost {
     // of caller column c, or -1.  Empty: all columns, in the caller's order.
     std::vector<int32_t> colpos;
 };
+// The reuse circuit of a column-constant sparse A (circuit.cu).  Row q of
+// A (x) X is the minimum, over the rows p with an arc q -> p, of z_p + X[p];
+// when the arcs out of q' are a subset of those out of q, that minimum over
+// q' is a part of q's, so row q is the minimum of a few rows of the result
+// itself (its cover) and of the rows X[p] the cover leaves out.  Rows are
+// computed in levels (a row after every row of its cover), one column chunk
+// of W columns per CTA with the chunk of X, of the result and the circuit
+// itself in shared memory.
+struct CircuitCover {
+    int64_t N = 0;
+    int levels = 0;
+    // per row its list: rows of X (p < N) and rows of the result (N + q')
+    std::vector<std::vector<uint32_t>> lists;
+    std::vector<int> level;
+    int64_t reads = 0, cover_reads = 0;  // list entries, of them result rows
+};
+struct CircuitHost {
+    int64_t N = 0;
+    int W = 0, levels = 0;
+    std::vector<int32_t> level_slice0;  // [levels + 1] first slice of each level
+    // per slice {first vector of its later entry blocks in ents, entry blocks
+    // per row}; a slice has 32 / (W / 8) rows
+    std::vector<uint32_t> slices;
+    std::vector<uint32_t> rows;         // per slice, its rows (0xFFFFFFFF: none)
+    // Entry blocks: per row, 8 row indices of the shared-memory image (X rows
+    // 0..N-1, result rows N..2N-1, 2N the INF row).  first holds every
+    // slice's first block (row i of slice s at s * rows-per-slice + i), ents
+    // the later blocks, block by block and row by row.
+    std::vector<uint16_t> first, ents;
+    int64_t reads = 0, cover_reads = 0;  // row reads of the circuit, of them result rows
+};
+struct CircuitDev {
+    int W = 0, levels = 0;
+    int64_t nslices = 0;
+    // the circuit as one blob, copied whole into shared memory: level
+    // starts, slice descriptors, per slot {row | label << 16, diagonal
+    // column | caller row << 16}, first entry blocks, later entry blocks
+    DevBuf meta;
+    uint32_t meta_bytes = 0, off_slices = 0, off_rowinfo = 0, off_first = 0, off_ents = 0;
+    bool ready = false;
+};
+
 struct PlanDev {
     int64_t N = 0, ldb = 0, nnz = 0;
     int ngroups = 0, nchunks = 0, cap_rows = 0, blob_cap = 0;
@@ -84,6 +126,7 @@ struct PlanDev {
     bool permuted = false;
     DevBuf colpos;         // empty: all columns
     bool narrow = false;
+    CircuitDev circuit;    // used for the steps when ready
 };
 
 struct SpStepArgs {
@@ -116,5 +159,21 @@ int sparse_init_from_csr(const PlanDev &p, const int64_t *row_ptr, const int32_t
                          const int16_t *val, uint16_t *B0, int16_t *user0, int32_t *g0,
                          cudaStream_t s);
 int dense_to_csr(const int16_t *A, int64_t N, HostCsr *csr, DevCsr *dcsr, cudaStream_t s);
+
+// The covers and levels of a column-constant CSR (a row's arcs may not
+// repeat), and their slicing for chunks of W columns (8 or 16).
+int circuit_cover_host(const HostCsr &csr, CircuitCover *out);
+int circuit_slice_host(const CircuitCover &cv, int W, CircuitHost *out);
+int circuit_build_host(const HostCsr &csr, int W, CircuitHost *out);
+// Shared memory a step takes with this circuit (0: too large for the device).
+int circuit_smem_bytes(const CircuitHost &h, size_t *bytes);
+// Attach a circuit to a plan: z = the rows' labels, diagcol[q] = the buffer
+// column of internal row q's diagonal entry or -1, caller[q] = the caller's
+// row of internal row q.
+int circuit_upload(const CircuitHost &h, const std::vector<uint16_t> &z,
+                   const std::vector<int32_t> &diagcol, const std::vector<int32_t> &caller,
+                   PlanDev *d, cudaStream_t s);
+int circuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,
+                 int32_t *gdiag, cudaStream_t s);
 
 }  // namespace mp

@@ -1,0 +1,122 @@
+// CPU check of the reuse circuit of the sparse transfer step (host logic
+// only, no GPU).  Builds A(D_n) and its circuit with the library's own host
+// code, then runs the power chain on the CPU with the circuit's semantics:
+// levels in order, each slice's rows the minimum over their lists (rows of
+// the labelled previous power, rows of the result computed at an earlier
+// level, or the INF row).  Every row must be computed exactly once and only
+// read after it is done.  The powers P_1..P_k go to stdout as raw int16 so
+// the test can compare them with the oracle; the circuit's statistics go to
+// stderr.
+//
+// usage: circuit_emulation n k width
+#include <cstdarg>
+#include <cstdio>
+
+#include "../paper_2409_17688_gb300/csrc/circuit.cu"
+
+namespace mp {
+int set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vfprintf(stderr, fmt, ap);
+    va_end(ap);
+    fputc('\n', stderr);
+    return code;
+}
+int device_info(DeviceInfo *o) {
+    o->device = 0;
+    o->sms = 1;
+    o->smem_optin = 0;
+    return MP_OK;
+}
+int device_status_ptr(int **p) {
+    *p = nullptr;
+    return MP_OK;
+}
+}  // namespace mp
+
+using namespace mp;
+
+static bool arc(const std::vector<WordMasks> &m, int64_t q, int64_t p, uint32_t full) {
+    // the arc rule in the library's bit-sliced form, restated for the host
+    const WordMasks a = m[q], b = m[p];
+    if (a.two & ~b.zero) return false;
+    const uint32_t left = ((uint32_t)b.zero << 1) & full, right = (uint32_t)b.zero >> 1, prev = a.zero;
+    const uint32_t any2 = (left & right) | (left & prev) | (right & prev);
+    const uint32_t one = (left ^ right ^ prev) & ~(left & right & prev);
+    return !(b.two & ~one) && !(b.one & ~any2);
+}
+
+int main(int argc, char **argv) {
+    if (argc < 4) return 2;
+    const int n = atoi(argv[1]), kmax = atoi(argv[2]), W = atoi(argv[3]);
+    std::vector<uint32_t> words;
+    enumerate_words(n, &words);
+    std::vector<WordMasks> masks;
+    word_masks(n, words, &masks);
+    const int64_t N = (int64_t)words.size();
+    const uint32_t full = (1u << n) - 1u;
+    HostCsr csr;
+    csr.N = N;
+    csr.row_ptr.push_back(0);
+    std::vector<uint16_t> z((size_t)N);
+    for (int64_t p = 0; p < N; ++p) z[p] = (uint16_t)__builtin_popcount(masks[p].zero);
+    for (int64_t q = 0; q < N; ++q) {
+        for (int64_t p = 0; p < N; ++p)
+            if (arc(masks, q, p, full)) {
+                csr.col.push_back((int32_t)p);
+                csr.val.push_back((int16_t)z[p]);
+            }
+        csr.row_ptr.push_back((int64_t)csr.col.size());
+    }
+    CircuitHost C;
+    if (circuit_build_host(csr, W, &C) != MP_OK) return 3;
+    fprintf(stderr, "levels %d slices %zu reads %lld cover %lld nnz %lld\n", C.levels, C.slices.size() / 2,
+            (long long)C.reads, (long long)C.cover_reads, (long long)csr.row_ptr[N]);
+    const int SR = 32 / (W / 8);
+    const uint32_t INF = 0x7FFF;
+    std::vector<int16_t> Pk((size_t)(N * N), (int16_t)INF);
+    for (int64_t q = 0; q < N; ++q)
+        for (int64_t e = csr.row_ptr[q]; e < csr.row_ptr[q + 1]; ++e) Pk[q * N + csr.col[e]] = csr.val[e];
+    fwrite(Pk.data(), 2, Pk.size(), stdout);
+    std::vector<uint32_t> X((size_t)(N * N)), R((size_t)(N * N));
+    for (int k = 2; k <= kmax; ++k) {
+        for (int64_t q = 0; q < N; ++q)  // the labelled buffer z_q + P_k[q]
+            for (int64_t c = 0; c < N; ++c) X[q * N + c] = (uint32_t)(uint16_t)Pk[q * N + c] + z[q];
+        std::vector<int> done((size_t)N, -1);
+        for (int l = 0; l < C.levels; ++l)
+            for (int s = C.level_slice0[l]; s < C.level_slice0[l + 1]; ++s) {
+                const uint32_t e0 = C.slices[2 * s], nb = C.slices[2 * s + 1];
+                if (nb < 1) return 8;
+                for (int i = 0; i < SR; ++i) {
+                    const uint32_t q = C.rows[(size_t)s * SR + i];
+                    if (q == 0xFFFFFFFFu) continue;
+                    if (q >= (uint32_t)N || done[q] >= 0) return 4;  // a row computed once
+                    for (int64_t c = 0; c < N; ++c) {
+                        uint32_t acc = INF;
+                        for (uint32_t jb = 0; jb < nb; ++jb)
+                            for (int t = 0; t < 8; ++t) {
+                                // block 0 at the slice's own place, later ones in ents
+                                const uint32_t idx =
+                                    jb == 0 ? C.first[((size_t)s * SR + i) * 8 + t]
+                                            : C.ents[((size_t)(e0 + (jb - 1) * SR + i)) * 8 + t];
+                                if (idx < (uint32_t)N) acc = std::min(acc, X[idx * N + c]);
+                                else if (idx < (uint32_t)(2 * N)) {
+                                    const int64_t qq = idx - N;
+                                    if (done[qq] < 0 || done[qq] >= l) return 5;  // read after its level
+                                    acc = std::min(acc, R[qq * N + c]);
+                                } else if (idx != (uint32_t)(2 * N)) return 6;
+                            }
+                        R[q * N + c] = acc;
+                    }
+                    done[q] = l;
+                }
+            }
+        for (int64_t q = 0; q < N; ++q) {
+            if (done[q] < 0) return 7;  // every row computed
+            for (int64_t c = 0; c < N; ++c) Pk[q * N + c] = (int16_t)R[q * N + c];
+        }
+        fwrite(Pk.data(), 2, Pk.size(), stdout);
+    }
+    return 0;
+}

@@ -211,6 +211,38 @@ def test_transfer_chain_sampled_rows(mp, torch, n):
     assert bool(torch.equal(P[kmax - 1].to(torch.int32), P[kmax - 1 - a].to(torch.int32) + b))
 
 
+_GATHER_PLAN_SCRIPT = r"""
+import sys
+import numpy as np
+import torch
+import paper_2409_17688_gb300 as mp
+out = sys.argv[1]
+P, g = mp.mp_transfer_power_sequence(6, 40)
+_, g9 = mp.mp_transfer_power_sequence(9, 60, keep_powers=False)
+torch.cuda.synchronize()
+np.savez(out, P=P.cpu().numpy(), g=g.cpu().numpy(), g9=g9.cpu().numpy())
+"""
+
+
+def test_gather_plan_steps_without_circuit(mp, torch, tmp_path):
+    """With MP_SPARSE_CIRCUIT=0 the transfer steps run on the gather plan
+    (the cluster kernel) instead of the reuse circuit; a full chain and a
+    mirror-column chain still give the oracle's powers and diagonals."""
+    import subprocess
+    import sys
+    out = str(tmp_path / "gather.npz")
+    env = dict(os.environ, MP_SPARSE_CIRCUIT="0")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _GATHER_PLAN_SCRIPT, out], env=env, cwd=root,
+                       capture_output=True, timeout=600)
+    assert r.returncode == 0, r.stderr.decode()[-2000:]
+    got = np.load(out)
+    Po, go = oracle.power_sequence(oracle.build_transfer(6), 40, threads=THREADS)
+    assert np.array_equal(got["P"], Po) and np.array_equal(got["g"], go)
+    _, g9 = oracle.power_sequence(oracle.build_transfer(9), 60, keep_powers=False, threads=THREADS)
+    assert np.array_equal(got["g9"], g9)
+
+
 def _large_order_rows(mp, torch, n, kmax, nsample):
     """Powers A^1..A^kmax of a large path order on the GPU, checked on
     sampled rows (first, last and drawn ones) against the oracle's rows,
