@@ -67,6 +67,17 @@ extern "C" {
  */
 int64_t mp_transfer_size(int n);
 
+/* The reuse circuit of A(D_n)'s sparse step on the current device (built
+ * with the transfer plan on first use; no step runs).  A row of a product
+ * A (x) X is the minimum, over its arcs q -> p, of z_p + X[p]; when the arcs
+ * out of q' are a subset of those out of q, row q' of the result is part of
+ * row q's minimum, so the step computes each row from a few result rows
+ * (its cover) and the arcs they leave out, in levels.  Writes into the HOST
+ * array info[0..cap): {columns per CTA chunk (0: the step runs without a
+ * circuit), levels, row reads per column, of them result rows, nnz(A), N}.
+ * Returns the number of fields written (at most 6), or a negative status. */
+int mp_transfer_circuit_info(int n, int64_t *info, int cap);
+
 /* Writes the correct n-words into the HOST array words[0..cap) in
  * lexicographic order (letter 1 most significant, 0 < 1 < 2), each packed
  * two bits per letter with letter 1 in bits 2(n-1)..2n-1, so the packed

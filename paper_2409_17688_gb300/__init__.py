@@ -54,6 +54,7 @@ def lib() -> ctypes.CDLL:
     P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
     sig = {
         "mp_transfer_size": (I64, [I]),
+        "mp_transfer_circuit_info": (I, [I, P, I]),
         "mp_transfer_words": (I64, [I, P, I64]),
         "mp_build_transfer_matrix": (I, [I, P, I64, P, P]),
         "mp_minplus_mul": (I, [P, P, P, I64, I64, I64, I64, I64, I64, I, P]),
@@ -116,6 +117,15 @@ def _dev(t):
 
 
 # ------------------------------------------------------------------ words / A
+
+def mp_transfer_circuit_info(n: int) -> dict:
+    """The reuse circuit of A(D_n)'s sparse step on the current device."""
+    import numpy as np
+    info = np.zeros(6, dtype=np.int64)
+    k = _check(lib().mp_transfer_circuit_info(int(n), ctypes.c_void_p(info.ctypes.data), 6))
+    keys = ("width", "levels", "reads", "cover_reads", "nnz", "N")
+    return {key: int(info[i]) for i, key in enumerate(keys[:k])}
+
 
 def mp_transfer_size(n: int) -> int:
     """N = |C_n|, the number of correct n-words."""

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -306,6 +307,9 @@ static int narrow_plan(TransferEntry *te, cudaStream_t s, const PlanDev **out) {
 // The chain over a prepared sparse plan; B0 already holds P_1.
 static int run_sparse_chain(const PlanDev &plan, uint16_t *B0, uint16_t *B1, int k_max,
                             int16_t *powers, size_t slot, int32_t *gdiag, cudaStream_t s) {
+    // with a circuit the whole chain is one launch, each CTA keeping its
+    // column chunk on chip from step to step
+    if (plan.circuit.ready) return circuit_chain(plan, B0, k_max, powers, slot, gdiag, s);
     uint16_t *buf[2] = {B0, B1};
     for (int k = 2; k <= k_max; ++k) {
         MP_TRY(sparse_step(plan, buf[(k - 2) & 1], buf[(k - 1) & 1],
@@ -505,12 +509,17 @@ int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
     const int rc = transfer_chain_direct(te, k_max, powers_opt, slot, gdiag_opt, cap);
     const cudaError_t ec = cudaStreamEndCapture(cap, &graph);
     cudaStreamDestroy(cap);
-    if (rc != MP_OK) {
+    if (rc != MP_OK || ec != cudaSuccess) {
+        // A capture can be invalidated from outside it (another host thread
+        // synchronising the whole device while it runs), and nothing of a
+        // failed capture has run: the chain runs directly instead and is not
+        // captured again.  A genuine error repeats there and is returned.
         if (graph) cudaGraphDestroy(graph);
-        return rc;
-    }
-    if (ec != cudaSuccess) {
         cudaGetLastError();
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            g_chain_graphs[key].calls = std::numeric_limits<int>::min() / 2;
+        }
         return transfer_chain_direct(te, k_max, powers_opt, slot, gdiag_opt, s);
     }
     const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
@@ -630,6 +639,19 @@ int64_t mp_transfer_words(int n, uint32_t *words, int64_t cap) {
     if (words && cap > 0)
         memcpy(words, w.data(), sizeof(uint32_t) * (size_t)std::min<int64_t>(cap, (int64_t)w.size()));
     return (int64_t)w.size();
+}
+
+int mp_transfer_circuit_info(int n, int64_t *info, int cap) {
+    MP_TRY(check_n(n));
+    if (!info || cap < 0) return set_error(MP_EINVAL, "info buffer missing");
+    TransferEntry *te;
+    MP_TRY(transfer_entry(n, nullptr, &te));
+    MP_CUDA_TRY(cudaStreamSynchronize(nullptr));
+    const CircuitHost &c = te->circuit;
+    const int64_t v[6] = {c.W, c.levels, c.reads, c.cover_reads, te->plan.nnz, te->N};
+    const int k = std::min(cap, 6);
+    for (int i = 0; i < k; ++i) info[i] = v[i];
+    return k;
 }
 
 int mp_build_transfer_matrix(int n, int16_t *A, int64_t lda, uint32_t *words_opt, void *stream) {

@@ -32,6 +32,7 @@
 // min-reduced and folded into g[k].
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "mp_internal.cuh"
 #include "spmm.cuh"
@@ -105,14 +106,16 @@ __device__ __forceinline__ void csts_v4(uint32_t addr, uint4 v) {
 }
 
 struct CircArgs {
-    const uint16_t *Bin;
-    uint16_t *Bout;
-    int64_t N, ldb;
+    const uint16_t *Bin;  // X: the labelled buffer of P_k (P_1 for a chain)
+    uint16_t *Bout;       // one step: the labelled buffer of P_{k+1}
+    int64_t N, Nh, ldb;
     const uint8_t *meta;
-    uint32_t meta_bytes, off_slices, off_rowinfo, off_first, off_ents;
+    uint32_t meta_bytes, off_slices, off_rowinfo, off_first, off_ents, off_z;
     int levels;
-    int16_t *user_out;
-    int32_t *gdiag;
+    int k_max;            // a chain: P_2 .. P_{k_max}
+    int16_t *user_out;    // the caller's power(s), or null
+    size_t slot;          // a chain: entries between the caller's powers
+    int32_t *gdiag;       // one step: g[k]; a chain: g[0 .. k_max - 1]
     int *status;
 };
 
@@ -121,15 +124,20 @@ __device__ __forceinline__ uint32_t pick_word(const uint4 &v, int k) {
 }
 
 // acc = min(acc, the image rows an entry block names), 16 bytes per lane;
-// entries naming the INF row (the padding of short lists) load nothing.
+// entries naming the INF row (the padding of short lists, index 2Nh) load
+// nothing, the others live at image row (index + sh) mod 2Nh.
 template <int RB>
-__device__ __forceinline__ void fold8(uint4 &acc, const uint4 &e, uint32_t rbase, uint32_t pad) {
-    uint32_t ix[8] = {e.x & 0xFFFFu, e.x >> 16, e.y & 0xFFFFu, e.y >> 16,
-                      e.z & 0xFFFFu, e.z >> 16, e.w & 0xFFFFu, e.w >> 16};
+__device__ __forceinline__ void fold8(uint4 &acc, const uint4 &e, uint32_t rbase, uint32_t N2,
+                                      uint32_t sh) {
+    const uint32_t ix[8] = {e.x & 0xFFFFu, e.x >> 16, e.y & 0xFFFFu, e.y >> 16,
+                            e.z & 0xFFFFu, e.z >> 16, e.w & 0xFFFFu, e.w >> 16};
     uint4 v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-        v[k] = ix[k] != pad ? clds_v4(rbase + ix[k] * RB) : make_uint4(~0u, ~0u, ~0u, ~0u);
+    for (int k = 0; k < 8; ++k) {
+        uint32_t j = ix[k] + sh;
+        if (j >= N2) j -= N2;
+        v[k] = ix[k] != N2 ? clds_v4(rbase + j * RB) : make_uint4(~0u, ~0u, ~0u, ~0u);
+    }
     acc.x = __vimin3_u16x2(__vimin3_u16x2(acc.x, v[0].x, v[1].x), __vimin3_u16x2(v[2].x, v[3].x, v[4].x),
                            __vimin3_u16x2(v[5].x, v[6].x, v[7].x));
     acc.y = __vimin3_u16x2(__vimin3_u16x2(acc.y, v[0].y, v[1].y), __vimin3_u16x2(v[2].y, v[3].y, v[4].y),
@@ -149,7 +157,14 @@ constexpr uint32_t kCircBarBytes = 16;
 constexpr uint32_t kMetaCopy = 32768;  // bytes per bulk copy of the circuit
 
 // W columns per CTA; a row is 2W bytes, read by W / 8 lanes (16 bytes each).
-template <int W>
+// One step (kChain false): X from Bin, the result (labelled) to Bout.  A
+// chain (kChain true): the CTA runs every step of the chain on its chunk
+// without leaving the SM -- column chunk c of P_{k+1} depends only on chunk c
+// of P_k -- so after a step the result region, with the labels added in
+// place, is the next step's X, and the two regions swap: with sh = 0 or N,
+// image index j (X rows 0..N-1, result rows Nh..Nh+N-1, Nh = N rounded up to
+// 8) lives at (j + sh) mod 2Nh, sh = 0 or Nh.
+template <int W, bool kChain>
 __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs a) {
     constexpr int LPR = W / 8;       // lanes per row
     constexpr int SR = 32 / LPR;     // rows per slice
@@ -158,8 +173,10 @@ __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs 
     const uint32_t sbase = csmem_u32(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t N = a.N;
+    const uint32_t Nh = (uint32_t)a.Nh, N2 = 2 * Nh;
     const int64_t c0 = (int64_t)blockIdx.x * W;
-    const uint32_t mb = sbase + (uint32_t)circuit_image_bytes(N, W);
+    const uint32_t mb = sbase + (uint32_t)circuit_image_bytes(Nh, W);
+    __shared__ int32_t s_dmin;
 
     // The circuit: plan data only, so its bulk copies start before the
     // previous step has finished.  The barrier's initialisation is made
@@ -167,14 +184,15 @@ __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs 
     // them waits on it.
     const uint32_t bar = mb + a.meta_bytes;
     if (threadIdx.x == 0) {
+        s_dmin = (int32_t)kInf16;
         cmbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         cmbar_arrive_expect_tx(bar, a.meta_bytes);
         for (uint32_t o = 0; o < a.meta_bytes; o += kMetaCopy)
             cbulk_copy(mb + o, a.meta + o, min(kMetaCopy, a.meta_bytes - o), bar);
     }
-    // row 2N of the image: above every value, the padding of short lists
-    if (threadIdx.x < RB / 4) reinterpret_cast<uint32_t *>(smem + 2 * N * RB)[threadIdx.x] = 0xFFFFFFFFu;
+    // row 2Nh of the image: above every value, the padding of short lists
+    if (threadIdx.x < RB / 4) reinterpret_cast<uint32_t *>(smem + (size_t)N2 * RB)[threadIdx.x] = 0xFFFFFFFFu;
     // Programmatic dependent launch: the previous step's output (our X) is
     // read only after its grid has completed.
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -197,51 +215,82 @@ __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs 
     }
 
     const int i = lane / LPR, h = lane % LPR;
-    const uint32_t rbase = sbase + (uint32_t)h * 16;
+    const uint32_t hb = (uint32_t)h * 16;
     const int64_t col0 = c0 + (int64_t)h * 8;
     const uint32_t m_sl = mb + a.off_slices, m_ri = mb + a.off_rowinfo;
     const uint32_t m_fi = mb + a.off_first, m_en = mb + a.off_ents;
-    const uint32_t pad = (uint32_t)(2 * N);
-    int32_t dmin = (int32_t)kInf16;
-    for (int l = 0; l < a.levels; ++l) {
-        const int s1 = (int)clds_u32(mb + 4u * (uint32_t)(l + 1));
-        for (int s = (int)clds_u32(mb + 4u * (uint32_t)l) + warp; s < s1; s += kCircWarps) {
-            const uint32_t slot = (uint32_t)s * SR + (uint32_t)i;
-            const uint2 d = clds_v2(m_sl + 8u * (uint32_t)s);
-            const uint2 ri = clds_v2(m_ri + 8u * slot);
-            uint4 acc = make_uint4(kInf16x2, kInf16x2, kInf16x2, kInf16x2);
-            fold8<RB>(acc, clds_v4(m_fi + 16u * slot), rbase, pad);
-            // the few rows longer than one block: their later blocks
-            for (uint32_t jb = 1; jb < d.y; ++jb)
-                fold8<RB>(acc, clds_v4(m_en + 16u * (d.x + (jb - 1) * SR + (uint32_t)i)), rbase, pad);
-            const uint32_t q = ri.x & 0xFFFFu;
-            if (q == 0xFFFFu) continue;
-            // the result row for the later levels, then the next buffer
-            csts_v4(sbase + (uint32_t)((N + (int64_t)q) * RB) + (uint32_t)h * 16, acc);
-            const uint32_t zq = (ri.x >> 16) * 0x10001u;
-            *reinterpret_cast<uint4 *>(a.Bout + (int64_t)q * a.ldb + col0) =
-                make_uint4(acc.x + zq, acc.y + zq, acc.z + zq, acc.w + zq);
-            const uint32_t dc = ri.y & 0xFFFFu;
-            if (a.gdiag && dc != 0xFFFFu && (int64_t)dc >= col0 && (int64_t)dc < col0 + 8) {
-                const int k = (int)((int64_t)dc - col0);
-                const uint32_t wv = pick_word(acc, k >> 1);
-                dmin = min(dmin, (int32_t)((k & 1) ? wv >> 16 : wv & 0xFFFFu));
-            }
-            if (a.user_out) {
-                int16_t *orow = a.user_out + (int64_t)(ri.y >> 16) * N;
+    const int k_last = kChain ? a.k_max : 2;
+    uint32_t sh = 0;
+    for (int k = 2; k <= k_last; ++k) {
+        int32_t dmin = (int32_t)kInf16;
+        for (int l = 0; l < a.levels; ++l) {
+            const int s1 = (int)clds_u32(mb + 4u * (uint32_t)(l + 1));
+            for (int s = (int)clds_u32(mb + 4u * (uint32_t)l) + warp; s < s1; s += kCircWarps) {
+                const uint32_t slot = (uint32_t)s * SR + (uint32_t)i;
+                const uint2 d = clds_v2(m_sl + 8u * (uint32_t)s);
+                const uint2 ri = clds_v2(m_ri + 8u * slot);
+                uint4 acc = make_uint4(kInf16x2, kInf16x2, kInf16x2, kInf16x2);
+                fold8<RB>(acc, clds_v4(m_fi + 16u * slot), sbase + hb, N2, sh);
+                // the few rows longer than one block: their later blocks
+                for (uint32_t jb = 1; jb < d.y; ++jb)
+                    fold8<RB>(acc, clds_v4(m_en + 16u * (d.x + (jb - 1) * SR + (uint32_t)i)), sbase + hb,
+                              N2, sh);
+                const uint32_t q = ri.x & 0xFFFFu;
+                if (q == 0xFFFFu) continue;
+                // the result row, for the later levels (and the next step)
+                uint32_t rr = Nh + q + sh;
+                if (rr >= N2) rr -= N2;
+                csts_v4(sbase + rr * RB + hb, acc);
+                if (!kChain) {
+                    const uint32_t zq = (ri.x >> 16) * 0x10001u;
+                    *reinterpret_cast<uint4 *>(a.Bout + (int64_t)q * a.ldb + col0) =
+                        make_uint4(acc.x + zq, acc.y + zq, acc.z + zq, acc.w + zq);
+                }
+                const uint32_t dc = ri.y & 0xFFFFu;
+                if (a.gdiag && dc != 0xFFFFu && (int64_t)dc >= col0 && (int64_t)dc < col0 + 8) {
+                    const int kk = (int)((int64_t)dc - col0);
+                    const uint32_t wv = pick_word(acc, kk >> 1);
+                    dmin = min(dmin, (int32_t)((kk & 1) ? wv >> 16 : wv & 0xFFFFu));
+                }
+                if (a.user_out) {
+                    int16_t *orow = a.user_out + (kChain ? (size_t)(k - 1) * a.slot : 0) +
+                                    (int64_t)(ri.y >> 16) * N;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t wv = pick_word(acc, k >> 1);
-                    if (col0 + k < N) orow[col0 + k] = (int16_t)((k & 1) ? wv >> 16 : wv & 0xFFFFu);
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const uint32_t wv = pick_word(acc, kk >> 1);
+                        if (col0 + kk < N) orow[col0 + kk] = (int16_t)((kk & 1) ? wv >> 16 : wv & 0xFFFFu);
+                    }
                 }
             }
+            __syncthreads();  // this level's rows are read by the later levels
         }
-        __syncthreads();  // this level's rows are read by the later levels
-    }
-    if (a.gdiag) {
+        if (a.gdiag) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dmin = min(dmin, __shfl_xor_sync(0xFFFFFFFFu, dmin, o));
-        if (lane == 0 && dmin < (int32_t)kInf16) atomicMin(a.gdiag, dmin);
+            for (int o = 16; o > 0; o >>= 1) dmin = min(dmin, __shfl_xor_sync(0xFFFFFFFFu, dmin, o));
+            if (lane == 0 && dmin < (int32_t)kInf16) atomicMin(&s_dmin, dmin);
+        }
+        if (kChain) {
+            // the labels, in place: the result becomes the next step's X
+            const uint32_t m_z = mb + a.off_z;
+            for (int64_t pc = threadIdx.x; pc < N * LPR; pc += kCircThreads) {
+                const uint32_t q = (uint32_t)(pc / LPR);
+                const uint32_t part = (uint32_t)(pc - (int64_t)q * LPR);
+                uint32_t rr = Nh + q + sh;
+                if (rr >= N2) rr -= N2;
+                const uint32_t addr = sbase + rr * RB + part * 16;
+                const uint32_t zw = clds_u32(m_z + 4u * (q >> 1));
+                const uint32_t zq = ((q & 1) ? zw >> 16 : zw & 0xFFFFu) * 0x10001u;
+                const uint4 v = clds_v4(addr);
+                csts_v4(addr, make_uint4(v.x + zq, v.y + zq, v.z + zq, v.w + zq));
+            }
+            sh = Nh - sh;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && a.gdiag) {
+            const int32_t v = s_dmin;
+            if (v < (int32_t)kInf16) atomicMin(kChain ? a.gdiag + (k - 1) : a.gdiag, v);
+            s_dmin = (int32_t)kInf16;  // the next step's minima arrive after its levels
+        }
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
@@ -328,13 +377,17 @@ int circuit_slice_host(const CircuitCover &cv, int W, CircuitHost *out) {
     CircuitHost &C = *out;
     C = CircuitHost();
     C.N = N;
+    C.Nh = (N + 7) & ~(int64_t)7;
     C.W = W;
     C.levels = cv.levels;
     C.reads = cv.reads;
     C.cover_reads = cv.cover_reads;
     // per level: rows longest list first, cut into slices of one warp's rows
     const int SR = 32 / (W / 8);
-    const uint16_t pad = (uint16_t)(2 * N);
+    if (2 * C.Nh + 1 > 0xFFFF) return set_error(MP_EINVAL, "N = %lld too large for a circuit", (long long)N);
+    const uint16_t pad = (uint16_t)(2 * C.Nh);
+    // a list entry in image rows: X rows stay, result row N + q' moves to Nh + q'
+    auto img = [&](uint32_t v) { return v < (uint32_t)N ? v : v - (uint32_t)N + (uint32_t)C.Nh; };
     C.level_slice0.push_back(0);
     for (int l = 0; l < C.levels; ++l) {
         std::vector<int64_t> lr;
@@ -352,19 +405,25 @@ int circuit_slice_host(const CircuitCover &cv, int W, CircuitHost *out) {
             for (int i = 0; i < SR; ++i)
                 C.rows.push_back(r0 + (size_t)i < r1 ? (uint32_t)lr[r0 + (size_t)i] : 0xFFFFFFFFu);
             // Each list in an order of its own (min is order-free), chosen so
-            // that at every entry position the warp's loads spread over the
-            // shared-memory banks: an image row of 2W bytes sits in bank group
-            // (row mod groups), and a position's load takes as many passes as
-            // its fullest group.  Greedy: position by position, each row
-            // takes its remaining entry whose group is least used so far.
+            // that at every entry position the loads spread over the
+            // shared-memory banks.  An image row of 2W bytes sits in bank
+            // group (row mod groups), groups = 128 / 2W; a 16-byte load is
+            // served a quarter warp (8 lanes, so `groups` rows) at a time, and
+            // a quarter takes as many passes as its fullest group.  Greedy:
+            // position by position, each row of a quarter takes its remaining
+            // entry whose group that quarter uses least so far.  The result
+            // rows start at a multiple of 8, so the regions' swap in a chain
+            // keeps every row's group.
             const int groups = 128 / (2 * W);
             std::vector<std::vector<uint32_t>> rem((size_t)SR);
             for (int i = 0; i < SR; ++i)
-                if (r0 + (size_t)i < r1) rem[(size_t)i] = cv.lists[(size_t)lr[r0 + (size_t)i]];
+                if (r0 + (size_t)i < r1)
+                    for (uint32_t v : cv.lists[(size_t)lr[r0 + (size_t)i]]) rem[(size_t)i].push_back(img(v));
             std::vector<uint16_t> blk((size_t)nb * SR * 8, pad);
             for (uint32_t j = 0; j < nb * 8; ++j) {
                 std::vector<int> used((size_t)groups, 0);
                 for (int i = 0; i < SR; ++i) {
+                    if (i % groups == 0) std::fill(used.begin(), used.end(), 0);
                     auto &li = rem[(size_t)i];
                     if (li.empty()) continue;
                     size_t best = 0;
@@ -389,24 +448,27 @@ int circuit_build_host(const HostCsr &csr, int W, CircuitHost *out) {
     return circuit_slice_host(cv, W, out);
 }
 
-// Section sizes of the circuit blob (bytes, each a multiple of 16).
-static void circuit_layout(const CircuitHost &h, uint32_t *off_sl, uint32_t *off_ri, uint32_t *off_fi,
-                           uint32_t *off_en, uint32_t *total) {
+// Section offsets of the circuit blob (bytes, each section a multiple of 16).
+struct CircLayout {
+    uint32_t sl = 0, ri = 0, fi = 0, en = 0, z = 0, total = 0;
+};
+static CircLayout circuit_layout(const CircuitHost &h) {
     auto r16 = [](size_t b) { return (uint32_t)((b + 15) & ~(size_t)15); };
-    *off_sl = r16(h.level_slice0.size() * 4);
-    *off_ri = *off_sl + r16(h.slices.size() * 4);       // two words per slice
-    *off_fi = *off_ri + r16(h.rows.size() * 8);         // two words per slot
-    *off_en = *off_fi + r16(h.first.size() * 2);
-    *total = *off_en + r16(h.ents.size() * 2);
+    CircLayout L;
+    L.sl = r16(h.level_slice0.size() * 4);
+    L.ri = L.sl + r16(h.slices.size() * 4);     // two words per slice
+    L.fi = L.ri + r16(h.rows.size() * 8);       // two words per slot
+    L.en = L.fi + r16(h.first.size() * 2);
+    L.z = L.en + r16(h.ents.size() * 2);
+    L.total = L.z + r16((size_t)h.N * 2);       // the rows' labels
+    return L;
 }
 
 int circuit_smem_bytes(const CircuitHost &h, size_t *bytes) {
-    uint32_t a, b, c, d, total;
-    circuit_layout(h, &a, &b, &c, &d, &total);
-    *bytes = circuit_image_bytes(h.N, h.W) + total + kCircBarBytes;
+    *bytes = circuit_image_bytes(h.Nh, h.W) + circuit_layout(h).total + kCircBarBytes;
     DeviceInfo di;
     MP_TRY(device_info(&di));
-    if (*bytes > di.smem_optin) *bytes = 0;
+    if (*bytes + 1024 > di.smem_optin) *bytes = 0;  // a margin for the kernel's static shared memory
     return MP_OK;
 }
 
@@ -419,11 +481,10 @@ int circuit_upload(const CircuitHost &h, const std::vector<uint16_t> &z,
         h.N != d->N)
         return set_error(MP_EINVAL, "circuit of the wrong size");
     if (d->ldb % h.W) return set_error(MP_EINVAL, "circuit width does not divide the buffer");
-    uint32_t off_sl, off_ri, off_fi, off_en, total;
-    circuit_layout(h, &off_sl, &off_ri, &off_fi, &off_en, &total);
-    std::vector<uint8_t> blob(total, 0);
+    const CircLayout L = circuit_layout(h);
+    std::vector<uint8_t> blob(L.total, 0);
     memcpy(blob.data(), h.level_slice0.data(), h.level_slice0.size() * 4);
-    memcpy(blob.data() + off_sl, h.slices.data(), h.slices.size() * 4);
+    memcpy(blob.data() + L.sl, h.slices.data(), h.slices.size() * 4);
     std::vector<uint32_t> ri(h.rows.size() * 2);
     for (size_t k = 0; k < h.rows.size(); ++k) {
         const uint32_t q = h.rows[k];
@@ -433,31 +494,35 @@ int circuit_upload(const CircuitHost &h, const std::vector<uint16_t> &z,
             continue;
         }
         const int32_t dc = diagcol[q];
-        if (z[q] > 0xFFFFu || dc >= 0xFFFF || caller[q] < 0 || caller[q] > 0xFFFF)
+        if (z[q] > 0x7FFFu || dc >= 0xFFFF || caller[q] < 0 || caller[q] > 0xFFFF)
             return set_error(MP_EINVAL, "circuit row fields out of range");
         ri[2 * k] = q | ((uint32_t)z[q] << 16);
         ri[2 * k + 1] = (dc < 0 ? 0xFFFFu : (uint32_t)dc) | ((uint32_t)caller[q] << 16);
     }
-    memcpy(blob.data() + off_ri, ri.data(), ri.size() * 4);
-    memcpy(blob.data() + off_fi, h.first.data(), h.first.size() * 2);
-    memcpy(blob.data() + off_en, h.ents.data(), h.ents.size() * 2);
-    MP_TRY(c.meta.alloc(total ? total : 16, s, true));
-    MP_CUDA_TRY(cudaMemcpyAsync(c.meta.p, blob.data(), total, cudaMemcpyHostToDevice, s));
+    memcpy(blob.data() + L.ri, ri.data(), ri.size() * 4);
+    memcpy(blob.data() + L.fi, h.first.data(), h.first.size() * 2);
+    memcpy(blob.data() + L.en, h.ents.data(), h.ents.size() * 2);
+    memcpy(blob.data() + L.z, z.data(), z.size() * 2);
+    MP_TRY(c.meta.alloc(L.total ? L.total : 16, s, true));
+    MP_CUDA_TRY(cudaMemcpyAsync(c.meta.p, blob.data(), L.total, cudaMemcpyHostToDevice, s));
     MP_CUDA_TRY(cudaStreamSynchronize(s));  // the host blob goes out of scope
     c.W = h.W;
+    c.Nh = h.Nh;
     c.levels = h.levels;
     c.nslices = (int64_t)h.slices.size() / 2;
-    c.meta_bytes = total;
-    c.off_slices = off_sl;
-    c.off_rowinfo = off_ri;
-    c.off_first = off_fi;
-    c.off_ents = off_en;
+    c.meta_bytes = L.total;
+    c.off_slices = L.sl;
+    c.off_rowinfo = L.ri;
+    c.off_first = L.fi;
+    c.off_ents = L.en;
+    c.off_z = L.z;
     c.ready = true;
     return MP_OK;
 }
 
-int circuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,
-                 int32_t *gdiag, cudaStream_t s) {
+// One launch: a step (Bin -> Bout) or a whole chain from Bin = P_1.
+static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uint16_t *Bout, int k_max,
+                          int16_t *user_out, size_t slot, int32_t *gdiag, cudaStream_t s) {
     const CircuitDev &c = p.circuit;
     if (!c.ready) return set_error(MP_EINVAL, "plan has no circuit");
     if (p.narrow && user_out) return set_error(MP_EINVAL, "a narrow chain has no full powers to write");
@@ -468,6 +533,7 @@ int circuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t 
     a.Bin = Bin;
     a.Bout = Bout;
     a.N = p.N;
+    a.Nh = c.Nh;
     a.ldb = p.ldb;
     a.meta = c.meta.as<uint8_t>();
     a.meta_bytes = c.meta_bytes;
@@ -475,24 +541,29 @@ int circuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t 
     a.off_rowinfo = c.off_rowinfo;
     a.off_first = c.off_first;
     a.off_ents = c.off_ents;
+    a.off_z = c.off_z;
     a.levels = c.levels;
+    a.k_max = k_max;
     a.user_out = user_out;
+    a.slot = slot;
     a.gdiag = gdiag;
     MP_TRY(device_status_ptr(&a.status));
-    const size_t smem = circuit_image_bytes(p.N, c.W) + c.meta_bytes + kCircBarBytes;
+    const size_t smem = circuit_image_bytes(c.Nh, c.W) + c.meta_bytes + kCircBarBytes;
     if (smem > di.smem_optin) return set_error(MP_EINVAL, "circuit does not fit shared memory");
     const unsigned grid = (unsigned)(p.ldb / c.W);
     if (grid == 0) return MP_OK;
-    static bool attr_set[2][64] = {};
-    const int kind = c.W == 16 ? 0 : 1;
-    if (di.device < 64 && !attr_set[kind][di.device]) {
-        if (c.W == 16)
-            MP_CUDA_TRY(cudaFuncSetAttribute(circuit_step_kernel<16>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)di.smem_optin));
-        else
-            MP_CUDA_TRY(cudaFuncSetAttribute(circuit_step_kernel<8>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)di.smem_optin));
-        attr_set[kind][di.device] = true;
+    auto *kern = c.W == 16 ? (chain ? circuit_step_kernel<16, true> : circuit_step_kernel<16, false>)
+                           : (chain ? circuit_step_kernel<8, true> : circuit_step_kernel<8, false>);
+    // the dynamic size each kernel may take, raised as larger plans come
+    static std::mutex attr_mu;
+    static size_t attr_set[4][64] = {};
+    const int kind = (c.W == 16 ? 0 : 2) + (chain ? 1 : 0);
+    {
+        std::lock_guard<std::mutex> lk(attr_mu);
+        if (di.device >= 64 || attr_set[kind][di.device] < smem) {
+            MP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            if (di.device < 64) attr_set[kind][di.device] = smem;
+        }
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -504,10 +575,21 @@ int circuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (c.W == 16) MP_CUDA_TRY(cudaLaunchKernelEx(&cfg, circuit_step_kernel<16>, a));
-    else MP_CUDA_TRY(cudaLaunchKernelEx(&cfg, circuit_step_kernel<8>, a));
+    MP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
+}
+
+int circuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,
+                 int32_t *gdiag, cudaStream_t s) {
+    return circuit_launch(p, false, Bin, Bout, 2, user_out, 0, gdiag, s);
+}
+
+int circuit_chain(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *powers, size_t slot,
+                  int32_t *gdiag, cudaStream_t s) {
+    if (k_max < 2) return MP_OK;
+    if (powers && slot < (size_t)p.N * (size_t)p.N) return set_error(MP_EINVAL, "power slots too small");
+    return circuit_launch(p, true, B1, nullptr, k_max, powers, slot, gdiag, s);
 }
 
 }  // namespace mp

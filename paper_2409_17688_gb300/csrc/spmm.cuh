@@ -91,6 +91,7 @@ struct CircuitCover {
 };
 struct CircuitHost {
     int64_t N = 0;
+    int64_t Nh = 0;  // N rounded up to 8: the result rows start at image row Nh
     int W = 0, levels = 0;
     std::vector<int32_t> level_slice0;  // [levels + 1] first slice of each level
     // per slice {first vector of its later entry blocks in ents, entry blocks
@@ -98,7 +99,7 @@ struct CircuitHost {
     std::vector<uint32_t> slices;
     std::vector<uint32_t> rows;         // per slice, its rows (0xFFFFFFFF: none)
     // Entry blocks: per row, 8 row indices of the shared-memory image (X rows
-    // 0..N-1, result rows N..2N-1, 2N the INF row).  first holds every
+    // 0..N-1, result rows Nh..Nh+N-1, 2Nh the INF row).  first holds every
     // slice's first block (row i of slice s at s * rows-per-slice + i), ents
     // the later blocks, block by block and row by row.
     std::vector<uint16_t> first, ents;
@@ -106,12 +107,14 @@ struct CircuitHost {
 };
 struct CircuitDev {
     int W = 0, levels = 0;
+    int64_t Nh = 0;
     int64_t nslices = 0;
     // the circuit as one blob, copied whole into shared memory: level
     // starts, slice descriptors, per slot {row | label << 16, diagonal
-    // column | caller row << 16}, first entry blocks, later entry blocks
+    // column | caller row << 16}, first entry blocks, later entry blocks,
+    // the rows' labels
     DevBuf meta;
-    uint32_t meta_bytes = 0, off_slices = 0, off_rowinfo = 0, off_first = 0, off_ents = 0;
+    uint32_t meta_bytes = 0, off_slices = 0, off_rowinfo = 0, off_first = 0, off_ents = 0, off_z = 0;
     bool ready = false;
 };
 
@@ -175,5 +178,11 @@ int circuit_upload(const CircuitHost &h, const std::vector<uint16_t> &z,
                    PlanDev *d, cudaStream_t s);
 int circuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,
                  int32_t *gdiag, cudaStream_t s);
+// The whole chain P_2 .. P_{k_max} from B1 (the labelled buffer of P_1) in
+// one launch: each CTA keeps its column chunk in shared memory from step to
+// step.  powers (optional): P_k at powers + (k - 1) * slot in the caller's
+// layout; gdiag (optional): g[k - 1] = min diag P_k, folded by atomicMin.
+int circuit_chain(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *powers, size_t slot,
+                  int32_t *gdiag, cudaStream_t s);
 
 }  // namespace mp

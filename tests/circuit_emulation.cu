@@ -100,12 +100,13 @@ int main(int argc, char **argv) {
                                 const uint32_t idx =
                                     jb == 0 ? C.first[((size_t)s * SR + i) * 8 + t]
                                             : C.ents[((size_t)(e0 + (jb - 1) * SR + i)) * 8 + t];
+                                // X rows 0..N-1, result rows Nh..Nh+N-1, INF row 2Nh
                                 if (idx < (uint32_t)N) acc = std::min(acc, X[idx * N + c]);
-                                else if (idx < (uint32_t)(2 * N)) {
-                                    const int64_t qq = idx - N;
+                                else if (idx >= (uint32_t)C.Nh && idx < (uint32_t)(C.Nh + N)) {
+                                    const int64_t qq = idx - C.Nh;
                                     if (done[qq] < 0 || done[qq] >= l) return 5;  // read after its level
                                     acc = std::min(acc, R[qq * N + c]);
-                                } else if (idx != (uint32_t)(2 * N)) return 6;
+                                } else if (idx != (uint32_t)(2 * C.Nh)) return 6;
                             }
                         R[q * N + c] = acc;
                     }

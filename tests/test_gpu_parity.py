@@ -243,6 +243,19 @@ def test_gather_plan_steps_without_circuit(mp, torch, tmp_path):
     assert np.array_equal(got["g9"], g9)
 
 
+def test_circuit_info(mp):
+    """Path orders whose column chunk fits shared memory run on the reuse
+    circuit, which reads far fewer rows than the arcs; n = 10 does not fit."""
+    for n in (3, 6, 9):
+        c = mp.mp_transfer_circuit_info(n)
+        A = oracle.build_transfer(n)
+        assert c["N"] == A.shape[0] and c["nnz"] == int((A < INF).sum())
+        assert c["width"] in (8, 16) and c["levels"] >= 1
+        assert 0 < c["cover_reads"] < c["reads"] <= c["nnz"]
+    assert mp.mp_transfer_circuit_info(9)["reads"] * 10 < mp.mp_transfer_circuit_info(9)["nnz"]
+    assert mp.mp_transfer_circuit_info(10)["width"] == 0
+
+
 def _large_order_rows(mp, torch, n, kmax, nsample):
     """Powers A^1..A^kmax of a large path order on the GPU, checked on
     sampled rows (first, last and drawn ones) against the oracle's rows,
@@ -756,7 +769,10 @@ def test_threads_share_the_plan_caches(mp, torch):
             n = 4 + i % 4
             results[i] = mp.mp_gamma2_table(n, 60)
             P, g = mp.mp_transfer_power_sequence(n, 20)
-            torch.cuda.synchronize()
+            # this thread's stream only: a device-wide synchronisation would
+            # also reach another thread's chain while it is being captured
+            # into a graph (the library then runs that chain directly)
+            torch.cuda.current_stream().synchronize()
             results[(i, "g")] = (n, host(g))
         except Exception as e:  # reported below
             errors.append(repr(e))
