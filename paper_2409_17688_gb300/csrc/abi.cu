@@ -230,7 +230,12 @@ static int transfer_entry(int n, cudaStream_t s, TransferEntry **out) {
     ph.canon = canon;
     MP_TRY(plan_upload(ph, &e->plan, s, true));
     MP_CUDA_TRY(cudaStreamSynchronize(s));
-    if (circuit_enabled() && 2 * N + 1 <= 0xFFFF) {
+    DeviceInfo di;
+    MP_TRY(device_info(&di));
+    const int64_t nh = (N + 7) & ~(int64_t)7;
+    // a circuit only where an 8-column image alone (2 Nh + 1 rows of 16
+    // bytes) leaves room in shared memory: the covers of larger N are not built
+    if (circuit_enabled() && 2 * nh + 1 <= 0xFFFF && (size_t)(2 * nh + 1) * 16 + 1024 < di.smem_optin) {
         // rows are internal, and so are the gathered rows of pcsr; chunks of
         // 8 columns (measured faster than 16 at n = 8: more CTAs, less
         // shared memory each), 16 where asked by MP_CIRCUIT_WIDTH
