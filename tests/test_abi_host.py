@@ -58,3 +58,12 @@ def test_invalid_path_order_rejected(mp):
             mp.mp_transfer_size(n)
         assert e.value.code == -1
         assert "path order" in mp.mp_last_error()
+
+
+def test_circuit_info_rejects_bad_arguments_before_any_cuda_call(mp):
+    info = np.zeros(6, dtype=np.int64)
+    for n in (0, 17):
+        assert mp.lib().mp_transfer_circuit_info(n, ctypes.c_void_p(info.ctypes.data), 6) == -1
+    assert mp.lib().mp_transfer_circuit_info(5, None, 6) == -1
+    assert mp.lib().mp_transfer_circuit_info(5, ctypes.c_void_p(info.ctypes.data), -1) == -1
+    assert not info.any()
