@@ -153,6 +153,14 @@ int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max,
 /* The same chain for the transfer matrix A(D_n) itself, built on the device
  * from n (no dense A is formed).  The plan for n is cached per device after
  * the first call.  powers_opt / gdiag_opt as above with N = |C_n|.
+ * Where a column chunk fits shared memory (n <= 9 on GB300) the chain runs
+ * on the reuse circuit (mp_transfer_circuit_info) as one launch: each CTA
+ * keeps an 8-column chunk of the powers on chip for every step.  Larger n
+ * run one gather-plan launch per step.  The results are the same bit for
+ * bit.  A repeated call with the same arguments is replayed from a CUDA
+ * graph captured on its second call; a capture that fails (for instance
+ * because another host thread synchronised the whole device meanwhile) is
+ * dropped and the chain runs directly. */
  * With powers_opt NULL the chain computes only one column of every pair
  * {w, reversed w} of column words: reading words backwards is an
  * automorphism of A(D_n), so the dropped columns repeat kept ones, every
