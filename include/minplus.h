@@ -160,7 +160,7 @@ int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max,
  * bit.  A repeated call with the same arguments is replayed from a CUDA
  * graph captured on its second call; a capture that fails (for instance
  * because another host thread synchronised the whole device meanwhile) is
- * dropped and the chain runs directly. */
+ * dropped and the chain runs directly.
  * With powers_opt NULL the chain computes only one column of every pair
  * {w, reversed w} of column words: reading words backwards is an
  * automorphism of A(D_n), so the dropped columns repeat kept ones, every
