@@ -284,7 +284,7 @@ def run_ours(args):
     g9 = gam[9].numpy()
     assert all(int(g9[m - 1]) == -(-11 * m // 3) for m in range(22, K_MAX + 1))
 
-    # ---- per-n chain times and the dominant kernel (one transfer step at n = 9)
+    # ---- per-n chain times and the dominant kernel (the n = 9 circuit chain launch)
     per_n = {}
     for n in PATH_ORDERS:
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
