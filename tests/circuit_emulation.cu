@@ -8,9 +8,17 @@
 // the test can compare them with the oracle; the circuit's statistics go to
 // stderr.
 //
-// usage: circuit_emulation n k width
+// With a fourth argument "image" the chain runs the way the chain kernel
+// keeps it in shared memory instead: one image of 2Nh + 1 rows (X, the
+// result from row Nh, the INF row 2Nh), entry j read at (j + sh) mod 2Nh,
+// result row q written at (Nh + q + sh) mod 2Nh, the labels added in place
+// after each step, and sh swapping between 0 and Nh; the rows between the
+// regions must never be read.
+//
+// usage: circuit_emulation n k width [image]
 #include <cstdarg>
 #include <cstdio>
+#include <string>
 
 #include "../paper_2409_17688_gb300/csrc/circuit.cu"
 
@@ -79,6 +87,47 @@ int main(int argc, char **argv) {
     for (int64_t q = 0; q < N; ++q)
         for (int64_t e = csr.row_ptr[q]; e < csr.row_ptr[q + 1]; ++e) Pk[q * N + csr.col[e]] = csr.val[e];
     fwrite(Pk.data(), 2, Pk.size(), stdout);
+    if (argc > 4 && std::string(argv[4]) == "image") {
+        const int64_t Nh = C.Nh, N2 = 2 * C.Nh;
+        std::vector<uint32_t> img((size_t)((N2 + 1) * N), 0xDEADu);  // gap rows: never read
+        for (int64_t q = 0; q < N; ++q)
+            for (int64_t c = 0; c < N; ++c) img[q * N + c] = (uint32_t)(uint16_t)Pk[q * N + c] + z[q];
+        for (int64_t c = 0; c < N; ++c) img[N2 * N + c] = 0xFFFFu;
+        int64_t sh = 0;
+        auto at = [&](int64_t j) { j += sh; return j >= N2 ? j - N2 : j; };
+        for (int k = 2; k <= kmax; ++k) {
+            for (int l = 0; l < C.levels; ++l)
+                for (int s = C.level_slice0[l]; s < C.level_slice0[l + 1]; ++s) {
+                    const uint32_t e0 = C.slices[2 * s], nb = C.slices[2 * s + 1];
+                    for (int i = 0; i < SR; ++i) {
+                        const uint32_t q = C.rows[(size_t)s * SR + i];
+                        if (q == 0xFFFFFFFFu) continue;
+                        for (int64_t c = 0; c < N; ++c) {
+                            uint32_t acc = INF;
+                            for (uint32_t jb = 0; jb < nb; ++jb)
+                                for (int t = 0; t < 8; ++t) {
+                                    const uint32_t idx =
+                                        jb == 0 ? C.first[((size_t)s * SR + i) * 8 + t]
+                                                : C.ents[((size_t)(e0 + (jb - 1) * SR + i)) * 8 + t];
+                                    if (idx == (uint32_t)N2) continue;  // padding: no load
+                                    if ((idx >= (uint32_t)N && idx < (uint32_t)Nh) || idx >= (uint32_t)(Nh + N))
+                                        return 9;  // a row between the regions
+                                    const uint32_t v = img[at(idx) * N + c];
+                                    if (v == 0xDEADu) return 10;  // never written
+                                    acc = std::min(acc, v);
+                                }
+                            img[at(Nh + q) * N + c] = acc;
+                            Pk[q * N + c] = (int16_t)acc;
+                        }
+                    }
+                }
+            for (int64_t q = 0; q < N; ++q)  // the labels, in place
+                for (int64_t c = 0; c < N; ++c) img[at(Nh + q) * N + c] += z[q];
+            sh = Nh - sh;
+            fwrite(Pk.data(), 2, Pk.size(), stdout);
+        }
+        return 0;
+    }
     std::vector<uint32_t> X((size_t)(N * N)), R((size_t)(N * N));
     for (int k = 2; k <= kmax; ++k) {
         for (int64_t q = 0; q < N; ++q)  // the labelled buffer z_q + P_k[q]

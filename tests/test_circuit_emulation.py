@@ -47,6 +47,18 @@ def test_circuit_semantics_match_oracle(emu, n, k, w):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("n,k,w", [(3, 20, 8), (5, 12, 16), (6, 9, 8)])
+def test_chain_image_bookkeeping_matches_oracle(emu, n, k, w):
+    """The chain kernel's shared-memory image: result rows from Nh, reads at
+    (index + sh) mod 2Nh, labels added in place, regions swapped per step."""
+    r = subprocess.run([emu, str(n), str(k), str(w), "image"], capture_output=True)
+    assert r.returncode == 0, (r.returncode, r.stderr.decode())
+    N = oracle.transfer_size(n)
+    got = np.frombuffer(r.stdout, dtype=np.int16).reshape(k, N, N)
+    want, _ = oracle.power_sequence(oracle.build_transfer(n), k, threads=os.cpu_count() or 1)
+    assert np.array_equal(got, want)
+
+
 def test_circuit_reads_far_fewer_rows_than_arcs(emu):
     # the arc rule nests successor sets: at n = 7 the covers read under a
     # fifth of the arcs
