@@ -124,11 +124,15 @@ int mp_minplus_mul(const void *X, const void *Y, void *Z, int64_t M, int64_t N,
  * that every GPU which loads the library holds until the process exits.
  * Arguments, results and errors as mp_minplus_mul, plus MP_EINVAL when
  * ceil(M/128)*ceil(K/128) + ceil(K/128)*ceil(N/128) exceeds 1048576 (about
- * N = 90000 for square operands).  The first call on a device looks up the
- * array's device address with cudaGetSymbolAddress (with that device
- * current); make that first call before any stream capture.  Every call
- * shares the array: calls whose work overlaps on the GPU (other streams,
- * other host threads) race on it and must be serialized by the caller. */
+ * N = 90000 for square operands).  Unlike mp_minplus_mul, operands whose
+ * rows are off the 8-element grid are not repacked (that would need memory):
+ * they are read in place with scalar loads, which gives the same result
+ * more slowly.  The first call on a device looks up the array's device
+ * address with cudaGetSymbolAddress (with that device current); make that
+ * first call before any stream capture.  The address is kept per device
+ * and looked up again after a cudaDeviceReset.  Every call shares the
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialized by the caller. */
 int mp_minplus_mul_noalloc(const void *X, const void *Y, void *Z, int64_t M, int64_t N,
                            int64_t K, int64_t ldx, int64_t ldy, int64_t ldz, int dtype,
                            void *stream);
@@ -184,6 +188,18 @@ int mp_transfer_power_sequence(int n, int k_max, int16_t *powers_opt,
  * MP_ENOMEM, MP_ECUDA.
  */
 int mp_gamma2_cylinder(int n, int64_t m, int64_t *out);
+
+/* gamma_2(P_n x C_m) by repeated squaring alone (Theorem 2 with the power
+ * algebra of Lemma 1): S_0 = A(D_n), S_j = S_{j-1} (x) S_{j-1} = A^(2^j)
+ * (dense products, int16), R = the product of the S_j over the set bits
+ * of m below its highest bit t, and *out = min_{i,l} R_il + (S_t)_li, the
+ * minimum diagonal entry of A^m, without forming A^m (for m = 2^t,
+ * R = S_t = S_{t-1}).  About log2(m) + popcount(m) dense N^3 products, no
+ * recurrence and no chain; mp_gamma2_cylinder takes this route itself only
+ * when its cost model prefers it.  Needs 4 N^2 * 2 bytes of device memory.
+ * Synchronous; *out is a HOST int64.  Errors: MP_EINVAL (n out of range,
+ * m < 3, out NULL), MP_ERANGE (m * n >= 32767), MP_ENOMEM, MP_ECUDA. */
+int mp_gamma2_squaring(int n, int64_t m, int64_t *out);
 
 /* ---- NEXT f1: the recurrence of Theorem 3 ---------------------------------
  * mp_diff_const (K4): for two DEVICE int16 arrays of count entries, writes to
@@ -354,9 +370,24 @@ int mp_server_destroy(mp_server *server);
  * Runs independent __viaddmin_u16x2 chains on every SM for `iters`
  * iterations and writes the achieved add-min rate (two per instruction) in
  * operations per second to *ops_per_s (HOST).  variant 0: viaddmin u16x2;
- * 1: vimin3 u16x2 (counted as two minima per lane pair); 2: plain vmin u16x2.
- * Synchronous. */
+ * 1: vimin3 u16x2 (counted as two minima per lane pair); 2: plain vmin u16x2;
+ * 3: conflict-free 16-byte shared-memory loads, written as BYTES per second
+ * (the roof of the shared-memory-bound transfer step).  Synchronous. */
 int mp_dpx_peak(int variant, int64_t iters, double *ops_per_s);
+
+/* ---- failure injection (tests) -------------------------------------------
+ * Kernels that wait on the device (the reuse circuit's wait for the bulk
+ * copies of its blob) give up after about a second, latch MP_ETIMEOUT in the
+ * device status word and return, so a stalled copy cannot hang the GPU.
+ * mp_inject_circuit_timeout makes that happen on purpose: it enqueues on
+ * stream one step of A(D_n)'s circuit kernel whose wait expects 16 bytes
+ * that no copy sends.  Every CTA's wait runs out (about two seconds in all,
+ * after the real copies have landed) and the CTA returns without computing
+ * or writing anything; the next mp_device_status() returns MP_ETIMEOUT and
+ * clears it, and the context stays usable.  The paper has no counterpart.
+ * Errors: MP_EINVAL (n out of range or without a circuit), MP_ENOMEM,
+ * MP_ECUDA. */
+int mp_inject_circuit_timeout(int n, void *stream);
 
 /* ---- device status and errors --------------------------------------------
  * mp_device_status synchronizes the current device, then returns MP_OK or

@@ -61,6 +61,8 @@ def lib() -> ctypes.CDLL:
         "mp_minplus_power_sequence": (I, [P, I64, I, P, P, P]),
         "mp_transfer_power_sequence": (I, [I, I, P, P, P]),
         "mp_gamma2_cylinder": (I, [I, I64, P]),
+        "mp_gamma2_squaring": (I, [I, I64, P]),
+        "mp_inject_circuit_timeout": (I, [I, P]),
         "mp_gamma2_table": (I, [I, I, P]),
         "mp_transfer_power_sequences": (I, [P, I, I, P, P]),
         "mp_gamma2_tables": (I, [P, I, I, P]),
@@ -302,6 +304,13 @@ def mp_gamma2_cylinder(n: int, m: int) -> int:
     return int(out.value)
 
 
+def mp_gamma2_squaring(n: int, m: int) -> int:
+    """gamma_2(P_n x C_m) by repeated squaring and a min-trace, synchronous."""
+    out = ctypes.c_int64(0)
+    _check(lib().mp_gamma2_squaring(int(n), int(m), ctypes.byref(out)))
+    return int(out.value)
+
+
 def mp_gamma2_table(n: int, k_max: int) -> np.ndarray:
     """gamma_2(P_n x C_m) for m = 0..k_max (entries m < 3 are -1), synchronous."""
     out = np.zeros(k_max + 1, dtype=np.int64)
@@ -455,6 +464,12 @@ def mp_dpx_peak(variant: int = 0, iters: int = 1 << 16) -> float:
 
 def mp_device_status() -> int:
     return _check(lib().mp_device_status())
+
+
+def mp_inject_circuit_timeout(n: int, stream=None) -> None:
+    """Failure injection: one circuit step of A(D_n) whose bounded device
+    wait runs out; the next mp_device_status() reports MP_ETIMEOUT."""
+    _check(lib().mp_inject_circuit_timeout(int(n), _stream(stream)))
 
 
 def mp_last_error() -> str:

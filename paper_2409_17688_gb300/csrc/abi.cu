@@ -616,6 +616,62 @@ static int transfer_recurrence_ring(int n, int k_limit, int R, Recurrence *out, 
     return MP_OK;
 }
 
+// Repeated squaring (Theorem 2 with the power algebra of Lemma 1):
+// S_0 = A, S_j = S_{j-1} (x) S_{j-1} = A^(2^j), and A^m is the product of the
+// S_j over the set bits j of m.  The highest factor enters only through the
+// min-trace min_{i,l} R_il + S_li, which is min diag (R (x) S) without forming
+// the product.  Dense products on the DPX kernel; four N x N buffers.
+// Synchronous on s; m >= 3 and m * n below the INF code (checked by callers).
+static int gamma2_by_squaring(TransferEntry *te, int64_t m, cudaStream_t s, int32_t *result) {
+    const int64_t N = te->N;
+    const size_t mat = (size_t)N * (size_t)N;
+    DevBuf buf, g;
+    MP_TRY(buf.alloc(4 * mat * 2, s));
+    MP_TRY(g.alloc(sizeof(int32_t), s));
+    int16_t *S = buf.as<int16_t>(), *S2 = S + mat, *R = S + 2 * mat, *R2 = S + 3 * mat;
+    std::vector<WordMasks> masks;
+    word_masks(te->n, te->words, &masks);
+    DevBuf dm;
+    MP_TRY(dm.alloc(masks.size() * sizeof(WordMasks), s));
+    MP_CUDA_TRY(cudaMemcpyAsync(dm.p, masks.data(), masks.size() * sizeof(WordMasks),
+                                cudaMemcpyHostToDevice, s));
+    MP_TRY(launch_build_transfer(te->n, dm.as<WordMasks>(), N, S, N, s));
+    int top = 0;
+    while ((m >> (top + 1)) != 0) ++top;
+    if ((m & (m - 1)) == 0) {
+        // m = 2^top: A^m = S_{top-1} (x) S_{top-1}
+        for (int j = 0; j + 1 < top; ++j) {
+            MP_TRY(dense_minplus(S, S, S2, N, N, N, N, N, N, MP_I16, nullptr, s));
+            std::swap(S, S2);
+        }
+        MP_TRY(launch_min_trace(S, S, N, N, N, g.as<int32_t>(), s));
+    } else {
+        // R collects the factors of the set bits below the top one
+        bool have_r = false;
+        for (int j = 0; j <= top; ++j) {
+            if ((m >> j) & 1) {
+                if (j == top) {
+                    MP_TRY(launch_min_trace(R, S, N, N, N, g.as<int32_t>(), s));
+                    break;
+                }
+                if (!have_r) {
+                    MP_CUDA_TRY(cudaMemcpyAsync(R, S, mat * 2, cudaMemcpyDeviceToDevice, s));
+                    have_r = true;
+                } else {
+                    MP_TRY(dense_minplus(R, S, R2, N, N, N, N, N, N, MP_I16, nullptr, s));
+                    std::swap(R, R2);
+                }
+            }
+            MP_TRY(dense_minplus(S, S, S2, N, N, N, N, N, N, MP_I16, nullptr, s));
+            std::swap(S, S2);
+        }
+    }
+    MP_CUDA_TRY(cudaMemcpyAsync(result, g.as<int32_t>(), 4, cudaMemcpyDeviceToHost, s));
+    // the host masks were copied from pageable memory; the result is read here
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    return MP_OK;
+}
+
 static int check_n(int n) {
     if (n < 1 || n > MP_MAX_PATH_ORDER)
         return set_error(MP_EINVAL, "path order n = %d outside [1, %d]", n, MP_MAX_PATH_ORDER);
@@ -989,60 +1045,36 @@ int mp_gamma2_cylinder(int n, int64_t m, int64_t *out) {
     const double chain_cost = (double)m * (double)N * (double)te->plan.nnz;
     const double lg = std::floor(std::log2((double)m)) + 1.0;
     const double square_cost = 2.5 * (2.0 * lg) * (double)N * (double)N * (double)N;
-    DevBuf g;
-    MP_TRY(g.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(m, 1), s));
-    int32_t result = 0;
-    if (chain_cost <= square_cost || N * N * 2 * 4 > (int64_t)64 << 30) {
-        MP_TRY(mp_transfer_power_sequence(n, (int)m, nullptr, g.as<int32_t>(), s));
-        MP_CUDA_TRY(cudaMemcpyAsync(&result, g.as<int32_t>() + (m - 1), 4, cudaMemcpyDeviceToHost, s));
-    } else {
-        // repeated squaring: S_0 = A, S_j = S_{j-1} (x) S_{j-1}; A^m is the
-        // product of the S_j over the set bits j of m (Lemma 1's algebra), and
-        // the last factor enters only through the min-trace, which gives
-        // min diag of the product without forming it (Theorem 2).
-        const size_t mat = (size_t)N * (size_t)N;
-        DevBuf buf;
-        MP_TRY(buf.alloc(4 * mat * 2, s));
-        int16_t *S = buf.as<int16_t>(), *S2 = S + mat, *R = S + 2 * mat, *R2 = S + 3 * mat;
-        std::vector<WordMasks> masks;
-        word_masks(n, te->words, &masks);
-        DevBuf dm;
-        MP_TRY(dm.alloc(masks.size() * sizeof(WordMasks), s));
-        MP_CUDA_TRY(cudaMemcpyAsync(dm.p, masks.data(), masks.size() * sizeof(WordMasks),
-                                    cudaMemcpyHostToDevice, s));
-        MP_TRY(launch_build_transfer(n, dm.as<WordMasks>(), N, S, N, s));
-        int top = 0;
-        while ((m >> (top + 1)) != 0) ++top;
-        if ((m & (m - 1)) == 0) {
-            // m = 2^top: A^m = S_{top-1} (x) S_{top-1}
-            for (int j = 0; j + 1 < top; ++j) {
-                MP_TRY(dense_minplus(S, S, S2, N, N, N, N, N, N, MP_I16, nullptr, s));
-                std::swap(S, S2);
-            }
-            MP_TRY(launch_min_trace(S, S, N, N, N, g.as<int32_t>(), s));
-        } else {
-            bool have_r = false;
-            for (int j = 0; j <= top; ++j) {
-                if ((m >> j) & 1) {
-                    if (j == top) {
-                        MP_TRY(launch_min_trace(R, S, N, N, N, g.as<int32_t>(), s));
-                        break;
-                    }
-                    if (!have_r) {
-                        MP_CUDA_TRY(cudaMemcpyAsync(R, S, mat * 2, cudaMemcpyDeviceToDevice, s));
-                        have_r = true;
-                    } else {
-                        MP_TRY(dense_minplus(R, S, R2, N, N, N, N, N, N, MP_I16, nullptr, s));
-                        std::swap(R, R2);
-                    }
-                }
-                MP_TRY(dense_minplus(S, S, S2, N, N, N, N, N, N, MP_I16, nullptr, s));
-                std::swap(S, S2);
-            }
-        }
-        MP_CUDA_TRY(cudaMemcpyAsync(&result, g.as<int32_t>(), 4, cudaMemcpyDeviceToHost, s));
+    if (chain_cost > square_cost && N * N * 2 * 4 <= (int64_t)64 << 30) {
+        int32_t result = 0;
+        MP_TRY(gamma2_by_squaring(te, m, s, &result));
+        *out = result;
+        return MP_OK;
     }
+    DevBuf g;
+    MP_TRY(g.alloc(sizeof(int32_t) * (size_t)m, s));
+    int32_t result = 0;
+    MP_TRY(mp_transfer_power_sequence(n, (int)m, nullptr, g.as<int32_t>(), s));
+    MP_CUDA_TRY(cudaMemcpyAsync(&result, g.as<int32_t>() + (m - 1), 4, cudaMemcpyDeviceToHost, s));
     MP_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = result;
+    return MP_OK;
+}
+
+int mp_gamma2_squaring(int n, int64_t m, int64_t *out) {
+    MP_TRY(check_n(n));
+    if (m < 3) return set_error(MP_EINVAL, "cycle length m = %lld < 3", (long long)m);
+    if (!out) return set_error(MP_EINVAL, "out is NULL");
+    if (m * (int64_t)n >= (int64_t)kInf16)
+        return set_error(MP_ERANGE, "m * n = %lld reaches the int16 INF code",
+                         (long long)(m * n));
+    DeviceState *st;
+    MP_TRY(device_state(&st));
+    cudaStream_t s = st->sync_stream;
+    TransferEntry *te;
+    MP_TRY(transfer_entry(n, s, &te));
+    int32_t result = 0;
+    MP_TRY(gamma2_by_squaring(te, m, s, &result));
     *out = result;
     return MP_OK;
 }
@@ -1080,6 +1112,22 @@ int mp_tuning_get(int32_t *table) {
 int mp_dpx_peak(int variant, int64_t iters, double *ops_per_s) {
     if (!ops_per_s) return set_error(MP_EINVAL, "ops_per_s is NULL");
     return dpx_peak(variant, iters, ops_per_s);
+}
+
+int mp_inject_circuit_timeout(int n, void *stream) {
+    MP_TRY(check_n(n));
+    cudaStream_t s = (cudaStream_t)stream;
+    TransferEntry *te;
+    MP_TRY(transfer_entry(n, s, &te));
+    const PlanDev &plan = te->plan;
+    if (!plan.circuit.ready) return set_error(MP_EINVAL, "path order %d has no circuit", n);
+    // valid buffers for the step's reads (the chunk of X is staged before the
+    // wait); nothing is written to them
+    DevBuf B;
+    const size_t elems = (size_t)plan.N * (size_t)plan.ldb;
+    MP_TRY(B.alloc(2 * elems * 2, s));
+    MP_CUDA_TRY(cudaMemsetAsync(B.p, 0, 2 * elems * 2, s));
+    return circuit_timeout_probe(plan, B.as<uint16_t>(), B.as<uint16_t>() + elems, s);
 }
 
 int mp_device_status(void) {

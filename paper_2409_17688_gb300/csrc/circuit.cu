@@ -41,7 +41,10 @@ namespace mp {
 
 namespace {
 
-constexpr int kCircThreads = 512;
+#ifndef MP_CIRC_THREADS
+#define MP_CIRC_THREADS 512
+#endif
+constexpr int kCircThreads = MP_CIRC_THREADS;
 constexpr int kCircWarps = kCircThreads / 32;
 
 __device__ __forceinline__ uint32_t csmem_u32(const void *p) {
@@ -117,6 +120,7 @@ struct CircArgs {
     size_t slot;          // a chain: entries between the caller's powers
     int32_t *gdiag;       // one step: g[k]; a chain: g[0 .. k_max - 1]
     int *status;
+    uint32_t extra_tx;    // bytes expected beyond the circuit's (0; > 0 only to inject a timeout)
 };
 
 __device__ __forceinline__ uint32_t pick_word(const uint4 &v, int k) {
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs 
         s_dmin = (int32_t)kInf16;
         cmbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        cmbar_arrive_expect_tx(bar, a.meta_bytes);
+        cmbar_arrive_expect_tx(bar, a.meta_bytes + a.extra_tx);
         for (uint32_t o = 0; o < a.meta_bytes; o += kMetaCopy)
             cbulk_copy(mb + o, a.meta + o, min(kMetaCopy, a.meta_bytes - o), bar);
     }
@@ -522,7 +526,8 @@ int circuit_upload(const CircuitHost &h, const std::vector<uint16_t> &z,
 
 // One launch: a step (Bin -> Bout) or a whole chain from Bin = P_1.
 static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uint16_t *Bout, int k_max,
-                          int16_t *user_out, size_t slot, int32_t *gdiag, cudaStream_t s) {
+                          int16_t *user_out, size_t slot, int32_t *gdiag, cudaStream_t s,
+                          uint32_t extra_tx = 0) {
     const CircuitDev &c = p.circuit;
     if (!c.ready) return set_error(MP_EINVAL, "plan has no circuit");
     if (p.narrow && user_out) return set_error(MP_EINVAL, "a narrow chain has no full powers to write");
@@ -547,6 +552,7 @@ static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uin
     a.user_out = user_out;
     a.slot = slot;
     a.gdiag = gdiag;
+    a.extra_tx = extra_tx;
     MP_TRY(device_status_ptr(&a.status));
     const size_t smem = circuit_image_bytes(c.Nh, c.W) + c.meta_bytes + kCircBarBytes;
     if (smem > di.smem_optin) return set_error(MP_EINVAL, "circuit does not fit shared memory");
@@ -583,6 +589,14 @@ static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uin
 int circuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,
                  int32_t *gdiag, cudaStream_t s) {
     return circuit_launch(p, false, Bin, Bout, 2, user_out, 0, gdiag, s);
+}
+
+// Failure injection: one step whose circuit copy expects 16 bytes that no
+// copy sends, so every CTA's bounded wait runs out, latches MP_ETIMEOUT and
+// the CTA returns (after a second bounded wait) without writing anything.
+// The real copies are issued before the wait and land long before it ends.
+int circuit_timeout_probe(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, cudaStream_t s) {
+    return circuit_launch(p, false, Bin, Bout, 2, nullptr, 0, nullptr, s, 16);
 }
 
 int circuit_chain(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *powers, size_t slot,

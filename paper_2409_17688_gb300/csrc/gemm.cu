@@ -845,14 +845,25 @@ static __device__ __align__(256) uint8_t g_noalloc_masks[kNoAllocMaskBytes];
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[256] = {};
 
-// Device address of g_noalloc_masks on the current device, looked up once
-// per device with that device current.  In host code the array's name is
-// only a host-side stand-in, never a device address.
+// Device address of g_noalloc_masks on the current device, looked up with
+// that device current the first time a device is used.  In host code the
+// array's name is only a host-side stand-in, never a device address.  A
+// cudaDeviceReset unloads the module, so a cached address is checked on
+// every call and looked up again once it no longer names device memory of
+// this device.
 int noalloc_scratch(uint8_t **out) {
     int dev = -1;
     MP_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 256) return set_error(MP_EINVAL, "device index %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_addr[dev]) {
+        cudaPointerAttributes at;
+        const cudaError_t e = cudaPointerGetAttributes(&at, g_noalloc_addr[dev]);
+        if (e != cudaSuccess || at.type != cudaMemoryTypeDevice || at.device != dev) {
+            cudaGetLastError();
+            g_noalloc_addr[dev] = nullptr;
+        }
+    }
     if (!g_noalloc_addr[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_masks);
@@ -865,14 +876,13 @@ int noalloc_scratch(uint8_t **out) {
     return MP_OK;
 }
 
+// Operands are read in place: rows off the 8-element grid take the product
+// kernel's scalar-load path instead of being repacked (a repack would need
+// memory).
 template <typename T>
 int run_dense_noalloc(const T *X, const T *Y, T *Z, int64_t M, int64_t N, int64_t K,
                       int64_t ldx, int64_t ldy, int64_t ldz, cudaStream_t s) {
-    const int64_t elems16 = 16 / (int64_t)sizeof(T);
-    int vecx = ((uintptr_t)X % 16 == 0) && (ldx % elems16 == 0);
-    int vecy = ((uintptr_t)Y % 16 == 0) && (ldy % elems16 == 0);
-    int vecz = ((uintptr_t)Z % 16 == 0) && (ldz % 8 == 0);
-    const int64_t mb = (M + BM - 1) / BM, nb = (N + BN - 1) / BN;
+    const int64_t mb = (M + MASK_BLOCK - 1) / MASK_BLOCK, nb = (N + MASK_BLOCK - 1) / MASK_BLOCK;
     const int64_t kb = (K + MASK_BLOCK - 1) / MASK_BLOCK;
     const uint8_t *xm = nullptr, *ym = nullptr;
     if (K > 0) {
@@ -889,9 +899,6 @@ int run_dense_noalloc(const T *X, const T *Y, T *Z, int64_t M, int64_t N, int64_
         xm = xmw;
         ym = ymw;
     }
-    (void)vecx;
-    (void)vecy;
-    (void)vecz;
     return launch_product<T>(make_args<T>(X, Y, Z, M, N, K, ldx, ldy, ldz, xm, ym, nullptr), 0, s);
 }
 
@@ -901,15 +908,17 @@ int dense_minplus_noalloc(const void *X, const void *Y, void *Z, int64_t M, int6
                           int64_t K, int64_t ldx, int64_t ldy, int64_t ldz, int dtype,
                           cudaStream_t s) {
     if (M == 0 || N == 0) return MP_OK;
-    const int64_t mb = (M + BM - 1) / BM, nb = (N + BN - 1) / BN;
+    const int64_t mb = (M + MASK_BLOCK - 1) / MASK_BLOCK, nb = (N + MASK_BLOCK - 1) / MASK_BLOCK;
     const int64_t kb = (K + MASK_BLOCK - 1) / MASK_BLOCK;
     if (mb > 65535)
         return set_error(MP_EINVAL, "M = %lld too large for one launch", (long long)M);
-    if ((double)(mb * kb + kb * nb) > (double)kNoAllocMaskBytes)
+    // in double: the block counts are below 2^57, their products may not fit int64
+    const double need = (double)mb * (double)kb + (double)kb * (double)nb;
+    if (need > (double)kNoAllocMaskBytes)
         return set_error(MP_EINVAL,
-                         "problem needs %lld mask bytes; the fixed scratch holds %zu "
+                         "problem needs %.0f mask bytes; the fixed scratch holds %zu "
                          "(ceil(M/128)*ceil(K/128) + ceil(K/128)*ceil(N/128) must not exceed it)",
-                         (long long)(mb * kb + kb * nb), kNoAllocMaskBytes);
+                         need, kNoAllocMaskBytes);
     if (dtype == MP_I16)
         return run_dense_noalloc<uint16_t>((const uint16_t *)X, (const uint16_t *)Y,
                                            (uint16_t *)Z, M, N, K, ldx, ldy, ldz, s);

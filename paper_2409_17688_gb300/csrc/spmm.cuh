@@ -184,5 +184,8 @@ int circuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t 
 // layout; gdiag (optional): g[k - 1] = min diag P_k, folded by atomicMin.
 int circuit_chain(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *powers, size_t slot,
                   int32_t *gdiag, cudaStream_t s);
+// Failure injection: one step whose bounded wait for the circuit's copies
+// runs out (MP_ETIMEOUT latched in the device status word, nothing written).
+int circuit_timeout_probe(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, cudaStream_t s);
 
 }  // namespace mp

@@ -67,3 +67,39 @@ def test_circuit_info_rejects_bad_arguments_before_any_cuda_call(mp):
     assert mp.lib().mp_transfer_circuit_info(5, None, 6) == -1
     assert mp.lib().mp_transfer_circuit_info(5, ctypes.c_void_p(info.ctypes.data), -1) == -1
     assert not info.any()
+
+
+_NOALLOC_REJECT = r"""
+import ctypes, sys
+L = ctypes.CDLL(sys.argv[1])
+f = L.mp_minplus_mul_noalloc
+P, I64 = ctypes.c_void_p, ctypes.c_int64
+f.restype = ctypes.c_int
+f.argtypes = [P, P, P, I64, I64, I64, I64, I64, I64, ctypes.c_int, P]
+L.mp_last_error.restype = ctypes.c_char_p
+big = 200_000  # ceil(200000/128)^2 * 2 mask bytes > 1 MiB
+X = 1 << 32    # never dereferenced: the size check comes first
+rc = f(X, X + (1 << 40), X + (1 << 41), big, big, big, big, big, big, 0, None)
+print(rc, L.mp_last_error().decode())
+# a single row against a 2^30 x 2^30 operand: 2^46 mask bytes
+K = N = 1 << 30
+rc2 = f(X, X + (1 << 40), X + (1 << 33), 1, N, K, K, N, N, 0, None)
+print(rc2, L.mp_last_error().decode())
+"""
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(mp):
+    """The no-allocation product refuses problems whose masks exceed its fixed
+    scratch before any CUDA call.  Run with no visible device, so a
+    regression of the check would fail with MP_ECUDA and launch nothing."""
+    import subprocess
+    import sys
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", _NOALLOC_REJECT, mp.LIB_PATH], env=env,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    lines = r.stdout.strip().splitlines()
+    rc, msg = lines[0].split(" ", 1)
+    assert int(rc) == -1 and "mask bytes" in msg
+    rc2, msg2 = lines[1].split(" ", 1)
+    assert int(rc2) == -1 and "mask bytes" in msg2

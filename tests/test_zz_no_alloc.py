@@ -53,14 +53,3 @@ def test_noalloc_matches_minplus_mul_twice(env):
         assert _call(torch, mp, f, X, Y, got) == 0, mp.mp_last_error()
         torch.cuda.synchronize()
         assert torch.equal(got, want), (M, K, N, dt)
-
-
-def test_noalloc_rejects_sizes_beyond_its_scratch(env):
-    torch, mp, f = env
-    X = torch.zeros((8, 8), dtype=torch.int16, device="cuda")
-    big = 200_000  # ceil(200000/128)^2 * 2 mask bytes > 1 MiB
-    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    rc = f(X.data_ptr(), X.data_ptr() + (1 << 40), X.data_ptr() + (1 << 41), big, big, big,
-           big, big, big, mp.MP_I16, s)
-    assert rc == -1
-    assert "mask bytes" in mp.mp_last_error()
