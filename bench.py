@@ -251,9 +251,10 @@ def run_ours(args):
     full_per_step = sum(Ns[n] * nnz[n] * (K_MAX - 1) for n in PATH_ORDERS)
     dense_per_step = sum(Ns[n] ** 3 * (K_MAX - 1) for n in PATH_ORDERS)
 
-    # ---- DPX peak (K6), measured in this process
+    # ---- DPX and shared-memory peaks (K6), measured in this process
     peak_vimin3 = mp.mp_dpx_peak(1, 1 << 15)
     peak_viaddmin = mp.mp_dpx_peak(0, 1 << 15)
+    peak_smem = mp.mp_dpx_peak(3, 1 << 14)  # bytes/s, conflict-free 16-byte loads
 
     gam = {}
     for _ in range(max(args.warmup, 3)):
@@ -343,8 +344,18 @@ def run_ours(args):
                     "launch_us": round(launch_ms * 1e3, 1),
                     "step_us": round(step_ms * 1e3, 2),
                     "circuit": circ,
+                    # what the kernel executes: one 16-bit minimum per circuit row read and column
+                    "executed_minima": {
+                        "per_s": round(circ["reads"] * cols[9] * steps9 / (launch_ms * 1e-3) / 1e9, 1),
+                        "unit": "G minima/s",
+                        "vs_vimin3_peak": round(circ["reads"] * cols[9] * steps9 / (launch_ms * 1e-3)
+                                                / peak_vimin3, 4),
+                        "rule": f"{circ['reads']} row reads x {cols[9]} columns x {steps9} steps"},
+                    # what the sparse product it replaces would evaluate (nnz(A) terms per column)
                     "product_equivalent": {"terms_per_s": round(achieved / 1e9, 1), "unit": "G terms/s",
-                                           "vs_vimin3_peak": round(achieved / peak_vimin3, 4)}}
+                                           "vs_vimin3_peak": round(achieved / peak_vimin3, 4),
+                                           "note": "terms of the sparse product A (x) P; the circuit "
+                                                   f"executes {circ['reads']} of every {nnz[9]}"}}
 
     # ---- e2e through the C ABI with host buffers (synchronous gamma_2 tables)
     out = np.zeros((len(PATH_ORDERS), K_MAX + 1), dtype=np.int64)
@@ -359,6 +370,7 @@ def run_ours(args):
            "api": "mp_gamma2_tables (synchronous, host int64 output)"}
 
     # ---- the dense N = 8192 products (K1), reported beside the chain
+    full = full_powers_extras(mp, torch, lib, sptr, stream, flush, Ns, nnz)
     dense = dense_extras(mp, torch, flush, stream, peak_viaddmin) if not args.no_dense else None
     batched = batched_extras(mp, torch, flush) if not args.no_batched else None
     serving = serving_extras(mp, torch) if not args.no_serving else None
@@ -370,14 +382,17 @@ def run_ours(args):
 
     clocks = clk.summary()
     if roofline is not None:
-        # shared-memory pipe: 32 banks x 4 bytes per clock per SM, at the clock
-        # sampled under load (nominal maximum when unsampled)
+        # the measured shared-memory load rate of this GPU (K6 variant 3); the
+        # nominal pipe (32 banks x 4 bytes per clock per SM at the sampled
+        # clock) is given beside it
         mhz = clocks.get("sm_mhz") or 2070
-        peak_smem = 128.0 * props.multi_processor_count * mhz * 1e6
+        nominal = 128.0 * props.multi_processor_count * mhz * 1e6
         roofline["peak"] = round(peak_smem / 1e9, 1)
         roofline["frac"] = round(roofline["achieved"] * 1e9 / peak_smem, 4)
-        roofline["peak_source"] = (f"derived: 128 B/clk/SM x {props.multi_processor_count} SMs x {mhz} MHz "
-                                   "(sampled SM clock)")
+        roofline["peak_source"] = ("measured in this process: K6 shared-memory probe (mp_dpx_peak variant 3, "
+                                   "conflict-free 16-byte loads, 8 CTAs per SM)")
+        roofline["nominal_peak"] = {"value": round(nominal / 1e9, 1), "unit": "GB/s",
+                                    "rule": f"128 B/clk/SM x {props.multi_processor_count} SMs x {mhz} MHz"}
     # our launches per chain: the diagonal fill, the initial power and the
     # chain (one launch with a circuit, one per step without)
     per_chain = {n: 3 if mp.mp_transfer_circuit_info(n)["width"] > 0 else K_MAX + 1 for n in PATH_ORDERS}
@@ -399,11 +414,16 @@ def run_ours(args):
         "time_to_gamma2_ms": round(ms_per_step, 3),
         "dense_equiv_gops": round(dense_per_step * args.steps * world / (ms_total * 1e-3) / 1e9, 1),
         "full_matrix_equiv_gops": round(full_per_step * args.steps * world / (ms_total * 1e-3) / 1e9, 1),
+        "value_counts": ("product-equivalent: N*nnz(A) terms per product on the computed columns, "
+                         "the terms the sparse product would evaluate; the reuse circuit executes a "
+                         "fraction of them (roofline.executed_minima)"),
         "dpx_peak_gops": {"vimin3_u16x2": round(peak_vimin3 / 1e9, 1),
-                          "viaddmin_u16x2": round(peak_viaddmin / 1e9, 1)},
+                          "viaddmin_u16x2": round(peak_viaddmin / 1e9, 1),
+                          "smem_load_gbs": round(peak_smem / 1e9, 1)},
         "per_n": per_n, "setup_ms": {n: round(v, 2) for n, v in setup.items()},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
+    line["full_powers"] = full
     if dense is not None:
         line["dense_gemm"] = dense
     if batched is not None:
@@ -416,6 +436,47 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def full_powers_extras(mp, torch, lib, sptr, stream, flush, Ns, nnz):
+    """The full-powers form of the same workload (Algorithm 2 as the paper
+    stores it): every power A^1..A^200 of each path order written to HBM
+    (int16, slot k-1 = A^k, N x N) with its min-diagonals, one order at a
+    time.  Written bytes are set against the measured copy bandwidth."""
+    hbm = hbm_frac(1.0)
+    peak = hbm["peak_gbs"] * 1e9 if hbm else None
+    out = {}
+    for n in PATH_ORDERS:
+        N = Ns[n]
+        P = torch.empty((K_MAX, N, N), dtype=torch.int16, device=stream.device)
+        g = torch.empty(K_MAX, dtype=torch.int32, device=stream.device)
+
+        def call():
+            mp._check(lib.mp_transfer_power_sequence(n, K_MAX, ctypes.c_void_p(P.data_ptr()),
+                                                     ctypes.c_void_p(g.data_ptr()), sptr))
+        for _ in range(3):  # the second call is captured into a graph, later calls replay it
+            call()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            flush.fill_(9)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            call()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = min(ts)
+        written = K_MAX * N * N * 2
+        out[n] = {"N": N, "ms": round(ms, 3), "bytes_written": written,
+                  "write_gbs": round(written / (ms * 1e-3) / 1e9, 1),
+                  "frac_of_hbm": round(written / (ms * 1e-3) / peak, 4) if peak else None,
+                  "full_matrix_terms_per_s": round(N * nnz[n] * (K_MAX - 1) / (ms * 1e-3) / 1e9, 1)}
+        del P, g
+        torch.cuda.empty_cache()
+    out["note"] = ("every power written in the caller's layout; frac_of_hbm = written bytes / time "
+                   "against MEASURED_PEAKS hbm_gbs (measured copy)")
+    return out
 
 
 def block_active_ops(X, Y, inf, block=128):
@@ -583,6 +644,48 @@ def serving_extras(mp, torch):
         out[f"rate_{f}mu"] = dict(run(arr), offered_qps=round(f * mu, 1))
     out["stats"] = srv.stats()
     srv.close()
+    out["plain"] = serving_plain(mp, ns, ms, truth, mu)
+    return out
+
+
+def serving_plain(mp, ns, ms, truth, mu):
+    """The same stream answered without continuous batching, on bounded
+    samples: (i) one query at a time through a server with one query per
+    launch (resident powers kept: the batching alone is taken away), the
+    next query submitted when the last is answered; (ii) one transfer chain
+    per query (Algorithm 2 to m, nothing resident but the cached plan), the
+    paper's own way to get one gamma_2."""
+    out = {}
+    srv = mp.Server(hbm_budget=64 << 30, max_batch=1, max_m=2000, max_tickets=1 << 15)
+    for n in range(2, 11):
+        srv.wait(srv.submit(n, 1000), timeout_s=600)
+    S = 2000
+    bad = 0
+    t0 = time.perf_counter()
+    for i in range(S):
+        t = srv.submit(int(ns[i]), int(ms[i]))
+        v = srv.poll(t)
+        while v is None:
+            v = srv.poll(t)
+        bad += v != truth[(int(ns[i]), int(ms[i]))]
+    dt = time.perf_counter() - t0
+    srv.close()
+    out["one_query_per_launch"] = {"qps": round(S / dt, 1), "sample": f"first {S} queries, closed loop",
+                                   "wrong": int(bad),
+                                   "continuous_batching_speedup": round(mu / (S / dt), 2)}
+    S2 = 40
+    for n in range(2, 11):
+        mp.mp_gamma2_table(n, 3)  # plans built outside the timed loop
+    bad = 0
+    t0 = time.perf_counter()
+    for i in range(S2):
+        n, m = int(ns[i]), int(ms[i])
+        v = int(mp.mp_gamma2_table(n, m)[m])
+        bad += v != truth[(n, m)]
+    dt = time.perf_counter() - t0
+    out["one_chain_per_query"] = {"qps": round(S2 / dt, 2), "sample": f"first {S2} queries",
+                                  "wrong": int(bad),
+                                  "continuous_batching_speedup": round(mu / (S2 / dt), 1)}
     return out
 
 

@@ -236,25 +236,15 @@ static int transfer_entry(int n, cudaStream_t s, TransferEntry **out) {
     // a circuit only where an 8-column image alone (2 Nh + 1 rows of 16
     // bytes) leaves room in shared memory: the covers of larger N are not built
     if (circuit_enabled() && 2 * nh + 1 <= 0xFFFF && (size_t)(2 * nh + 1) * 16 + 1024 < di.smem_optin) {
-        // rows are internal, and so are the gathered rows of pcsr; chunks of
-        // 8 columns (measured faster than 16 at n = 8: more CTAs, less
-        // shared memory each), 16 where asked by MP_CIRCUIT_WIDTH
-        CircuitCover cv;
-        MP_TRY(circuit_cover_host(pcsr, &cv));
-        const char *wenv = getenv("MP_CIRCUIT_WIDTH");
-        const int only = wenv ? atoi(wenv) : 0;
-        for (int w : {8, 16}) {
-            if (only && w != only) continue;
-            CircuitHost ch;
-            MP_TRY(circuit_slice_host(cv, w, &ch));
-            size_t bytes = 0;
-            MP_TRY(circuit_smem_bytes(ch, &bytes));
-            if (bytes > 0 && e->plan.ldb % w == 0) {
-                e->circuit = std::move(ch);
-                break;
-            }
+        // rows are internal, and so are the gathered rows of pcsr
+        CircuitHost ch;
+        MP_TRY(circuit_build_host(pcsr, &ch));
+        size_t bytes = 0;
+        MP_TRY(circuit_smem_bytes(ch, &bytes));
+        if (bytes > 0 && e->plan.ldb % kCircW == 0) {
+            e->circuit = std::move(ch);
+            MP_TRY(circuit_upload(e->circuit, pz, canon, canon, &e->plan, s));
         }
-        if (e->circuit.W > 0) MP_TRY(circuit_upload(e->circuit, pz, canon, canon, &e->plan, s));
     }
     e->h2d_bytes = masks.size() * sizeof(WordMasks) + (size_t)(N + 1) * 8 + (size_t)nnz * 2 +
                    e->plan.h2d_bytes;
@@ -300,7 +290,7 @@ static int narrow_plan(TransferEntry *te, cudaStream_t s, const PlanDev **out) {
         ph.colpos = colpos;
         MP_TRY(plan_upload(ph, &te->plan_narrow, s, true));
         MP_CUDA_TRY(cudaStreamSynchronize(s));
-        if (te->circuit.W > 0 && te->plan_narrow.ldb % te->circuit.W == 0)
+        if (te->circuit.W > 0 && te->plan_narrow.ldb % kCircW == 0)
             MP_TRY(circuit_upload(te->circuit, te->pz, dcol, te->canon, &te->plan_narrow, s));
         te->narrow_cols = ncols;
         te->have_narrow = true;
@@ -382,6 +372,7 @@ static int device_free_bytes(cudaStream_t s, size_t *free_b) {
 }
 
 static int transfer_recurrence(int n, int K, Recurrence *out, cudaStream_t s) {
+    NvtxScope nv("mp_transfer_recurrence n=%d K=%d", n, K);
     const int64_t N = words_of(n);
     const size_t mat = (size_t)N * (size_t)N;
     size_t free_b = 0;
@@ -472,6 +463,7 @@ constexpr size_t kChainGraphCap = 32;
 int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
                             int32_t *gdiag_opt, cudaStream_t s) {
     if (k_max < 1) return set_error(MP_EINVAL, "k_max = %d < 1", k_max);
+    NvtxScope nv("mp_transfer_chain n=%d k_max=%d%s", n, k_max, powers_opt ? " powers" : "");
     TransferEntry *te;
     MP_TRY(transfer_entry(n, s, &te));
     if (slot < (size_t)te->N * (size_t)te->N) return set_error(MP_EINVAL, "slot stride too small");
@@ -558,6 +550,7 @@ int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
 // n0 of Algorithm 4 and the period a with its constant b (Lemma 1 carries
 // it to every later power).
 static int transfer_recurrence_ring(int n, int k_limit, int R, Recurrence *out, cudaStream_t s) {
+    NvtxScope nv("mp_transfer_recurrence_stream n=%d ring=%d", n, R);
     // The ring is the chain itself, narrow: slot (k - 1) % R holds the k-th
     // buffer z + P_k on the mirror-representative columns.  Labels cancel in
     // a difference, and a difference that is constant on those columns is
@@ -623,6 +616,7 @@ static int transfer_recurrence_ring(int n, int k_limit, int R, Recurrence *out, 
 // the product.  Dense products on the DPX kernel; four N x N buffers.
 // Synchronous on s; m >= 3 and m * n below the INF code (checked by callers).
 static int gamma2_by_squaring(TransferEntry *te, int64_t m, cudaStream_t s, int32_t *result) {
+    NvtxScope nv("mp_gamma2_squaring n=%d m=%lld", te->n, (long long)m);
     const int64_t N = te->N;
     const size_t mat = (size_t)N * (size_t)N;
     DevBuf buf, g;

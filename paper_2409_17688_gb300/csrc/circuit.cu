@@ -14,22 +14,26 @@
 // the same minimum, bit for bit.
 //
 // Host: successor sets as bitsets; for each row, in order of set size, the
-// rows whose sets it contains, then the greedy cover (take the candidate
-// covering most of what is still uncovered while it covers at least two).
-// A row's level is one more than the deepest row of its cover.  Each level's
-// rows, longest list first, are cut into slices of one warp's rows; a slice
-// stores its lists in blocks of 8 row indices per row (16 bytes, one load
-// per lane for 8 entries; a short list is padded with the INF row).
+// rows whose sets it contains, then the greedy cover: take the candidate
+// whose coverage of what is still uncovered, less kCircLambda for every
+// level it would add to the row, is largest, while that score is at least
+// two.  A row's level is one more than the deepest row of its cover; the
+// level penalty trades a few more reads for fewer, fuller levels.  Each
+// level's rows become lane tasks of at most 8 list entries (16 bytes, one
+// load per lane): a longer list takes an aligned group of 2, 4, .. 32
+// lanes.  Rows are packed widest first into warp slices of 32 lanes, so
+// every lane of a level does the same work.
 //
-// Device (circuit_step_kernel): one CTA per chunk of W columns.  The circuit
+// Device (circuit_step_kernel): one CTA per chunk of 8 columns.  The circuit
 // (one blob, the same for every chunk and every step) is copied into shared
-// memory while the previous step finishes; then the chunk of X (N rows of W
+// memory while the previous step finishes; then the chunk of X (N rows of 8
 // columns).  The levels run in order with a block barrier between them,
 // touching only shared memory: a warp takes every 16th slice of a level,
-// each lane (or lane pair at W = 16) one row, 16 bytes of it per lane.  A
-// row's result goes to shared memory for the later levels and, with its
-// label added, straight to the next buffer; the diagonal entries are
-// min-reduced and folded into g[k].
+// each lane folds its 8 rows (16 bytes of each), the lanes of a row combine
+// by shuffles and the first of them writes the row's result to shared memory
+// for the later levels and, with its label added, straight to the next
+// buffer.  After the levels the (at most 8) rows whose diagonal entries lie
+// in the chunk are read back and min-reduced into g[k].
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -41,10 +45,7 @@ namespace mp {
 
 namespace {
 
-#ifndef MP_CIRC_THREADS
-#define MP_CIRC_THREADS 512
-#endif
-constexpr int kCircThreads = MP_CIRC_THREADS;
+constexpr int kCircThreads = 512;
 constexpr int kCircWarps = kCircThreads / 32;
 
 __device__ __forceinline__ uint32_t csmem_u32(const void *p) {
@@ -56,11 +57,6 @@ __device__ __forceinline__ void ccp_async16(uint32_t dst, const void *src) {
 __device__ __forceinline__ uint32_t clds_u32(uint32_t addr) {
     uint32_t v;
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-    return v;
-}
-__device__ __forceinline__ uint2 clds_v2(uint32_t addr) {
-    uint2 v;
-    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
     return v;
 }
 __device__ __forceinline__ uint4 clds_v4(uint32_t addr) {
@@ -113,11 +109,13 @@ struct CircArgs {
     uint16_t *Bout;       // one step: the labelled buffer of P_{k+1}
     int64_t N, Nh, ldb;
     const uint8_t *meta;
-    uint32_t meta_bytes, off_slices, off_rowinfo, off_first, off_ents, off_z;
+    uint32_t meta_bytes, off_info, off_ents, off_z;
     int levels;
     int k_max;            // a chain: P_2 .. P_{k_max}
     int16_t *user_out;    // the caller's power(s), or null
     size_t slot;          // a chain: entries between the caller's powers
+    const int32_t *caller;   // per internal row, the caller's row (for user_out)
+    const uint16_t *drow;    // per buffer column, the row whose diagonal entry it holds
     int32_t *gdiag;       // one step: g[k]; a chain: g[0 .. k_max - 1]
     int *status;
     uint32_t extra_tx;    // bytes expected beyond the circuit's (0; > 0 only to inject a timeout)
@@ -160,27 +158,23 @@ __host__ __device__ __forceinline__ size_t circuit_image_bytes(int64_t N, int W)
 constexpr uint32_t kCircBarBytes = 16;
 constexpr uint32_t kMetaCopy = 32768;  // bytes per bulk copy of the circuit
 
-// W columns per CTA; a row is 2W bytes, read by W / 8 lanes (16 bytes each).
 // One step (kChain false): X from Bin, the result (labelled) to Bout.  A
 // chain (kChain true): the CTA runs every step of the chain on its chunk
 // without leaving the SM -- column chunk c of P_{k+1} depends only on chunk c
 // of P_k -- so after a step the result region, with the labels added in
-// place, is the next step's X, and the two regions swap: with sh = 0 or N,
+// place, is the next step's X, and the two regions swap: with sh = 0 or Nh,
 // image index j (X rows 0..N-1, result rows Nh..Nh+N-1, Nh = N rounded up to
-// 8) lives at (j + sh) mod 2Nh, sh = 0 or Nh.
-template <int W, bool kChain>
+// 8) lives at (j + sh) mod 2Nh.
+template <bool kChain>
 __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs a) {
-    constexpr int LPR = W / 8;       // lanes per row
-    constexpr int SR = 32 / LPR;     // rows per slice
-    constexpr int RB = 2 * W;        // bytes per row
+    constexpr int RB = 2 * kCircW;  // bytes per image row
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t sbase = csmem_u32(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t N = a.N;
     const uint32_t Nh = (uint32_t)a.Nh, N2 = 2 * Nh;
-    const int64_t c0 = (int64_t)blockIdx.x * W;
-    const uint32_t mb = sbase + (uint32_t)circuit_image_bytes(Nh, W);
-    __shared__ int32_t s_dmin;
+    const int64_t c0 = (int64_t)blockIdx.x * kCircW;
+    const uint32_t mb = sbase + (uint32_t)circuit_image_bytes(Nh, kCircW);
 
     // The circuit: plan data only, so its bulk copies start before the
     // previous step has finished.  The barrier's initialisation is made
@@ -188,7 +182,6 @@ __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs 
     // them waits on it.
     const uint32_t bar = mb + a.meta_bytes;
     if (threadIdx.x == 0) {
-        s_dmin = (int32_t)kInf16;
         cmbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         cmbar_arrive_expect_tx(bar, a.meta_bytes + a.extra_tx);
@@ -197,15 +190,15 @@ __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs 
     }
     // row 2Nh of the image: above every value, the padding of short lists
     if (threadIdx.x < RB / 4) reinterpret_cast<uint32_t *>(smem + (size_t)N2 * RB)[threadIdx.x] = 0xFFFFFFFFu;
+    // the row whose diagonal entry lies in column c0 + t (threads t < 8)
+    uint32_t drow = 0xFFFFu;
+    if (a.gdiag && threadIdx.x < kCircW) drow = a.drow[c0 + threadIdx.x];
     // Programmatic dependent launch: the previous step's output (our X) is
     // read only after its grid has completed.
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    // X's chunk: N rows of RB bytes, in 16-byte pieces
-    for (int64_t pc = threadIdx.x; pc < N * LPR; pc += kCircThreads) {
-        const int64_t r = pc / LPR;
-        const int part = (int)(pc - r * LPR);
-        ccp_async16(sbase + (uint32_t)(r * RB + part * 16), a.Bin + r * a.ldb + c0 + part * 8);
-    }
+    // X's chunk: N rows of 16 bytes
+    for (int64_t r = threadIdx.x; r < N; r += kCircThreads)
+        ccp_async16(sbase + (uint32_t)r * RB, a.Bin + r * a.ldb + c0);
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
@@ -218,82 +211,85 @@ __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs 
         return;
     }
 
-    const int i = lane / LPR, h = lane % LPR;
-    const uint32_t hb = (uint32_t)h * 16;
-    const int64_t col0 = c0 + (int64_t)h * 8;
-    const uint32_t m_sl = mb + a.off_slices, m_ri = mb + a.off_rowinfo;
-    const uint32_t m_fi = mb + a.off_first, m_en = mb + a.off_ents;
+    const uint32_t m_info = mb + a.off_info, m_en = mb + a.off_ents, m_z = mb + a.off_z;
+    auto label = [&](uint32_t q) {
+        const uint32_t zw = clds_u32(m_z + 4u * (q >> 1));
+        return (q & 1) ? zw >> 16 : zw & 0xFFFFu;
+    };
     const int k_last = kChain ? a.k_max : 2;
     uint32_t sh = 0;
     for (int k = 2; k <= k_last; ++k) {
-        int32_t dmin = (int32_t)kInf16;
         for (int l = 0; l < a.levels; ++l) {
             const int s1 = (int)clds_u32(mb + 4u * (uint32_t)(l + 1));
             for (int s = (int)clds_u32(mb + 4u * (uint32_t)l) + warp; s < s1; s += kCircWarps) {
-                const uint32_t slot = (uint32_t)s * SR + (uint32_t)i;
-                const uint2 d = clds_v2(m_sl + 8u * (uint32_t)s);
-                const uint2 ri = clds_v2(m_ri + 8u * slot);
+                const uint32_t slot = (uint32_t)s * 32u + (uint32_t)lane;
+                const uint32_t info = clds_u32(m_info + 4u * slot);
                 uint4 acc = make_uint4(kInf16x2, kInf16x2, kInf16x2, kInf16x2);
-                fold8<RB>(acc, clds_v4(m_fi + 16u * slot), sbase + hb, N2, sh);
-                // the few rows longer than one block: their later blocks
-                for (uint32_t jb = 1; jb < d.y; ++jb)
-                    fold8<RB>(acc, clds_v4(m_en + 16u * (d.x + (jb - 1) * SR + (uint32_t)i)), sbase + hb,
-                              N2, sh);
-                const uint32_t q = ri.x & 0xFFFFu;
-                if (q == 0xFFFFu) continue;
+                fold8<RB>(acc, clds_v4(m_en + 16u * slot), sbase, N2, sh);
+                // the lanes of one row (an aligned group of 1 << lg) combine;
+                // the slice's widest row sits in lane 0
+                const uint32_t lg = (info >> 16) & 7u;
+                const uint32_t lg0 = __shfl_sync(0xFFFFFFFFu, lg, 0);
+                for (uint32_t o = 1; o < (1u << lg0); o <<= 1) {
+                    const uint32_t vx = __shfl_xor_sync(0xFFFFFFFFu, acc.x, o);
+                    const uint32_t vy = __shfl_xor_sync(0xFFFFFFFFu, acc.y, o);
+                    const uint32_t vz = __shfl_xor_sync(0xFFFFFFFFu, acc.z, o);
+                    const uint32_t vw = __shfl_xor_sync(0xFFFFFFFFu, acc.w, o);
+                    if (o < (1u << lg))
+                        acc = make_uint4(__vminu2(acc.x, vx), __vminu2(acc.y, vy), __vminu2(acc.z, vz),
+                                         __vminu2(acc.w, vw));
+                }
+                const uint32_t q = info & 0xFFFFu;
+                if (q == 0xFFFFu || (lane & ((1u << lg) - 1u)) != 0) continue;
                 // the result row, for the later levels (and the next step)
                 uint32_t rr = Nh + q + sh;
                 if (rr >= N2) rr -= N2;
-                csts_v4(sbase + rr * RB + hb, acc);
+                csts_v4(sbase + rr * RB, acc);
                 if (!kChain) {
-                    const uint32_t zq = (ri.x >> 16) * 0x10001u;
-                    *reinterpret_cast<uint4 *>(a.Bout + (int64_t)q * a.ldb + col0) =
+                    const uint32_t zq = label(q) * 0x10001u;
+                    *reinterpret_cast<uint4 *>(a.Bout + (int64_t)q * a.ldb + c0) =
                         make_uint4(acc.x + zq, acc.y + zq, acc.z + zq, acc.w + zq);
-                }
-                const uint32_t dc = ri.y & 0xFFFFu;
-                if (a.gdiag && dc != 0xFFFFu && (int64_t)dc >= col0 && (int64_t)dc < col0 + 8) {
-                    const int kk = (int)((int64_t)dc - col0);
-                    const uint32_t wv = pick_word(acc, kk >> 1);
-                    dmin = min(dmin, (int32_t)((kk & 1) ? wv >> 16 : wv & 0xFFFFu));
                 }
                 if (a.user_out) {
                     int16_t *orow = a.user_out + (kChain ? (size_t)(k - 1) * a.slot : 0) +
-                                    (int64_t)(ri.y >> 16) * N;
+                                    (int64_t)a.caller[q] * N;
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk) {
                         const uint32_t wv = pick_word(acc, kk >> 1);
-                        if (col0 + kk < N) orow[col0 + kk] = (int16_t)((kk & 1) ? wv >> 16 : wv & 0xFFFFu);
+                        if (c0 + kk < N) orow[c0 + kk] = (int16_t)((kk & 1) ? wv >> 16 : wv & 0xFFFFu);
                     }
                 }
             }
             __syncthreads();  // this level's rows are read by the later levels
         }
-        if (a.gdiag) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) dmin = min(dmin, __shfl_xor_sync(0xFFFFFFFFu, dmin, o));
-            if (lane == 0 && dmin < (int32_t)kInf16) atomicMin(&s_dmin, dmin);
-        }
+        const uint32_t shr = sh;  // where this step's result rows are
         if (kChain) {
             // the labels, in place: the result becomes the next step's X
-            const uint32_t m_z = mb + a.off_z;
-            for (int64_t pc = threadIdx.x; pc < N * LPR; pc += kCircThreads) {
-                const uint32_t q = (uint32_t)(pc / LPR);
-                const uint32_t part = (uint32_t)(pc - (int64_t)q * LPR);
-                uint32_t rr = Nh + q + sh;
+            for (int64_t q = threadIdx.x; q < N; q += kCircThreads) {
+                uint32_t rr = Nh + (uint32_t)q + sh;
                 if (rr >= N2) rr -= N2;
-                const uint32_t addr = sbase + rr * RB + part * 16;
-                const uint32_t zw = clds_u32(m_z + 4u * (q >> 1));
-                const uint32_t zq = ((q & 1) ? zw >> 16 : zw & 0xFFFFu) * 0x10001u;
+                const uint32_t addr = sbase + rr * RB;
+                const uint32_t zq = label((uint32_t)q) * 0x10001u;
                 const uint4 v = clds_v4(addr);
                 csts_v4(addr, make_uint4(v.x + zq, v.y + zq, v.z + zq, v.w + zq));
             }
             sh = Nh - sh;
+            __syncthreads();
         }
-        __syncthreads();
-        if (threadIdx.x == 0 && a.gdiag) {
-            const int32_t v = s_dmin;
-            if (v < (int32_t)kInf16) atomicMin(kChain ? a.gdiag + (k - 1) : a.gdiag, v);
-            s_dmin = (int32_t)kInf16;  // the next step's minima arrive after its levels
+        if (a.gdiag && warp == 0) {
+            // the diagonal entries of this chunk (unlabelled); the next step
+            // writes only the other region, so nothing races with these reads
+            int32_t v = (int32_t)kInf16;
+            if (lane < kCircW && drow != 0xFFFFu) {
+                uint32_t rr = Nh + drow + shr;
+                if (rr >= N2) rr -= N2;
+                const uint32_t w = clds_u32(sbase + rr * RB + 4u * (uint32_t)(lane >> 1));
+                v = (int32_t)((lane & 1) ? w >> 16 : w & 0xFFFFu);
+                if (kChain) v -= (int32_t)label(drow);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+            if (lane == 0 && v < (int32_t)kInf16) atomicMin(kChain ? a.gdiag + (k - 1) : a.gdiag, v);
         }
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -301,9 +297,10 @@ __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs 
 
 }  // namespace
 
-int circuit_cover_host(const HostCsr &csr, CircuitCover *out) {
+int circuit_cover_host(const HostCsr &csr, CircuitCover *out, int lambda) {
     const int64_t N = csr.N;
     if (N < 1 || 2 * N + 1 > 0xFFFF) return set_error(MP_EINVAL, "N = %lld too large for a circuit", (long long)N);
+    if (lambda < 0) return set_error(MP_EINVAL, "level penalty %d < 0", lambda);
     CircuitCover &C = *out;
     C = CircuitCover();
     C.N = N;
@@ -345,19 +342,24 @@ int circuit_cover_host(const HostCsr &csr, CircuitCover *out) {
         std::vector<uint32_t> &li = C.lists[(size_t)q];
         int lv = 0;
         while (!cand.empty()) {
-            int64_t best = -1, bg = 1;
+            // score: arcs still uncovered that the candidate covers, less the
+            // penalty for each level it adds to this row; a cover must score
+            // at least two (one read for two or more)
+            int64_t best = -1, bs = 1;
             size_t bi = 0;
             for (size_t k = 0; k < cand.size(); ++k) {
                 const uint64_t *Sc = &S[(size_t)(cand[k] * nw)];
                 int64_t g = 0;
                 for (int64_t w = 0; w < nw; ++w) g += __builtin_popcountll(Sc[w] & U[(size_t)w]);
-                if (g > bg) {
-                    bg = g;
+                const int64_t added = std::max(0, C.level[(size_t)cand[k]] + 1 - lv);
+                const int64_t sc = g - (int64_t)lambda * added;
+                if (g > 1 && sc > bs) {
+                    bs = sc;
                     best = cand[k];
                     bi = k;
                 }
             }
-            if (best < 0) break;  // no candidate covers two or more: read the rest directly
+            if (best < 0) break;  // nothing left worth a cover: read the rest directly
             const uint64_t *Sb = &S[(size_t)(best * nw)];
             for (int64_t w = 0; w < nw; ++w) U[(size_t)w] &= ~Sb[w];
             li.push_back((uint32_t)(N + best));
@@ -375,101 +377,201 @@ int circuit_cover_host(const HostCsr &csr, CircuitCover *out) {
     return MP_OK;
 }
 
-int circuit_slice_host(const CircuitCover &cv, int W, CircuitHost *out) {
-    if (W != 8 && W != 16) return set_error(MP_EINVAL, "circuit width %d", W);
+int circuit_slice_host(const CircuitCover &cv, CircuitHost *out) {
     const int64_t N = cv.N;
     CircuitHost &C = *out;
     C = CircuitHost();
     C.N = N;
     C.Nh = (N + 7) & ~(int64_t)7;
-    C.W = W;
+    C.W = kCircW;
     C.levels = cv.levels;
     C.reads = cv.reads;
     C.cover_reads = cv.cover_reads;
-    // per level: rows longest list first, cut into slices of one warp's rows
-    const int SR = 32 / (W / 8);
-    if (2 * C.Nh + 1 > 0xFFFF) return set_error(MP_EINVAL, "N = %lld too large for a circuit", (long long)N);
+    if (2 * C.Nh + 1 > 0xFFFF || N >= 0xFFFF)
+        return set_error(MP_EINVAL, "N = %lld too large for a circuit", (long long)N);
     const uint16_t pad = (uint16_t)(2 * C.Nh);
     // a list entry in image rows: X rows stay, result row N + q' moves to Nh + q'
     auto img = [&](uint32_t v) { return v < (uint32_t)N ? v : v - (uint32_t)N + (uint32_t)C.Nh; };
+    auto lanes_log2 = [](size_t len) {
+        int lg = 0;
+        while (((size_t)8 << lg) < len) ++lg;
+        return lg;
+    };
     C.level_slice0.push_back(0);
     for (int l = 0; l < C.levels; ++l) {
-        std::vector<int64_t> lr;
-        for (int64_t q = 0; q < N; ++q)
-            if (cv.level[(size_t)q] == l) lr.push_back(q);
-        std::stable_sort(lr.begin(), lr.end(), [&](int64_t x, int64_t y) {
-            return cv.lists[(size_t)x].size() > cv.lists[(size_t)y].size();
-        });
-        for (size_t r0 = 0; r0 < lr.size(); r0 += (size_t)SR) {
-            const size_t r1 = std::min(lr.size(), r0 + (size_t)SR);
-            const size_t len = cv.lists[(size_t)lr[r0]].size();
-            const uint32_t nb = (uint32_t)std::max<size_t>(1, (len + 7) / 8);
-            C.slices.push_back((uint32_t)(C.ents.size() / 8));
-            C.slices.push_back(nb);
-            for (int i = 0; i < SR; ++i)
-                C.rows.push_back(r0 + (size_t)i < r1 ? (uint32_t)lr[r0 + (size_t)i] : 0xFFFFFFFFu);
-            // Each list in an order of its own (min is order-free), chosen so
-            // that at every entry position the loads spread over the
-            // shared-memory banks.  An image row of 2W bytes sits in bank
-            // group (row mod groups), groups = 128 / 2W; a 16-byte load is
-            // served a quarter warp (8 lanes, so `groups` rows) at a time, and
-            // a quarter takes as many passes as its fullest group.  Greedy:
-            // position by position, each row of a quarter takes its remaining
-            // entry whose group that quarter uses least so far.  The result
-            // rows start at a multiple of 8, so the regions' swap in a chain
-            // keeps every row's group.
-            const int groups = 128 / (2 * W);
-            std::vector<std::vector<uint32_t>> rem((size_t)SR);
-            for (int i = 0; i < SR; ++i)
-                if (r0 + (size_t)i < r1)
-                    for (uint32_t v : cv.lists[(size_t)lr[r0 + (size_t)i]]) rem[(size_t)i].push_back(img(v));
-            std::vector<uint16_t> blk((size_t)nb * SR * 8, pad);
-            for (uint32_t j = 0; j < nb * 8; ++j) {
-                std::vector<int> used((size_t)groups, 0);
-                for (int i = 0; i < SR; ++i) {
-                    if (i % groups == 0) std::fill(used.begin(), used.end(), 0);
-                    auto &li = rem[(size_t)i];
-                    if (li.empty()) continue;
-                    size_t best = 0;
-                    for (size_t t = 1; t < li.size(); ++t)
-                        if (used[li[t] % groups] < used[li[best] % groups]) best = t;
-                    ++used[li[best] % groups];
-                    blk[((size_t)(j / 8) * SR + (size_t)i) * 8 + (j % 8)] = (uint16_t)li[best];
-                    li.erase(li.begin() + (long)best);
-                }
-            }
-            C.first.insert(C.first.end(), blk.begin(), blk.begin() + (size_t)SR * 8);
-            C.ents.insert(C.ents.end(), blk.begin() + (size_t)SR * 8, blk.end());
+        // this level's rows, widest first; the one-lane rows interleaved by
+        // q mod 8 (the bank group of result row Nh + q), so the first lanes of
+        // a quarter warp store to different bank groups
+        std::vector<std::vector<int64_t>> by_lg(6);
+        for (int64_t q = 0; q < N; ++q) {
+            if (cv.level[(size_t)q] != l) continue;
+            const int lg = lanes_log2(cv.lists[(size_t)q].size());
+            if ((1 << lg) > kCircLaneMax)
+                return set_error(MP_EINVAL, "row %lld reads %zu rows: too many for one warp", (long long)q,
+                                 cv.lists[(size_t)q].size());
+            by_lg[(size_t)lg].push_back(q);
         }
-        C.level_slice0.push_back((int32_t)(C.slices.size() / 2));
+        std::vector<int64_t> seq;
+        for (int lg = 5; lg >= 1; --lg) seq.insert(seq.end(), by_lg[(size_t)lg].begin(), by_lg[(size_t)lg].end());
+        {
+            std::vector<std::vector<int64_t>> bucket(8);
+            for (int64_t q : by_lg[0]) bucket[(size_t)(q & 7)].push_back(q);
+            std::vector<size_t> at(8, 0);
+            for (size_t left = by_lg[0].size(); left > 0;)
+                for (int r = 0; r < 8; ++r)
+                    if (at[(size_t)r] < bucket[(size_t)r].size()) {
+                        seq.push_back(bucket[(size_t)r][at[(size_t)r]++]);
+                        --left;
+                    }
+        }
+        // lanes: row q takes an aligned group of 1 << lg lanes (widest first,
+        // so every group starts at a multiple of its size)
+        std::vector<int64_t> lane_row;  // -1: idle
+        for (int64_t q : seq) {
+            const int g = 1 << lanes_log2(cv.lists[(size_t)q].size());
+            for (int i = 0; i < g; ++i) lane_row.push_back(q);
+        }
+        while (lane_row.size() % 32) lane_row.push_back(-1);
+        const size_t nsl = lane_row.size() / 32;
+        for (size_t sl = 0; sl < nsl; ++sl) {
+            const int64_t *lr = &lane_row[sl * 32];
+            // Each row's list spread over its lanes and over the 8 positions
+            // of the lanes' blocks (min is order-free), chosen so that at every
+            // position the loads spread over the shared-memory banks: an image
+            // row of 16 bytes sits in bank group (row mod 8) and a 16-byte load
+            // is served a quarter warp (8 lanes) at a time, taking as many
+            // passes as its fullest group.  A row's entries are dealt to its
+            // lanes by group; then per quarter the entries are the edges of a
+            // bipartite multigraph between its 8 lanes and the 8 groups, and
+            // positions are colours: a proper edge colouring (alternating-path
+            // construction; a bipartite graph of largest degree D needs only D
+            // colours) makes every position conflict-free.  Where a group holds
+            // more than 8 of the quarter's entries, the edges coloured 8 and
+            // above go to a position free at their lane whose group count is
+            // lowest.  The result rows start at a multiple of 8, so the
+            // regions' swap in a chain keeps every row's group.
+            std::vector<std::vector<uint32_t>> rem(32);
+            for (int i = 0; i < 32; ++i) {
+                if (lr[i] < 0 || (i > 0 && lr[i - 1] == lr[i])) continue;
+                int g = 1;
+                while (i + g < 32 && lr[i + g] == lr[i]) ++g;
+                std::vector<uint32_t> li;
+                for (uint32_t v : cv.lists[(size_t)lr[i]]) li.push_back(img(v));
+                std::stable_sort(li.begin(), li.end(), [](uint32_t x, uint32_t y) { return x % 8 < y % 8; });
+                for (size_t t = 0; t < li.size(); ++t) rem[(size_t)i + t % (size_t)g].push_back(li[t]);
+            }
+            std::vector<uint16_t> blk(32 * 8, pad);
+            for (int qw = 0; qw < 4; ++qw) {
+                // edges: (lane, group) per entry; colour[e] = position
+                std::vector<int> eu, ev;
+                std::vector<uint32_t> eval;
+                for (int i = 0; i < 8; ++i)
+                    for (uint32_t v : rem[(size_t)(qw * 8 + i)]) {
+                        eu.push_back(i);
+                        ev.push_back((int)(v % 8));
+                        eval.push_back(v);
+                    }
+                const int E = (int)eu.size();
+                int D = 8;
+                {
+                    int dv[8] = {0};
+                    for (int e = 0; e < E; ++e) D = std::max(D, ++dv[ev[(size_t)e]]);
+                }
+                // at[u][c] / bt[v][c]: the edge of colour c at lane u / group v
+                std::vector<int> at((size_t)8 * D, -1), bt((size_t)8 * D, -1), col((size_t)E, -1);
+                for (int e = 0; e < E; ++e) {
+                    const int u = eu[(size_t)e], v = ev[(size_t)e];
+                    int ca = 0, cb = 0;
+                    while (at[(size_t)u * D + ca] >= 0) ++ca;  // free at u
+                    while (bt[(size_t)v * D + cb] >= 0) ++cb;  // free at v
+                    if (bt[(size_t)v * D + ca] >= 0) {
+                        // swap colours ca and cb along the path from v that
+                        // alternates ca, cb, ...; it cannot reach u
+                        std::vector<int> path;
+                        int x = v, side = 1, c = ca;
+                        while (true) {
+                            const int f = side ? bt[(size_t)x * D + c] : at[(size_t)x * D + c];
+                            if (f < 0) break;
+                            path.push_back(f);
+                            x = side ? eu[(size_t)f] : ev[(size_t)f];
+                            side ^= 1;
+                            c = c == ca ? cb : ca;
+                        }
+                        for (int f : path) {
+                            at[(size_t)eu[(size_t)f] * D + col[(size_t)f]] = -1;
+                            bt[(size_t)ev[(size_t)f] * D + col[(size_t)f]] = -1;
+                        }
+                        for (int f : path) {
+                            col[(size_t)f] = col[(size_t)f] == ca ? cb : ca;
+                            at[(size_t)eu[(size_t)f] * D + col[(size_t)f]] = f;
+                            bt[(size_t)ev[(size_t)f] * D + col[(size_t)f]] = f;
+                        }
+                    }
+                    col[(size_t)e] = ca;
+                    at[(size_t)u * D + ca] = e;
+                    bt[(size_t)v * D + ca] = e;
+                }
+                // positions 0..7 as coloured; overflow edges where their lane
+                // is free and their group least used
+                int cnt[8][8] = {};
+                std::vector<int> over;
+                for (int e = 0; e < E; ++e) {
+                    if (col[(size_t)e] < 8) {
+                        blk[(size_t)(qw * 8 + eu[(size_t)e]) * 8 + (size_t)col[(size_t)e]] = (uint16_t)eval[(size_t)e];
+                        ++cnt[col[(size_t)e]][ev[(size_t)e]];
+                    } else {
+                        over.push_back(e);
+                    }
+                }
+                for (int e : over) {
+                    const int u = eu[(size_t)e], v = ev[(size_t)e];
+                    int bestp = -1;
+                    for (int p8 = 0; p8 < 8; ++p8)
+                        if (blk[(size_t)(qw * 8 + u) * 8 + (size_t)p8] == pad &&
+                            (bestp < 0 || cnt[p8][v] < cnt[bestp][v]))
+                            bestp = p8;
+                    if (bestp < 0) return set_error(MP_EINVAL, "circuit lane with more than 8 entries");
+                    blk[(size_t)(qw * 8 + u) * 8 + (size_t)bestp] = (uint16_t)eval[(size_t)e];
+                    ++cnt[bestp][v];
+                }
+                for (int i = 0; i < 8; ++i) rem[(size_t)(qw * 8 + i)].clear();
+            }
+            for (int i = 0; i < 32; ++i) {
+                if (lr[i] >= 0 && !rem[(size_t)i].empty())
+                    return set_error(MP_EINVAL, "circuit slicing left entries of row %lld", (long long)lr[i]);
+                const int lg = lr[i] >= 0 ? lanes_log2(cv.lists[(size_t)lr[i]].size()) : 0;
+                C.info.push_back(lr[i] >= 0 ? (uint32_t)lr[i] | ((uint32_t)lg << 16) : 0xFFFFu);
+                C.lanes += lr[i] >= 0;
+            }
+            C.ents.insert(C.ents.end(), blk.begin(), blk.end());
+        }
+        C.level_slice0.push_back(C.level_slice0.back() + (int32_t)nsl);
     }
     return MP_OK;
 }
 
-int circuit_build_host(const HostCsr &csr, int W, CircuitHost *out) {
+int circuit_build_host(const HostCsr &csr, CircuitHost *out) {
     CircuitCover cv;
     MP_TRY(circuit_cover_host(csr, &cv));
-    return circuit_slice_host(cv, W, out);
+    return circuit_slice_host(cv, out);
 }
 
 // Section offsets of the circuit blob (bytes, each section a multiple of 16).
 struct CircLayout {
-    uint32_t sl = 0, ri = 0, fi = 0, en = 0, z = 0, total = 0;
+    uint32_t info = 0, ents = 0, z = 0, total = 0;
 };
 static CircLayout circuit_layout(const CircuitHost &h) {
     auto r16 = [](size_t b) { return (uint32_t)((b + 15) & ~(size_t)15); };
     CircLayout L;
-    L.sl = r16(h.level_slice0.size() * 4);
-    L.ri = L.sl + r16(h.slices.size() * 4);     // two words per slice
-    L.fi = L.ri + r16(h.rows.size() * 8);       // two words per slot
-    L.en = L.fi + r16(h.first.size() * 2);
-    L.z = L.en + r16(h.ents.size() * 2);
-    L.total = L.z + r16((size_t)h.N * 2);       // the rows' labels
+    L.info = r16(h.level_slice0.size() * 4);
+    L.ents = L.info + r16(h.info.size() * 4);
+    L.z = L.ents + r16(h.ents.size() * 2);
+    L.total = L.z + r16((size_t)h.N * 2);  // the rows' labels
     return L;
 }
 
 int circuit_smem_bytes(const CircuitHost &h, size_t *bytes) {
-    *bytes = circuit_image_bytes(h.Nh, h.W) + circuit_layout(h).total + kCircBarBytes;
+    *bytes = circuit_image_bytes(h.Nh, kCircW) + circuit_layout(h).total + kCircBarBytes;
     DeviceInfo di;
     MP_TRY(device_info(&di));
     if (*bytes + 1024 > di.smem_optin) *bytes = 0;  // a margin for the kernel's static shared memory
@@ -482,43 +584,38 @@ int circuit_upload(const CircuitHost &h, const std::vector<uint16_t> &z,
     CircuitDev &c = d->circuit;
     c.ready = false;
     if ((int64_t)diagcol.size() != h.N || (int64_t)z.size() != h.N || (int64_t)caller.size() != h.N ||
-        h.N != d->N)
+        h.N != d->N || h.W != kCircW)
         return set_error(MP_EINVAL, "circuit of the wrong size");
-    if (d->ldb % h.W) return set_error(MP_EINVAL, "circuit width does not divide the buffer");
+    if (d->ldb % kCircW) return set_error(MP_EINVAL, "circuit width does not divide the buffer");
     const CircLayout L = circuit_layout(h);
     std::vector<uint8_t> blob(L.total, 0);
     memcpy(blob.data(), h.level_slice0.data(), h.level_slice0.size() * 4);
-    memcpy(blob.data() + L.sl, h.slices.data(), h.slices.size() * 4);
-    std::vector<uint32_t> ri(h.rows.size() * 2);
-    for (size_t k = 0; k < h.rows.size(); ++k) {
-        const uint32_t q = h.rows[k];
-        if (q == 0xFFFFFFFFu) {
-            ri[2 * k] = 0xFFFFu;
-            ri[2 * k + 1] = 0xFFFFu;
-            continue;
-        }
-        const int32_t dc = diagcol[q];
-        if (z[q] > 0x7FFFu || dc >= 0xFFFF || caller[q] < 0 || caller[q] > 0xFFFF)
-            return set_error(MP_EINVAL, "circuit row fields out of range");
-        ri[2 * k] = q | ((uint32_t)z[q] << 16);
-        ri[2 * k + 1] = (dc < 0 ? 0xFFFFu : (uint32_t)dc) | ((uint32_t)caller[q] << 16);
-    }
-    memcpy(blob.data() + L.ri, ri.data(), ri.size() * 4);
-    memcpy(blob.data() + L.fi, h.first.data(), h.first.size() * 2);
-    memcpy(blob.data() + L.en, h.ents.data(), h.ents.size() * 2);
+    memcpy(blob.data() + L.info, h.info.data(), h.info.size() * 4);
+    memcpy(blob.data() + L.ents, h.ents.data(), h.ents.size() * 2);
+    for (int64_t q = 0; q < h.N; ++q)
+        if (z[(size_t)q] > 0x7FFFu) return set_error(MP_EINVAL, "circuit label out of range");
     memcpy(blob.data() + L.z, z.data(), z.size() * 2);
+    std::vector<uint16_t> drow((size_t)d->ldb, 0xFFFFu);
+    for (int64_t q = 0; q < h.N; ++q) {
+        const int32_t dc = diagcol[(size_t)q];
+        if (dc >= (int32_t)d->ldb || caller[(size_t)q] < 0)
+            return set_error(MP_EINVAL, "circuit row fields out of range");
+        if (dc >= 0) drow[(size_t)dc] = (uint16_t)q;
+    }
     MP_TRY(c.meta.alloc(L.total ? L.total : 16, s, true));
+    MP_TRY(c.drow.alloc(drow.size() * 2, s, true));
+    MP_TRY(c.caller.alloc((size_t)h.N * 4, s, true));
     MP_CUDA_TRY(cudaMemcpyAsync(c.meta.p, blob.data(), L.total, cudaMemcpyHostToDevice, s));
-    MP_CUDA_TRY(cudaStreamSynchronize(s));  // the host blob goes out of scope
-    c.W = h.W;
+    MP_CUDA_TRY(cudaMemcpyAsync(c.drow.p, drow.data(), drow.size() * 2, cudaMemcpyHostToDevice, s));
+    MP_CUDA_TRY(cudaMemcpyAsync(c.caller.p, caller.data(), (size_t)h.N * 4, cudaMemcpyHostToDevice, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors go out of scope
+    c.W = kCircW;
     c.Nh = h.Nh;
     c.levels = h.levels;
-    c.nslices = (int64_t)h.slices.size() / 2;
+    c.nslices = (int64_t)h.level_slice0.back();
     c.meta_bytes = L.total;
-    c.off_slices = L.sl;
-    c.off_rowinfo = L.ri;
-    c.off_first = L.fi;
-    c.off_ents = L.en;
+    c.off_info = L.info;
+    c.off_ents = L.ents;
     c.off_z = L.z;
     c.ready = true;
     return MP_OK;
@@ -542,28 +639,27 @@ static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uin
     a.ldb = p.ldb;
     a.meta = c.meta.as<uint8_t>();
     a.meta_bytes = c.meta_bytes;
-    a.off_slices = c.off_slices;
-    a.off_rowinfo = c.off_rowinfo;
-    a.off_first = c.off_first;
+    a.off_info = c.off_info;
     a.off_ents = c.off_ents;
     a.off_z = c.off_z;
     a.levels = c.levels;
     a.k_max = k_max;
     a.user_out = user_out;
     a.slot = slot;
+    a.caller = c.caller.as<int32_t>();
+    a.drow = c.drow.as<uint16_t>();
     a.gdiag = gdiag;
     a.extra_tx = extra_tx;
     MP_TRY(device_status_ptr(&a.status));
-    const size_t smem = circuit_image_bytes(c.Nh, c.W) + c.meta_bytes + kCircBarBytes;
+    const size_t smem = circuit_image_bytes(c.Nh, kCircW) + c.meta_bytes + kCircBarBytes;
     if (smem > di.smem_optin) return set_error(MP_EINVAL, "circuit does not fit shared memory");
-    const unsigned grid = (unsigned)(p.ldb / c.W);
+    const unsigned grid = (unsigned)(p.ldb / kCircW);
     if (grid == 0) return MP_OK;
-    auto *kern = c.W == 16 ? (chain ? circuit_step_kernel<16, true> : circuit_step_kernel<16, false>)
-                           : (chain ? circuit_step_kernel<8, true> : circuit_step_kernel<8, false>);
+    auto *kern = chain ? circuit_step_kernel<true> : circuit_step_kernel<false>;
     // the dynamic size each kernel may take, raised as larger plans come
     static std::mutex attr_mu;
-    static size_t attr_set[4][64] = {};
-    const int kind = (c.W == 16 ? 0 : 2) + (chain ? 1 : 0);
+    static size_t attr_set[2][64] = {};
+    const int kind = chain ? 1 : 0;
     {
         std::lock_guard<std::mutex> lk(attr_mu);
         if (di.device >= 64 || attr_set[kind][di.device] < smem) {

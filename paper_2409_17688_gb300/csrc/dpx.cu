@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(256) smem_peak_kernel(int64_t iters, uint32_t 
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             uint32_t x, y, z, w;
-            const uint32_t a = base + ((off + (uint32_t)j * 4096u) & (kSmemProbeBytes - 1));
+            // eight distinct 512-byte segments, 2 KB apart
+            const uint32_t a = base + ((off + (uint32_t)j * 2048u) & (kSmemProbeBytes - 1));
             asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                          : "=r"(x), "=r"(y), "=r"(z), "=r"(w)
                          : "r"(a));

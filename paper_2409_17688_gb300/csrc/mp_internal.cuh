@@ -2,8 +2,11 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
+
+#include <stdarg.h>
 
 #include <string>
 #include <vector>
@@ -29,6 +32,22 @@ const char *last_error();
         int _s = (expr);               \
         if (_s != MP_OK) return _s;    \
     } while (0)
+
+// NVTX range over a scope of host code (a no-op unless a profiler is
+// attached), named with printf-style arguments.
+struct NvtxScope {
+    explicit NvtxScope(const char *fmt, ...) {
+        char buf[96];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        nvtxRangePushA(buf);
+    }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
 
 // ------------------------------------------------------------ constants
 constexpr uint32_t kInf16 = 0x7FFFu;

@@ -173,6 +173,7 @@ struct Batch {
     TraceJob *h_jobs = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
+    nvtxRangeId_t range = 0;  // NVTX range of the batch in flight
 };
 
 }  // namespace
@@ -235,6 +236,7 @@ int64_t words_count(int n) {
 // rows and all columns is the minimum over all of them, and a trace reads
 // about half of each slot.
 void build_path(mp_server *sv, PathState *ps) {
+    NvtxScope nv("mp_server build n=%d", ps->n);
     cudaSetDevice(sv->device);
     cudaStream_t s = nullptr;
     int rc = MP_OK;
@@ -395,6 +397,13 @@ void route(mp_server *sv, const Query &q, std::vector<Query> &ready) {
 
 int launch_batch(mp_server *sv, Batch &b, std::vector<Query> &ready) {
     const int cnt = (int)std::min<size_t>(ready.size(), (size_t)sv->max_batch);
+    // the batch's lifetime, from launch to completion (ended in complete_batch)
+    {
+        char name[64];
+        snprintf(name, sizeof name, "mp_server batch %llu (%d queries)",
+                 (unsigned long long)sv->stat_batches, cnt);
+        b.range = nvtxRangeStartA(name);
+    }
     b.qs.assign(ready.begin(), ready.begin() + cnt);
     ready.erase(ready.begin(), ready.begin() + cnt);
     std::map<int, int> use;
@@ -430,6 +439,7 @@ int launch_batch(mp_server *sv, Batch &b, std::vector<Query> &ready) {
 }
 
 void complete_batch(mp_server *sv, Batch &b) {
+    nvtxRangeEnd(b.range);
     for (size_t i = 0; i < b.qs.size(); ++i) finish(sv, b.qs[i].ticket, MP_OK, b.h_out[i]);
     for (auto &u : b.uses) sv->paths[u.first]->inflight -= u.second;
     b.qs.clear();

@@ -79,7 +79,7 @@ struct PlanHost {
 // q' is a part of q's, so row q is the minimum of a few rows of the result
 // itself (its cover) and of the rows X[p] the cover leaves out.  Rows are
 // computed in levels (a row after every row of its cover), one column chunk
-// of W columns per CTA with the chunk of X, of the result and the circuit
+// of 8 columns per CTA with the chunk of X, of the result and the circuit
 // itself in shared memory.
 struct CircuitCover {
     int64_t N = 0;
@@ -89,32 +89,38 @@ struct CircuitCover {
     std::vector<int> level;
     int64_t reads = 0, cover_reads = 0;  // list entries, of them result rows
 };
+// Columns per CTA chunk: a row of the chunk is 16 bytes, one lane's load.
+constexpr int kCircW = 8;
+// Rows of one lane task: a list of up to 8 image rows; a row with a longer
+// list takes 2, 4, ... 32 lanes (an aligned group), whose partial minima a
+// warp combines by shuffles.
+constexpr int kCircLaneMax = 32;
+// A cover candidate must save more than kCircLambda row reads for each level
+// it adds to its row: fewer, fuller levels for a few more reads.
+constexpr int kCircLambda = 4;
 struct CircuitHost {
     int64_t N = 0;
     int64_t Nh = 0;  // N rounded up to 8: the result rows start at image row Nh
     int W = 0, levels = 0;
-    std::vector<int32_t> level_slice0;  // [levels + 1] first slice of each level
-    // per slice {first vector of its later entry blocks in ents, entry blocks
-    // per row}; a slice has 32 / (W / 8) rows
-    std::vector<uint32_t> slices;
-    std::vector<uint32_t> rows;         // per slice, its rows (0xFFFFFFFF: none)
-    // Entry blocks: per row, 8 row indices of the shared-memory image (X rows
-    // 0..N-1, result rows Nh..Nh+N-1, 2Nh the INF row).  first holds every
-    // slice's first block (row i of slice s at s * rows-per-slice + i), ents
-    // the later blocks, block by block and row by row.
-    std::vector<uint16_t> first, ents;
+    std::vector<int32_t> level_slice0;  // [levels + 1] first warp slice of each level
+    // per lane task, 32 per warp slice: info = row | log2(lanes of its row)
+    // << 16 (row 0xFFFF: an idle lane), and a block of 8 image-row indices
+    // (X rows 0..N-1, result rows Nh..Nh+N-1; 2Nh, the INF row, pads)
+    std::vector<uint32_t> info;
+    std::vector<uint16_t> ents;
     int64_t reads = 0, cover_reads = 0;  // row reads of the circuit, of them result rows
+    int64_t lanes = 0;                   // lane tasks that hold a row
 };
 struct CircuitDev {
     int W = 0, levels = 0;
     int64_t Nh = 0;
     int64_t nslices = 0;
     // the circuit as one blob, copied whole into shared memory: level
-    // starts, slice descriptors, per slot {row | label << 16, diagonal
-    // column | caller row << 16}, first entry blocks, later entry blocks,
-    // the rows' labels
+    // starts, lane infos, lane entry blocks, the rows' labels
     DevBuf meta;
-    uint32_t meta_bytes = 0, off_slices = 0, off_rowinfo = 0, off_first = 0, off_ents = 0, off_z = 0;
+    uint32_t meta_bytes = 0, off_info = 0, off_ents = 0, off_z = 0;
+    DevBuf drow;    // per buffer column: the internal row whose diagonal entry it holds (0xFFFF: none)
+    DevBuf caller;  // per internal row: the caller's row (int32), for writing full powers
     bool ready = false;
 };
 
@@ -164,10 +170,11 @@ int sparse_init_from_csr(const PlanDev &p, const int64_t *row_ptr, const int32_t
 int dense_to_csr(const int16_t *A, int64_t N, HostCsr *csr, DevCsr *dcsr, cudaStream_t s);
 
 // The covers and levels of a column-constant CSR (a row's arcs may not
-// repeat), and their slicing for chunks of W columns (8 or 16).
-int circuit_cover_host(const HostCsr &csr, CircuitCover *out);
-int circuit_slice_host(const CircuitCover &cv, int W, CircuitHost *out);
-int circuit_build_host(const HostCsr &csr, int W, CircuitHost *out);
+// repeat; lambda: cover reads given up per level saved), and their slicing
+// into lane tasks.
+int circuit_cover_host(const HostCsr &csr, CircuitCover *out, int lambda = kCircLambda);
+int circuit_slice_host(const CircuitCover &cv, CircuitHost *out);
+int circuit_build_host(const HostCsr &csr, CircuitHost *out);
 // Shared memory a step takes with this circuit (0: too large for the device).
 int circuit_smem_bytes(const CircuitHost &h, size_t *bytes);
 // Attach a circuit to a plan: z = the rows' labels, diagcol[q] = the buffer

@@ -30,13 +30,13 @@ def emu():
     return exe
 
 
-# (n, k, chunk width)
-CASES = [(1, 6, 16), (2, 8, 8), (3, 20, 16), (4, 12, 8), (5, 10, 16), (6, 8, 16), (7, 5, 8)]
+# (n, k)
+CASES = [(1, 6), (2, 8), (3, 20), (4, 12), (5, 10), (6, 8), (7, 5)]
 
 
-@pytest.mark.parametrize("n,k,w", CASES)
-def test_circuit_semantics_match_oracle(emu, n, k, w):
-    r = subprocess.run([emu, str(n), str(k), str(w)], capture_output=True)
+@pytest.mark.parametrize("n,k", CASES)
+def test_circuit_semantics_match_oracle(emu, n, k):
+    r = subprocess.run([emu, str(n), str(k)], capture_output=True)
     assert r.returncode == 0, (r.returncode, r.stderr.decode())
     stats = r.stderr.decode().split()
     reads, nnz = int(stats[5]), int(stats[9])
@@ -47,11 +47,11 @@ def test_circuit_semantics_match_oracle(emu, n, k, w):
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("n,k,w", [(3, 20, 8), (5, 12, 16), (6, 9, 8)])
-def test_chain_image_bookkeeping_matches_oracle(emu, n, k, w):
+@pytest.mark.parametrize("n,k", [(3, 20), (5, 12), (6, 9), (7, 4)])
+def test_chain_image_bookkeeping_matches_oracle(emu, n, k):
     """The chain kernel's shared-memory image: result rows from Nh, reads at
     (index + sh) mod 2Nh, labels added in place, regions swapped per step."""
-    r = subprocess.run([emu, str(n), str(k), str(w), "image"], capture_output=True)
+    r = subprocess.run([emu, str(n), str(k), "image"], capture_output=True)
     assert r.returncode == 0, (r.returncode, r.stderr.decode())
     N = oracle.transfer_size(n)
     got = np.frombuffer(r.stdout, dtype=np.int16).reshape(k, N, N)
@@ -62,7 +62,7 @@ def test_chain_image_bookkeeping_matches_oracle(emu, n, k, w):
 def test_circuit_reads_far_fewer_rows_than_arcs(emu):
     # the arc rule nests successor sets: at n = 7 the covers read under a
     # fifth of the arcs
-    r = subprocess.run([emu, "7", "2", "16"], capture_output=True)
+    r = subprocess.run([emu, "7", "2"], capture_output=True)
     assert r.returncode == 0, r.stderr.decode()
     stats = r.stderr.decode().split()
     reads, cover, nnz = int(stats[5]), int(stats[7]), int(stats[9])
