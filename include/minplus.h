@@ -48,6 +48,8 @@ extern "C" {
 #define MP_ETIMEOUT -6 /* a bounded device-side wait ran out                   */
 #define MP_EBUSY -7    /* a server queue is full                               */
 #define MP_ENOTREADY -8 /* a polled server ticket has not finished yet          */
+#define MP_EIO -9      /* a file cannot be read or written, or is not a checkpoint
+                          of this library's powers                            */
 
 /* ---- element types ----------------------------------------------------- */
 #define MP_I16 0 /* int16 entries in [0, 0x7FFF], INF = 0x7FFF */
@@ -174,6 +176,39 @@ int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max,
  * given n. */
 int mp_transfer_power_sequence(int n, int k_max, int16_t *powers_opt,
                                int32_t *gdiag_opt, void *stream);
+
+/* ---- checkpoint and resume ------------------------------------------------
+ * The paper keeps A and its powers on disk between its algorithms
+ * (Section 3); a checkpoint lets a long chain stop and resume.  A file holds
+ * `count` consecutive powers A^k0 .. A^(k0+count-1) of A(D_n): a 64-byte
+ * header ("MPPOWERS", format version 1, n, k0, N, count, the INF code 0x7FFF,
+ * the word order -- lexicographic, letter 1 most significant, 0 < 1 < 2 --
+ * and a 64-bit FNV-1a hash of the packed word list), then the int16 entries
+ * row-major, power after power, little-endian.
+ *
+ * mp_powers_save: writes DEVICE powers[count][N][N] (slot j = A^(k0+j)).
+ * mp_powers_info: HOST only (no CUDA call); writes {n, N, k0, count} into
+ *   the HOST array info[0..cap) after checking the header, the word-list
+ *   hash and the file size; returns the number of fields written.
+ * mp_powers_load: reads every stored power into DEVICE powers (at least
+ *   count slots of N x N; cap_slots is the buffer's capacity in slots).
+ * mp_transfer_power_sequence_from: Algorithm 2 resumed from a stored power:
+ *   given DEVICE P_k0 = A^k0 (N x N, the library's word order), computes
+ *   A^(k0+1) .. A^k_max: powers_opt slot j and gdiag_opt[j] receive A^(k0+1+j)
+ *   and its minimum diagonal entry (k_max - k0 slots each; either may be
+ *   NULL, and without powers the chain runs on the mirror-representative
+ *   columns as mp_transfer_power_sequence does).  Bit-identical to the
+ *   uninterrupted chain.  Asynchronous apart from one synchronization of the
+ *   stream when the plan is first built.
+ * save, info and load are synchronous (they wait for stream).  Errors:
+ * MP_EINVAL (arguments, a buffer too small), MP_EALIAS, MP_EIO (open, read
+ * or write failed; not a checkpoint, another format version, another word
+ * list, a size that does not match the header), MP_ENOMEM, MP_ECUDA. */
+int mp_powers_save(const char *path, int n, int k0, int64_t count, const int16_t *powers, void *stream);
+int mp_powers_info(const char *path, int64_t *info, int cap);
+int mp_powers_load(const char *path, int16_t *powers, int64_t cap_slots, void *stream);
+int mp_transfer_power_sequence_from(int n, int k0, const int16_t *P_k0, int k_max, int16_t *powers_opt,
+                                    int32_t *gdiag_opt, void *stream);
 
 /* ---- a6: gamma_2 of one cylinder --------------------------------------------
  * Theorem 2: gamma_2(P_n x C_m) = min_i (A^m)_ii, for n >= 1 and m >= 3.

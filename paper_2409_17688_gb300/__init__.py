@@ -23,7 +23,7 @@ MP_I16 = 0
 MP_U8 = 1
 
 STATUS = {0: "MP_OK", -1: "MP_EINVAL", -2: "MP_EALIAS", -3: "MP_ENOMEM", -4: "MP_ERANGE",
-          -5: "MP_ECUDA", -6: "MP_ETIMEOUT", -7: "MP_EBUSY", -8: "MP_ENOTREADY"}
+          -5: "MP_ECUDA", -6: "MP_ETIMEOUT", -7: "MP_EBUSY", -8: "MP_ENOTREADY", -9: "MP_EIO"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libminplus.so")
@@ -63,6 +63,10 @@ def lib() -> ctypes.CDLL:
         "mp_gamma2_cylinder": (I, [I, I64, P]),
         "mp_gamma2_squaring": (I, [I, I64, P]),
         "mp_inject_circuit_timeout": (I, [I, P]),
+        "mp_powers_save": (I, [ctypes.c_char_p, I, I, I64, P, P]),
+        "mp_powers_info": (I, [ctypes.c_char_p, P, I]),
+        "mp_powers_load": (I, [ctypes.c_char_p, P, I64, P]),
+        "mp_transfer_power_sequence_from": (I, [I, I, P, I, P, P, P]),
         "mp_gamma2_table": (I, [I, I, P]),
         "mp_transfer_power_sequences": (I, [P, I, I, P, P]),
         "mp_gamma2_tables": (I, [P, I, I, P]),
@@ -295,6 +299,46 @@ def mp_transfer_power_sequence(n: int, k_max: int, keep_powers: bool = True, str
     _check(lib().mp_transfer_power_sequence(int(n), int(k_max), _dev(P) if keep_powers else None,
                                             _dev(g), _stream(stream)))
     return P, g
+
+
+def mp_transfer_power_sequence_from(n: int, k0: int, P_k0, k_max: int, keep_powers: bool = True,
+                                    stream=None):
+    """Algorithm 2 resumed from P_k0 = A(D_n)^k0 (a CUDA int16 N x N tensor):
+    returns (A^(k0+1)..A^k_max or None, their diagonal minima)."""
+    import torch
+    N = mp_transfer_size(n)
+    assert P_k0.dtype == torch.int16 and tuple(P_k0.shape) == (N, N) and P_k0.is_contiguous()
+    steps = int(k_max) - int(k0)
+    P = torch.empty((steps, N, N), dtype=torch.int16, device=P_k0.device) if keep_powers else None
+    g = torch.empty(max(steps, 0), dtype=torch.int32, device=P_k0.device)
+    _check(lib().mp_transfer_power_sequence_from(int(n), int(k0), _dev(P_k0), int(k_max),
+                                                 _dev(P) if keep_powers else None, _dev(g),
+                                                 _stream(stream)))
+    return P, g
+
+
+def mp_powers_save(path: str, n: int, k0: int, powers, stream=None) -> None:
+    """Checkpoint powers[j] = A(D_n)^(k0 + j) (CUDA int16 [count, N, N]) to a file."""
+    import torch
+    assert powers.dtype == torch.int16 and powers.is_contiguous() and powers.dim() == 3
+    _check(lib().mp_powers_save(os.fsencode(path), int(n), int(k0), int(powers.shape[0]), _dev(powers),
+                                _stream(stream)))
+
+
+def mp_powers_info(path: str) -> dict:
+    """Header of a powers checkpoint: n, N, k0, count (host only)."""
+    info = np.zeros(4, dtype=np.int64)
+    _check(lib().mp_powers_info(os.fsencode(path), info.ctypes.data, 4))
+    return dict(zip(["n", "N", "k0", "count"], (int(x) for x in info)))
+
+
+def mp_powers_load(path: str, stream=None):
+    """The stored powers as a CUDA int16 [count, N, N] tensor, with the header."""
+    import torch
+    h = mp_powers_info(path)
+    P = torch.empty((h["count"], h["N"], h["N"]), dtype=torch.int16, device="cuda")
+    _check(lib().mp_powers_load(os.fsencode(path), _dev(P), int(h["count"]), _stream(stream)))
+    return P, h
 
 
 def mp_gamma2_cylinder(n: int, m: int) -> int:

@@ -17,6 +17,9 @@
 namespace mp {
 
 int dpx_peak(int variant, int64_t iters, double *ops_per_s);
+int powers_save(const char *path, int n, int k0, int64_t count, const int16_t *powers, cudaStream_t s);
+int powers_info(const char *path, int64_t *info, int cap);
+int powers_load(const char *path, int16_t *powers, int64_t cap_slots, cudaStream_t s);
 int dense_minplus_noalloc(const void *X, const void *Y, void *Z, int64_t M, int64_t N,
                           int64_t K, int64_t ldx, int64_t ldy, int64_t ldz, int dtype,
                           cudaStream_t s);
@@ -106,7 +109,38 @@ struct TransferEntry {
     bool have_narrow = false;
     int64_t narrow_cols = 0;
     CircuitHost circuit;       // reuse circuit of the rows (empty: none)
+    CircuitCover gcover;       // covers of the global circuit (levels = 0: none)
 };
+
+// Lanes per row of the global circuit for a chain of `ncols` buffer columns:
+// chunks of 8 L columns, at least about two per SM, from 32 to 256 columns.
+static int gcircuit_lanes(int64_t ncols, int sms) {
+    int W = 256;
+    while (W > 32 && ncols / W < 2 * (int64_t)sms) W /= 2;
+    return W / 8;
+}
+
+// A plan that only shapes the chain's buffers for the global circuit (no
+// gather schedule): ncols columns kept (colpos: caller column -> buffer
+// column, empty for all), rows in the internal order canon, buffer rows
+// padded to 256 columns so every chunk width divides them.
+static int gcircuit_plan(TransferEntry *e, const std::vector<int32_t> &colpos, int64_t ncols,
+                         const std::vector<int32_t> &diagcol, PlanDev *d, cudaStream_t s) {
+    DeviceInfo di;
+    MP_TRY(device_info(&di));
+    PlanHost ph;
+    ph.N = e->N;
+    ph.ldb = (ncols + 255) / 256 * 256;
+    ph.nnz = e->pcsr.row_ptr[(size_t)e->N];
+    ph.colconst = true;
+    ph.z = e->pz;
+    ph.canon = e->canon;
+    ph.colpos = colpos;
+    MP_TRY(plan_upload(ph, d, s, true));
+    GCircuitHost gh;
+    MP_TRY(gcircuit_slice_host(e->gcover, e->pz, gcircuit_lanes(ncols, di.sms), &gh));
+    return gcircuit_upload(gh, diagcol, e->canon, d, s);
+}
 
 // Steps of transfer chains run on the reuse circuit where a column chunk fits
 // shared memory; MP_SPARSE_CIRCUIT=0 in the environment keeps the gather
@@ -223,34 +257,47 @@ static int transfer_entry(int n, cudaStream_t s, TransferEntry **out) {
     if (nnz)
         MP_CUDA_TRY(cudaMemcpyAsync(e->csr.val.p, pcsr.val.data(), (size_t)nnz * 2,
                                     cudaMemcpyHostToDevice, s));
-    int cap = 0, blob_cap = 0, grid = 0;
-    MP_TRY(sparse_cap_rows(&cap, &blob_cap, &grid));
-    PlanHost ph;
-    MP_TRY(plan_build_host(pcsr, true, pz, &canon, 0, cap, blob_cap, grid, &ph));
-    ph.canon = canon;
-    MP_TRY(plan_upload(ph, &e->plan, s, true));
-    MP_CUDA_TRY(cudaStreamSynchronize(s));
     DeviceInfo di;
     MP_TRY(device_info(&di));
     const int64_t nh = (N + 7) & ~(int64_t)7;
-    // a circuit only where an 8-column image alone (2 Nh + 1 rows of 16
-    // bytes) leaves room in shared memory: the covers of larger N are not built
-    if (circuit_enabled() && 2 * nh + 1 <= 0xFFFF && (size_t)(2 * nh + 1) * 16 + 1024 < di.smem_optin) {
+    // The shared-memory circuit where an 8-column image (2 Nh + 1 rows of 16
+    // bytes) leaves room in shared memory; past that the global circuit, on
+    // covers taken from the arc rule; the gather plan where circuits are
+    // switched off.
+    const bool smem_circuit = circuit_enabled() && 2 * nh + 1 <= 0xFFFF &&
+                              (size_t)(2 * nh + 1) * 16 + 1024 < di.smem_optin;
+    const bool global_circuit = circuit_enabled() && !smem_circuit;
+    e->pcsr = std::move(pcsr);
+    e->pz = std::move(pz);
+    e->canon = std::move(canon);
+    const HostCsr &pcsr_ = e->pcsr;
+    const std::vector<uint16_t> &pz_ = e->pz;
+    const std::vector<int32_t> &canon_ = e->canon;
+    if (global_circuit) {
+        MP_TRY(circuit_cover_structured(n, e->words, canon_, pcsr_, kCircLambda, &e->gcover));
+        MP_TRY(gcircuit_plan(e.get(), {}, N, canon_, &e->plan, s));
+    } else {
+        int cap = 0, blob_cap = 0, grid = 0;
+        MP_TRY(sparse_cap_rows(&cap, &blob_cap, &grid));
+        PlanHost ph;
+        MP_TRY(plan_build_host(pcsr_, true, pz_, &canon_, 0, cap, blob_cap, grid, &ph));
+        ph.canon = canon_;
+        MP_TRY(plan_upload(ph, &e->plan, s, true));
+        MP_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (smem_circuit) {
         // rows are internal, and so are the gathered rows of pcsr
         CircuitHost ch;
-        MP_TRY(circuit_build_host(pcsr, &ch));
+        MP_TRY(circuit_build_host(pcsr_, &ch));
         size_t bytes = 0;
         MP_TRY(circuit_smem_bytes(ch, &bytes));
         if (bytes > 0 && e->plan.ldb % kCircW == 0) {
             e->circuit = std::move(ch);
-            MP_TRY(circuit_upload(e->circuit, pz, canon, canon, &e->plan, s));
+            MP_TRY(circuit_upload(e->circuit, pz_, canon_, canon_, &e->plan, s));
         }
     }
     e->h2d_bytes = masks.size() * sizeof(WordMasks) + (size_t)(N + 1) * 8 + (size_t)nnz * 2 +
                    e->plan.h2d_bytes;
-    e->pcsr = std::move(pcsr);
-    e->pz = std::move(pz);
-    e->canon = std::move(canon);
     e->d2h_bytes = (size_t)N * 8 + (size_t)nnz * 4;
     std::lock_guard<std::mutex> lk(g_mu);
     auto &slot = g_transfer[{dev, n}];
@@ -282,6 +329,13 @@ static int narrow_plan(TransferEntry *te, cudaStream_t s, const PlanDev **out) {
         // per internal row, the buffer column of its diagonal entry (or none)
         std::vector<int32_t> dcol((size_t)N);
         for (int64_t i = 0; i < N; ++i) dcol[(size_t)i] = colpos[(size_t)te->canon[(size_t)i]];
+        if (te->gcover.levels > 0) {
+            MP_TRY(gcircuit_plan(te, colpos, ncols, dcol, &te->plan_narrow, s));
+            te->narrow_cols = ncols;
+            te->have_narrow = true;
+            *out = &te->plan_narrow;
+            return MP_OK;
+        }
         int cap = 0, blob_cap = 0, grid = 0;
         MP_TRY(sparse_cap_rows(&cap, &blob_cap, &grid));
         PlanHost ph;
@@ -300,16 +354,20 @@ static int narrow_plan(TransferEntry *te, cudaStream_t s, const PlanDev **out) {
 }
 
 // The chain over a prepared sparse plan; B0 already holds P_1.
+// P_k goes to powers slot k - out_k0 and gdiag[k - out_k0] (out_k0 = 1 when
+// B0 holds A itself).
 static int run_sparse_chain(const PlanDev &plan, uint16_t *B0, uint16_t *B1, int k_max,
-                            int16_t *powers, size_t slot, int32_t *gdiag, cudaStream_t s) {
+                            int16_t *powers, size_t slot, int32_t *gdiag, cudaStream_t s,
+                            int out_k0 = 1) {
     // with a circuit the whole chain is one launch, each CTA keeping its
     // column chunk on chip from step to step
-    if (plan.circuit.ready) return circuit_chain(plan, B0, k_max, powers, slot, gdiag, s);
+    if (plan.circuit.ready) return circuit_chain(plan, B0, k_max, powers, slot, gdiag, s, out_k0);
+    if (plan.gcircuit.ready) return gcircuit_chain(plan, B0, B1, k_max, powers, slot, gdiag, s, out_k0);
     uint16_t *buf[2] = {B0, B1};
     for (int k = 2; k <= k_max; ++k) {
         MP_TRY(sparse_step(plan, buf[(k - 2) & 1], buf[(k - 1) & 1],
-                           powers ? powers + (size_t)(k - 1) * slot : nullptr,
-                           gdiag ? gdiag + (k - 1) : nullptr, s));
+                           powers ? powers + (size_t)(k - out_k0) * slot : nullptr,
+                           gdiag ? gdiag + (k - out_k0) : nullptr, s));
     }
     return MP_OK;
 }
@@ -666,6 +724,39 @@ static int gamma2_by_squaring(TransferEntry *te, int64_t m, cudaStream_t s, int3
     return MP_OK;
 }
 
+// The chain resumed from a caller's power P_k0 (caller layout): the
+// labelled buffer is built from it and the steps run as from A, with P_k
+// written to output slot k - k0 - 1.  Without powers to write, the narrow
+// plan's mirror-representative columns are taken from P_k0.
+static int transfer_chain_resume(TransferEntry *te, int k0, const int16_t *Pk0, int k_max,
+                                 int16_t *powers_opt, int32_t *gdiag_opt, cudaStream_t s) {
+    const PlanDev *pp = &te->plan;
+    DevBuf cm;
+    int64_t ncols = te->N;
+    if (!powers_opt) {
+        MP_TRY(narrow_plan(te, s, &pp));
+        std::vector<int64_t> partner;
+        MP_TRY(mirror_words(te->n, te->words, &partner));
+        std::vector<int32_t> colmap;
+        for (int64_t c = 0; c < te->N; ++c)
+            if (c <= partner[(size_t)c]) colmap.push_back((int32_t)c);
+        ncols = (int64_t)colmap.size();
+        MP_TRY(cm.alloc(colmap.size() * 4, s));
+        MP_CUDA_TRY(cudaMemcpyAsync(cm.p, colmap.data(), colmap.size() * 4, cudaMemcpyHostToDevice, s));
+        MP_CUDA_TRY(cudaStreamSynchronize(s));  // the host map goes out of scope
+    }
+    const PlanDev &plan = *pp;
+    const int steps = k_max - k0;
+    if (gdiag_opt) MP_TRY(launch_fill_i32(gdiag_opt, steps, (int32_t)kInf16, s));
+    DevBuf B;
+    MP_TRY(B.alloc(2 * (size_t)plan.N * (size_t)plan.ldb * 2, s));
+    uint16_t *B0 = B.as<uint16_t>(), *B1 = B0 + (size_t)plan.N * (size_t)plan.ldb;
+    MP_TRY(sparse_init_from_power(plan, Pk0, cm.as<int32_t>(), ncols, B0, s));
+    // B0 plays A^1 of the chain: its step k makes A^(k0 + k - 1), slot k - 2
+    return run_sparse_chain(plan, B0, B1, steps + 1, powers_opt, (size_t)plan.N * (size_t)plan.N,
+                            gdiag_opt, s, 2);
+}
+
 static int check_n(int n) {
     if (n < 1 || n > MP_MAX_PATH_ORDER)
         return set_error(MP_EINVAL, "path order n = %d outside [1, %d]", n, MP_MAX_PATH_ORDER);
@@ -703,7 +794,10 @@ int mp_transfer_circuit_info(int n, int64_t *info, int cap) {
     MP_TRY(transfer_entry(n, nullptr, &te));
     MP_CUDA_TRY(cudaStreamSynchronize(nullptr));
     const CircuitHost &c = te->circuit;
-    const int64_t v[6] = {c.W, c.levels, c.reads, c.cover_reads, te->plan.nnz, te->N};
+    const GCircuitDev &g = te->plan.gcircuit;
+    const int64_t v[6] = {g.ready ? 8 * g.L : c.W, g.ready ? g.levels : c.levels,
+                          g.ready ? g.reads : c.reads, g.ready ? g.cover_reads : c.cover_reads,
+                          te->plan.nnz, te->N};
     const int k = std::min(cap, 6);
     for (int i = 0; i < k; ++i) info[i] = v[i];
     return k;
@@ -1106,6 +1200,43 @@ int mp_tuning_get(int32_t *table) {
 int mp_dpx_peak(int variant, int64_t iters, double *ops_per_s) {
     if (!ops_per_s) return set_error(MP_EINVAL, "ops_per_s is NULL");
     return dpx_peak(variant, iters, ops_per_s);
+}
+
+int mp_powers_save(const char *path, int n, int k0, int64_t count, const int16_t *powers, void *stream) {
+    MP_TRY(check_n(n));
+    if (!path || k0 < 1 || count < 0 || (count > 0 && !powers))
+        return set_error(MP_EINVAL, "need a path, k0 >= 1, count >= 0 and the powers");
+    return powers_save(path, n, k0, count, powers, (cudaStream_t)stream);
+}
+
+int mp_powers_info(const char *path, int64_t *info, int cap) {
+    if (!path || !info || cap < 0) return set_error(MP_EINVAL, "need a path and an info array");
+    return powers_info(path, info, cap);
+}
+
+int mp_powers_load(const char *path, int16_t *powers, int64_t cap_slots, void *stream) {
+    if (!path || (cap_slots > 0 && !powers) || cap_slots < 0)
+        return set_error(MP_EINVAL, "need a path and a buffer");
+    return powers_load(path, powers, cap_slots, (cudaStream_t)stream);
+}
+
+int mp_transfer_power_sequence_from(int n, int k0, const int16_t *P_k0, int k_max, int16_t *powers_opt,
+                                    int32_t *gdiag_opt, void *stream) {
+    MP_TRY(check_n(n));
+    if (!P_k0 || k0 < 1 || k_max <= k0)
+        return set_error(MP_EINVAL, "need the power P_k0, k0 >= 1 and k_max > k0");
+    cudaStream_t s = (cudaStream_t)stream;
+    TransferEntry *te;
+    MP_TRY(transfer_entry(n, s, &te));
+    const size_t mat = (size_t)te->N * (size_t)te->N * 2;
+    const size_t steps = (size_t)(k_max - k0);
+    if (powers_opt && ranges_overlap(powers_opt, mat * steps, P_k0, mat))
+        return set_error(MP_EALIAS, "powers overlap P_k0");
+    if (gdiag_opt && (ranges_overlap(gdiag_opt, steps * 4, P_k0, mat) ||
+                      (powers_opt && ranges_overlap(gdiag_opt, steps * 4, powers_opt, mat * steps))))
+        return set_error(MP_EALIAS, "gdiag overlaps P_k0 or the powers");
+    NvtxScope nv("mp_transfer_chain_from n=%d k0=%d k_max=%d", n, k0, k_max);
+    return transfer_chain_resume(te, k0, P_k0, k_max, powers_opt, gdiag_opt, s);
 }
 
 int mp_inject_circuit_timeout(int n, void *stream) {

@@ -112,6 +112,7 @@ struct CircArgs {
     uint32_t meta_bytes, off_info, off_ents, off_z;
     int levels;
     int k_max;            // a chain: P_2 .. P_{k_max}
+    int out_k0;           // a chain: P_k goes to output slot k - out_k0
     int16_t *user_out;    // the caller's power(s), or null
     size_t slot;          // a chain: entries between the caller's powers
     const int32_t *caller;   // per internal row, the caller's row (for user_out)
@@ -250,15 +251,10 @@ __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs 
                     *reinterpret_cast<uint4 *>(a.Bout + (int64_t)q * a.ldb + c0) =
                         make_uint4(acc.x + zq, acc.y + zq, acc.z + zq, acc.w + zq);
                 }
-                if (a.user_out) {
-                    int16_t *orow = a.user_out + (kChain ? (size_t)(k - 1) * a.slot : 0) +
-                                    (int64_t)a.caller[q] * N;
-#pragma unroll
-                    for (int kk = 0; kk < 8; ++kk) {
-                        const uint32_t wv = pick_word(acc, kk >> 1);
-                        if (c0 + kk < N) orow[c0 + kk] = (int16_t)((kk & 1) ? wv >> 16 : wv & 0xFFFFu);
-                    }
-                }
+                if (a.user_out)
+                    store_row8(a.user_out + (kChain ? (size_t)(k - a.out_k0) * a.slot : 0) +
+                                   (int64_t)a.caller[q] * N + c0,
+                               acc, N - c0);
             }
             __syncthreads();  // this level's rows are read by the later levels
         }
@@ -289,7 +285,7 @@ __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs 
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
-            if (lane == 0 && v < (int32_t)kInf16) atomicMin(kChain ? a.gdiag + (k - 1) : a.gdiag, v);
+            if (lane == 0 && v < (int32_t)kInf16) atomicMin(kChain ? a.gdiag + (k - a.out_k0) : a.gdiag, v);
         }
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -399,9 +395,7 @@ int circuit_slice_host(const CircuitCover &cv, CircuitHost *out) {
     };
     C.level_slice0.push_back(0);
     for (int l = 0; l < C.levels; ++l) {
-        // this level's rows, widest first; the one-lane rows interleaved by
-        // q mod 8 (the bank group of result row Nh + q), so the first lanes of
-        // a quarter warp store to different bank groups
+        // this level's rows, widest first
         std::vector<std::vector<int64_t>> by_lg(6);
         for (int64_t q = 0; q < N; ++q) {
             if (cv.level[(size_t)q] != l) continue;
@@ -414,15 +408,58 @@ int circuit_slice_host(const CircuitCover &cv, CircuitHost *out) {
         std::vector<int64_t> seq;
         for (int lg = 5; lg >= 1; --lg) seq.insert(seq.end(), by_lg[(size_t)lg].begin(), by_lg[(size_t)lg].end());
         {
-            std::vector<std::vector<int64_t>> bucket(8);
-            for (int64_t q : by_lg[0]) bucket[(size_t)(q & 7)].push_back(q);
-            std::vector<size_t> at(8, 0);
-            for (size_t left = by_lg[0].size(); left > 0;)
-                for (int r = 0; r < 8; ++r)
-                    if (at[(size_t)r] < bucket[(size_t)r].size()) {
-                        seq.push_back(bucket[(size_t)r][at[(size_t)r]++]);
-                        --left;
+            // One-lane rows, longest list first, grouped eight at a time into
+            // quarter warps.  Under the colouring below a quarter takes about
+            // max(longest list, fullest bank group) passes per block, so a
+            // quarter starts with the longest row left and takes, from the
+            // next rows in that order, the one that keeps its fullest bank
+            // group smallest.  The quarters line up with the hardware's only
+            // after the multi-lane rows, which fill whole groups of lanes.
+            std::vector<int64_t> rows1 = by_lg[0];
+            std::stable_sort(rows1.begin(), rows1.end(), [&](int64_t x, int64_t y) {
+                return cv.lists[(size_t)x].size() > cv.lists[(size_t)y].size();
+            });
+            auto hist = [&](int64_t q, int *h) {
+                for (uint32_t v : cv.lists[(size_t)q]) ++h[img(v) % 8];
+            };
+            size_t lane_at = 0;
+            for (int64_t q : seq) lane_at += (size_t)1 << lanes_log2(cv.lists[(size_t)q].size());
+            std::vector<char> taken(rows1.size(), 0);
+            size_t first = 0;  // first row not yet taken
+            const size_t window = 48;
+            int H[8] = {0};
+            while (first < rows1.size()) {
+                if (lane_at % 8 == 0) std::fill(H, H + 8, 0);
+                size_t best = rows1.size();
+                int best_max = 1 << 30, best_sq = 1 << 30;
+                for (size_t t = first, seen = 0; t < rows1.size() && seen < window; ++t) {
+                    if (taken[t]) continue;
+                    ++seen;
+                    int h[8];
+                    std::copy(H, H + 8, h);
+                    hist(rows1[t], h);
+                    int mx = 0, sq = 0;
+                    for (int r = 0; r < 8; ++r) {
+                        mx = std::max(mx, h[r]);
+                        sq += h[r] * h[r];
                     }
+                    // the quarter's first row is the longest left
+                    if (lane_at % 8 == 0) {
+                        best = t;
+                        break;
+                    }
+                    if (mx < best_max || (mx == best_max && sq < best_sq)) {
+                        best = t;
+                        best_max = mx;
+                        best_sq = sq;
+                    }
+                }
+                taken[best] = 1;
+                hist(rows1[best], H);
+                seq.push_back(rows1[best]);
+                ++lane_at;
+                while (first < rows1.size() && taken[first]) ++first;
+            }
         }
         // lanes: row q takes an aligned group of 1 << lg lanes (widest first,
         // so every group starts at a multiple of its size)
@@ -624,7 +661,7 @@ int circuit_upload(const CircuitHost &h, const std::vector<uint16_t> &z,
 // One launch: a step (Bin -> Bout) or a whole chain from Bin = P_1.
 static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uint16_t *Bout, int k_max,
                           int16_t *user_out, size_t slot, int32_t *gdiag, cudaStream_t s,
-                          uint32_t extra_tx = 0) {
+                          uint32_t extra_tx = 0, int out_k0 = 1) {
     const CircuitDev &c = p.circuit;
     if (!c.ready) return set_error(MP_EINVAL, "plan has no circuit");
     if (p.narrow && user_out) return set_error(MP_EINVAL, "a narrow chain has no full powers to write");
@@ -644,6 +681,7 @@ static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uin
     a.off_z = c.off_z;
     a.levels = c.levels;
     a.k_max = k_max;
+    a.out_k0 = out_k0;
     a.user_out = user_out;
     a.slot = slot;
     a.caller = c.caller.as<int32_t>();
@@ -696,10 +734,10 @@ int circuit_timeout_probe(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout,
 }
 
 int circuit_chain(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *powers, size_t slot,
-                  int32_t *gdiag, cudaStream_t s) {
+                  int32_t *gdiag, cudaStream_t s, int out_k0) {
     if (k_max < 2) return MP_OK;
     if (powers && slot < (size_t)p.N * (size_t)p.N) return set_error(MP_EINVAL, "power slots too small");
-    return circuit_launch(p, true, B1, nullptr, k_max, powers, slot, gdiag, s);
+    return circuit_launch(p, true, B1, nullptr, k_max, powers, slot, gdiag, s, 0, out_k0);
 }
 
 }  // namespace mp

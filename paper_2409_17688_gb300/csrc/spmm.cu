@@ -394,7 +394,9 @@ __global__ void init_from_csr_kernel(const int64_t *__restrict__ row_ptr,
                                      int64_t N, int64_t ldb, const uint16_t *__restrict__ z,
                                      const int32_t *__restrict__ canon,
                                      const int32_t *__restrict__ colpos, uint16_t *__restrict__ B,
-                                     int16_t *__restrict__ user0, int32_t *__restrict__ g0) {
+                                     int16_t *__restrict__ user0, int32_t *__restrict__ g0,
+                                     int64_t col_base) {
+    // B holds buffer columns col_base .. col_base + ldb - 1
     const int64_t q = blockIdx.x;
     const int64_t qc = canon ? (int64_t)canon[q] : q;
     const uint16_t zq = z ? z[q] : 0;
@@ -406,10 +408,30 @@ __global__ void init_from_csr_kernel(const int64_t *__restrict__ row_ptr,
     for (int64_t e = row_ptr[q] + threadIdx.x; e < row_ptr[q + 1]; e += blockDim.x) {
         const int64_t p = col[e];
         const uint32_t v = (uint32_t)(uint16_t)val[e];
-        const int64_t j = colpos ? (int64_t)colpos[p] : p;
-        if (j >= 0) B[q * ldb + j] = (uint16_t)(v + zq);
+        const int64_t j = (colpos ? (int64_t)colpos[p] : p) - col_base;
+        if (j >= 0 && j < ldb) B[q * ldb + j] = (uint16_t)(v + zq);
         if (user0) user0[qc * N + p] = (int16_t)v;
         if (g0 && p == qc) atomicMin(g0, (int32_t)v);
+    }
+}
+
+// The labelled buffer of a caller's power: internal row q (caller row
+// canon[q]), buffer column j (caller column colmap[j], or j), INF beyond the
+// kept columns; INF entries stay INF + z like the other initialisations.
+__global__ void init_from_power_kernel(const int16_t *__restrict__ P, int64_t N, int64_t ldb,
+                                       const uint16_t *__restrict__ z, const int32_t *__restrict__ canon,
+                                       const int32_t *__restrict__ colmap, int64_t ncols,
+                                       uint16_t *__restrict__ B) {
+    const int64_t q = blockIdx.x;
+    const int64_t qc = canon ? (int64_t)canon[q] : q;
+    const uint32_t zq = z ? z[q] : 0;
+    for (int64_t j = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; j < ldb; j += (int64_t)gridDim.y * blockDim.x) {
+        uint32_t v = kInf16;
+        if (j < ncols) {
+            const int64_t c = colmap ? (int64_t)colmap[j] : j;
+            v = min((uint32_t)(uint16_t)P[qc * N + c], kInf16);
+        }
+        B[q * ldb + j] = (uint16_t)(v + zq);
     }
 }
 
@@ -474,7 +496,7 @@ int plan_upload(const PlanHost &h, PlanDev *d, cudaStream_t s, bool persistent) 
     MP_TRY(up(d->blob_off, h.blob_off.data(), h.blob_off.size() * 8));
     MP_TRY(up(d->blob, h.blob.data(), h.blob.size() * 4));
     // the gathered rows as offsets into the padded power, in 16-byte units
-    if ((double)h.N * (double)h.ldb / 8.0 >= 4294967295.0)
+    if (!h.urows.empty() && (double)h.N * (double)h.ldb / 8.0 >= 4294967295.0)
         return set_error(MP_EINVAL, "N = %lld too large for 32-bit row offsets", (long long)h.N);
     std::vector<uint32_t> uoff(h.urows.size());
     for (size_t i = 0; i < uoff.size(); ++i) uoff[i] = (uint32_t)((int64_t)h.urows[i] * (h.ldb / 8));
@@ -518,6 +540,7 @@ int sparse_cap_rows(int *cap_rows, int *blob_cap, int *grid) {
 int sparse_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,
                 int32_t *gdiag, cudaStream_t s) {
     if (p.circuit.ready) return circuit_step(p, Bin, Bout, user_out, gdiag, s);
+    if (p.gcircuit.ready) return gcircuit_step(p, Bin, Bout, user_out, gdiag, s);
     if (p.narrow && user_out) return set_error(MP_EINVAL, "a narrow chain has no full powers to write");
     DeviceInfo di;
     MP_TRY(device_info(&di));
@@ -576,7 +599,7 @@ int sparse_init_from_dense(const PlanDev &p, const int16_t *A, uint16_t *B0, int
                            int32_t *g0, cudaStream_t s) {
     if (p.permuted) return set_error(MP_EINVAL, "dense initialisation of a reordered plan");
     dim3 grid((unsigned)p.N, (unsigned)std::min<int64_t>((p.ldb + 255) / 256, 64));
-    init_from_dense_kernel<<<grid, 256, 0, s>>>(A, p.N, p.ldb, p.colconst ? p.z.as<uint16_t>() : nullptr,
+    init_from_dense_kernel<<<grid, 256, 0, s>>>(A, p.N, p.ldb, plan_labelled(p) ? p.z.as<uint16_t>() : nullptr,
                                                 B0, user0, g0);
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
@@ -589,10 +612,36 @@ int sparse_init_from_csr(const PlanDev &p, const int64_t *row_ptr, const int32_t
     dim3 grid((unsigned)p.N, 1);
     if (p.narrow && user0) return set_error(MP_EINVAL, "a narrow chain has no full powers to write");
     init_from_csr_kernel<<<grid, 256, 0, s>>>(row_ptr, col, val, p.N, p.ldb,
-                                              p.colconst ? p.z.as<uint16_t>() : nullptr,
+                                              plan_labelled(p) ? p.z.as<uint16_t>() : nullptr,
                                               p.permuted ? p.canon.as<int32_t>() : nullptr,
                                               p.narrow ? p.colpos.as<int32_t>() : nullptr, B0,
-                                              user0, g0);
+                                              user0, g0, 0);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+int sparse_init_block_from_csr(const PlanDev &p, const int64_t *row_ptr, const int32_t *col,
+                               const int16_t *val, int64_t col_base, int64_t width, uint16_t *B0,
+                               int32_t *g0, cudaStream_t s) {
+    if (col_base < 0 || width < 1 || col_base + width > p.ldb)
+        return set_error(MP_EINVAL, "column block out of the plan's buffer");
+    dim3 grid((unsigned)p.N, 1);
+    init_from_csr_kernel<<<grid, 256, 0, s>>>(row_ptr, col, val, p.N, width,
+                                              plan_labelled(p) ? p.z.as<uint16_t>() : nullptr,
+                                              p.permuted ? p.canon.as<int32_t>() : nullptr,
+                                              p.narrow ? p.colpos.as<int32_t>() : nullptr, B0, nullptr, g0,
+                                              col_base);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+int sparse_init_from_power(const PlanDev &p, const int16_t *P, const int32_t *colmap, int64_t ncols,
+                           uint16_t *B0, cudaStream_t s) {
+    if (p.N < 1) return MP_OK;
+    dim3 grid((unsigned)p.N, (unsigned)std::min<int64_t>((p.ldb + 255) / 256, 16));
+    init_from_power_kernel<<<grid, 256, 0, s>>>(P, p.N, p.ldb, plan_labelled(p) ? p.z.as<uint16_t>() : nullptr,
+                                                p.permuted ? p.canon.as<int32_t>() : nullptr, colmap, ncols,
+                                                B0);
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

@@ -7,6 +7,45 @@
 
 namespace mp {
 
+#ifdef __CUDACC__
+// The 8 values of v (two per word, low half first) to dst[0..8), or only the
+// first `valid` of them at the right edge; the caller's rows have any length,
+// so the widest store the address allows: one 16-, two 8- or four 4-byte
+// stores, or, at an odd address, a 2-byte store, three 4-byte stores of
+// re-paired halves and a 2-byte store.
+__device__ __forceinline__ void store_row8(int16_t *dst, const uint4 &v, int64_t valid) {
+    const uintptr_t ad = (uintptr_t)dst;
+    if (valid >= 8) {
+        if ((ad & 15) == 0) {
+            *reinterpret_cast<uint4 *>(dst) = v;
+        } else if ((ad & 7) == 0) {
+            reinterpret_cast<uint2 *>(dst)[0] = make_uint2(v.x, v.y);
+            reinterpret_cast<uint2 *>(dst)[1] = make_uint2(v.z, v.w);
+        } else if ((ad & 3) == 0) {
+            uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+            d[0] = v.x;
+            d[1] = v.y;
+            d[2] = v.z;
+            d[3] = v.w;
+        } else {
+            dst[0] = (int16_t)(v.x & 0xFFFFu);
+            uint32_t *d = reinterpret_cast<uint32_t *>(dst + 1);
+            d[0] = __byte_perm(v.x, v.y, 0x5432);
+            d[1] = __byte_perm(v.y, v.z, 0x5432);
+            d[2] = __byte_perm(v.z, v.w, 0x5432);
+            dst[7] = (int16_t)(v.w >> 16);
+        }
+        return;
+    }
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        const uint32_t wv = kk < 2 ? v.x : kk < 4 ? v.y : kk < 6 ? v.z : v.w;
+        if (kk < valid) dst[kk] = (int16_t)((kk & 1) ? wv >> 16 : wv & 0xFFFFu);
+    }
+}
+
+#endif
+
 // Shape of the sparse step shared by the kernel (spmm.cu) and the host plan
 // builder (spmm_plan.cu).
 constexpr int kThreads = 512;                    // 16 warps
@@ -124,6 +163,32 @@ struct CircuitDev {
     bool ready = false;
 };
 
+// The circuit of a path order whose chunk does not fit shared memory
+// (gcircuit.cu): per level, warp tasks of 32 / L rows, each row slot
+// {row, first entry / 4, entries / 4, the task's longest list / 4}; entry
+// words: the row in bits 0..23, bit 31 for a result row (a cover), bit 30
+// for padding, the label of a direct read in bits 24..27.
+struct GCircuitHost {
+    int64_t N = 0;
+    int L = 0, levels = 0;  // lanes per row: chunks of 8 L columns
+    std::vector<uint32_t> level_task0;
+    struct Slot {
+        uint32_t row, off4, len4, tmax4;
+    };
+    std::vector<Slot> tasks;
+    std::vector<uint32_t> ents;
+    int64_t reads = 0, cover_reads = 0;
+};
+struct GCircuitDev {
+    int L = 0, levels = 0;
+    int64_t reads = 0, cover_reads = 0;
+    size_t bytes = 0;
+    DevBuf level_task0, tasks, ents;
+    DevBuf drow;    // per buffer column: the internal row with its diagonal entry there (uint32)
+    DevBuf caller;  // per internal row: the caller's row (int32)
+    bool ready = false;
+};
+
 struct PlanDev {
     int64_t N = 0, ldb = 0, nnz = 0;
     int ngroups = 0, nchunks = 0, cap_rows = 0, blob_cap = 0;
@@ -136,7 +201,12 @@ struct PlanDev {
     DevBuf colpos;         // empty: all columns
     bool narrow = false;
     CircuitDev circuit;    // used for the steps when ready
+    GCircuitDev gcircuit;  // used for the steps when ready; its buffers hold unlabelled powers
 };
+
+// Whether a plan's chain buffers hold z_q + P[q] (the gather plan and the
+// shared-memory circuit) or P itself (the global circuit).
+inline bool plan_labelled(const PlanDev &p) { return p.colconst && !p.gcircuit.ready; }
 
 struct SpStepArgs {
     const uint32_t *uoff16;  // gathered rows: offsets into Bin in 16-byte units
@@ -167,7 +237,17 @@ int sparse_init_from_dense(const PlanDev &p, const int16_t *A, uint16_t *B0, int
 int sparse_init_from_csr(const PlanDev &p, const int64_t *row_ptr, const int32_t *col,
                          const int16_t *val, uint16_t *B0, int16_t *user0, int32_t *g0,
                          cudaStream_t s);
+// The same for a block of `width` buffer columns from col_base (B0 holds
+// only the block, width columns per row).
+int sparse_init_block_from_csr(const PlanDev &p, const int64_t *row_ptr, const int32_t *col,
+                               const int16_t *val, int64_t col_base, int64_t width, uint16_t *B0,
+                               int32_t *g0, cudaStream_t s);
 int dense_to_csr(const int16_t *A, int64_t N, HostCsr *csr, DevCsr *dcsr, cudaStream_t s);
+// B0 = the labelled buffer of a caller's power P (N x N, caller rows and
+// columns): internal row q holds z_q + P[canon[q]][colmap[j]] at buffer
+// column j < ncols (colmap NULL: j itself), z_q + INF beyond.
+int sparse_init_from_power(const PlanDev &p, const int16_t *P, const int32_t *colmap, int64_t ncols,
+                           uint16_t *B0, cudaStream_t s);
 
 // The covers and levels of a column-constant CSR (a row's arcs may not
 // repeat; lambda: cover reads given up per level saved), and their slicing
@@ -189,8 +269,30 @@ int circuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t 
 // one launch: each CTA keeps its column chunk in shared memory from step to
 // step.  powers (optional): P_k at powers + (k - 1) * slot in the caller's
 // layout; gdiag (optional): g[k - 1] = min diag P_k, folded by atomicMin.
+// out_k0: P_k goes to powers slot k - out_k0 and gdiag[k - out_k0] (1 for a
+// chain from A itself).
 int circuit_chain(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *powers, size_t slot,
-                  int32_t *gdiag, cudaStream_t s);
+                  int32_t *gdiag, cudaStream_t s, int out_k0 = 1);
+// The global circuit (n >= 10): covers from the arc rule (words: the
+// caller's packed words; canon: internal row -> word), its warp tasks for
+// chunks of 8 L columns (z: labels of the internal rows), and the steps.
+int circuit_cover_structured(int n, const std::vector<uint32_t> &words, const std::vector<int32_t> &canon,
+                             const HostCsr &csr, int lambda, CircuitCover *out);
+int gcircuit_slice_host(const CircuitCover &cv, const std::vector<uint16_t> &z, int L, GCircuitHost *out);
+int gcircuit_upload(const GCircuitHost &h, const std::vector<int32_t> &diagcol, const std::vector<int32_t> &caller,
+                    PlanDev *d, cudaStream_t s);
+int gcircuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out, int32_t *gdiag,
+                  cudaStream_t s);
+int gcircuit_chain(const PlanDev &p, uint16_t *B0, uint16_t *B1, int k_max, int16_t *powers, size_t slot,
+                   int32_t *gdiag, cudaStream_t s, int out_k0 = 1);
+// The same on a block of `width` plan columns from col_base (both multiples
+// of the chunk): the buffers hold only the block, width columns per row.
+int gcircuit_block_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int64_t col_base, int64_t width,
+                        int32_t *gdiag, cudaStream_t s);
+int gcircuit_block_chain(const PlanDev &p, uint16_t *B0, uint16_t *B1, int k_max, int64_t col_base,
+                         int64_t width, int32_t *gdiag, cudaStream_t s);
+int gcircuit_chunk(const PlanDev &p);  // columns per chunk (0: no global circuit)
+
 // Failure injection: one step whose bounded wait for the circuit's copies
 // runs out (MP_ETIMEOUT latched in the device status word, nothing written).
 int circuit_timeout_probe(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, cudaStream_t s);

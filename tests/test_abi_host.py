@@ -103,3 +103,51 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(mp):
     assert int(rc) == -1 and "mask bytes" in msg
     rc2, msg2 = lines[1].split(" ", 1)
     assert int(rc2) == -1 and "mask bytes" in msg2
+
+
+def _fnv1a_words(words):
+    h = 1469598103934665603
+    for w in words:
+        for b in range(4):
+            h ^= (int(w) >> (8 * b)) & 0xFF
+            h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _checkpoint_bytes(n, k0, count, words, version=1, magic=b"MPPOWERS", extra=0):
+    import struct
+    N = len(words)
+    head = struct.pack("<8sIIiiqqiIQQ", magic, version, 64, n, k0, N, count, 0x7FFF, 1,
+                       _fnv1a_words(words), 0)
+    assert len(head) == 64
+    return head + bytes(2 * count * N * N + extra)
+
+
+def test_powers_checkpoint_header_is_checked_on_the_host(mp, tmp_path):
+    """A powers checkpoint names its path order, first exponent, count, INF
+    code and word order, and carries a hash of the word list; the library
+    reads it back and refuses files that are not its checkpoints, that were
+    written with another word list or version, or whose size does not match
+    the header.  Host only: no CUDA call."""
+    n = 4
+    words = mp.mp_transfer_words(n)
+    good = tmp_path / "good.mpp"
+    good.write_bytes(_checkpoint_bytes(n, 7, 3, words))
+    assert mp.mp_powers_info(str(good)) == {"n": n, "N": len(words), "k0": 7, "count": 3}
+    bad = {
+        "magic": _checkpoint_bytes(n, 7, 3, words, magic=b"NOTPOWER"),
+        "version": _checkpoint_bytes(n, 7, 3, words, version=2),
+        "words": _checkpoint_bytes(n, 7, 3, list(words[::-1])),
+        "short": _checkpoint_bytes(n, 7, 3, words)[:-2],
+        "long": _checkpoint_bytes(n, 7, 3, words, extra=2),
+        "header": _checkpoint_bytes(n, 7, 3, words)[:40],
+    }
+    for name, blob in bad.items():
+        f = tmp_path / f"{name}.mpp"
+        f.write_bytes(blob)
+        with pytest.raises(mp.MinplusError) as e:
+            mp.mp_powers_info(str(f))
+        assert e.value.code == -9, name
+    with pytest.raises(mp.MinplusError) as e:
+        mp.mp_powers_info(str(tmp_path / "missing.mpp"))
+    assert e.value.code == -9

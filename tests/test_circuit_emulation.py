@@ -67,3 +67,45 @@ def test_circuit_reads_far_fewer_rows_than_arcs(emu):
     stats = r.stderr.decode().split()
     reads, cover, nnz = int(stats[5]), int(stats[7]), int(stats[9])
     assert cover > 0 and reads * 5 < nnz
+
+
+@pytest.fixture(scope="module")
+def gemu():
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    d = tempfile.mkdtemp(prefix="gcircemu")
+    exe = os.path.join(d, "gcircuit_emulation")
+    cmd = [nvcc, "-std=c++17", "-O2", "-gencode", "arch=compute_103a,code=sm_103a",
+           os.path.join(HERE, "gcircuit_emulation.cu"),
+           os.path.join(ROOT, "paper_2409_17688_gb300", "csrc", "transfer.cu"), "-o", exe]
+    subprocess.run(cmd, check=True, capture_output=True)
+    return exe
+
+
+@pytest.mark.parametrize("n,k,lanes", [(1, 6, 4), (2, 9, 8), (3, 20, 32), (4, 12, 4), (5, 10, 16),
+                                       (6, 8, 8), (7, 5, 4)])
+def test_global_circuit_semantics_match_oracle(gemu, n, k, lanes):
+    """The global-memory circuit (path orders past shared memory): covers
+    from the arc rule (a 0 or 1 of the source word turned into a 2 keeps the
+    successors with a 0 there), warp tasks of 32 / lanes rows, entries that
+    carry their row's label, rows in the chain's internal order; every power
+    equals the oracle's."""
+    r = subprocess.run([gemu, str(n), str(k), str(lanes)], capture_output=True)
+    assert r.returncode == 0, (r.returncode, r.stderr.decode())
+    stats = r.stderr.decode().split()
+    reads, nnz = int(stats[5]), int(stats[9])
+    assert reads <= nnz
+    N = oracle.transfer_size(n)
+    got = np.frombuffer(r.stdout, dtype=np.int16).reshape(k, N, N)
+    want, _ = oracle.power_sequence(oracle.build_transfer(n), k, threads=os.cpu_count() or 1)
+    assert np.array_equal(got, want)
+
+
+def test_global_circuit_covers_read_few_arcs(gemu):
+    # the rule's subsets alone already cover most arcs at n = 7
+    r = subprocess.run([gemu, "7", "2", "8"], capture_output=True)
+    assert r.returncode == 0, r.stderr.decode()
+    stats = r.stderr.decode().split()
+    reads, cover, nnz = int(stats[5]), int(stats[7]), int(stats[9])
+    assert cover > 0 and reads * 4 < nnz

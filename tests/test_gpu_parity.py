@@ -277,9 +277,11 @@ def test_gather_plan_steps_without_circuit(mp, torch, tmp_path):
 
 
 def test_circuit_info(mp):
-    """Path orders whose column chunk fits shared memory run on the reuse
-    circuit, which reads far fewer rows than the arcs; n = 10 does not fit.
-    At n = 3 no cover pays for the level it adds: every row is read directly."""
+    """Path orders whose column chunk fits shared memory (n <= 9) run on the
+    reuse circuit in shared memory (8-column chunks), larger ones on the
+    circuit in global memory (chunks of 32 to 256 columns); both read far
+    fewer rows than the arcs.  At n = 3 no cover pays for the level it adds:
+    every row is read directly."""
     for n in (3, 6, 9):
         c = mp.mp_transfer_circuit_info(n)
         A = oracle.build_transfer(n)
@@ -288,7 +290,9 @@ def test_circuit_info(mp):
         assert 0 <= c["cover_reads"] < c["reads"] <= c["nnz"]
         assert (c["cover_reads"] > 0) == (n > 3)
     assert mp.mp_transfer_circuit_info(9)["reads"] * 10 < mp.mp_transfer_circuit_info(9)["nnz"]
-    assert mp.mp_transfer_circuit_info(10)["width"] == 0
+    c10 = mp.mp_transfer_circuit_info(10)
+    assert c10["width"] in (32, 64, 128, 256) and c10["levels"] >= 1
+    assert 0 < c10["cover_reads"] < c10["reads"] and c10["reads"] * 10 < c10["nnz"]
 
 
 def _large_order_rows(mp, torch, n, kmax, nsample):
@@ -328,6 +332,32 @@ def test_path_order_13_sampled_rows(mp, torch):
     if 6 * N * N * 2 * 1.05 > free:
         pytest.skip("not enough device memory for four powers and the chain buffers")
     _large_order_rows(mp, torch, 13, 4, 4)
+
+
+@pytest.mark.parametrize("n,kmax,cut", [(6, 40, 17), (9, 30, 12), (10, 12, 5)])
+def test_checkpoint_and_resume(mp, torch, tmp_path, n, kmax, cut):
+    """Checkpoint and resume (the paper keeps its powers on disk): powers
+    A^(cut-2)..A^cut saved, read back bit for bit, and the chain resumed from
+    the last of them equals the uninterrupted chain, powers and diagonal
+    minima, on the reuse circuit (n = 6, 9) and the gather plan (n = 10), in
+    full and mirror-column form; the diagonals equal the oracle's."""
+    P, g = mp.mp_transfer_power_sequence(n, kmax)
+    torch.cuda.synchronize()
+    path = str(tmp_path / f"powers{n}.mpp")
+    mp.mp_powers_save(path, n, cut - 2, P[cut - 3:cut])
+    assert mp.mp_powers_info(path) == {"n": n, "N": P.shape[1], "k0": cut - 2, "count": 3}
+    L, h = mp.mp_powers_load(path)
+    torch.cuda.synchronize()
+    assert torch.equal(L, P[cut - 3:cut])
+    R, gr = mp.mp_transfer_power_sequence_from(n, cut, L[-1].contiguous(), kmax)
+    _, gn = mp.mp_transfer_power_sequence_from(n, cut, L[-1].contiguous(), kmax, keep_powers=False)
+    torch.cuda.synchronize()
+    assert torch.equal(R, P[cut:]), n
+    assert torch.equal(gr, g[cut:]) and torch.equal(gn, g[cut:]), n
+    if n <= 9:
+        assert np.array_equal(host(gn), oracle_gdiag(n, kmax)[cut:]), n
+    del P, R, L
+    torch.cuda.empty_cache()
 
 
 def test_power_sequence_generic_matches_transfer(mp, torch):
