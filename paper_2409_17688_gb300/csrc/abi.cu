@@ -482,6 +482,41 @@ static int transfer_recurrence(int n, int K, Recurrence *out, cudaStream_t s) {
 
 // The transfer chain with slot k-1 of the powers at powers + (k-1)*slot
 // (slot >= N*N elements; the caller may pad slots for alignment).
+// Columns per block for chains over column blocks: the largest multiple of
+// the circuit's chunk whose `slabs` buffers of N rows take at most `frac` of
+// the free device memory (at most the whole buffer).
+static int block_width(const PlanDev &plan, int slabs, double frac, cudaStream_t s, int64_t *wb) {
+    const int64_t W = gcircuit_chunk(plan);
+    size_t free_b = 0;
+    MP_TRY(device_free_bytes(s, &free_b));
+    const double per_col = (double)slabs * (double)plan.N * 2.0;
+    int64_t w = (int64_t)(frac * (double)free_b / per_col) / W * W;
+    if (w < W) return set_error(MP_ENOMEM, "%d buffers of one %lld-column chunk do not fit", slabs, (long long)W);
+    *wb = std::min(w, plan.ldb);
+    return MP_OK;
+}
+
+// The chain without powers, one block of columns at a time where the two
+// chain buffers of the whole (mirror-column) width do not fit: column
+// chunks of a power depend only on the same chunks of the previous power,
+// so each block runs the whole chain from its part of P_1, and the diagonal
+// minima of the blocks fold into gdiag.
+static int transfer_chain_blocked(TransferEntry *te, const PlanDev &plan, int k_max, int32_t *gdiag,
+                                  cudaStream_t s) {
+    int64_t wb = 0;
+    MP_TRY(block_width(plan, 2, 0.8, s, &wb));
+    DevBuf B;
+    MP_TRY(B.alloc(2 * (size_t)plan.N * (size_t)wb * 2, s));
+    uint16_t *B0 = B.as<uint16_t>(), *B1 = B0 + (size_t)plan.N * (size_t)wb;
+    for (int64_t cb = 0; cb < plan.ldb; cb += wb) {
+        const int64_t w = std::min(wb, plan.ldb - cb);
+        MP_TRY(sparse_init_block_from_csr(plan, te->csr.row_ptr.as<int64_t>(), te->csr.col.as<int32_t>(),
+                                          te->csr.val.as<int16_t>(), cb, w, B0, gdiag, s));
+        MP_TRY(gcircuit_block_chain(plan, B0, B1, k_max, cb, w, gdiag, s));
+    }
+    return MP_OK;
+}
+
 static int transfer_chain_direct(TransferEntry *te, int k_max, int16_t *powers_opt, size_t slot,
                                  int32_t *gdiag_opt, cudaStream_t s) {
     // without powers to write, the narrow chain gives the same diagonals
@@ -489,6 +524,14 @@ static int transfer_chain_direct(TransferEntry *te, int k_max, int16_t *powers_o
     if (!powers_opt) MP_TRY(narrow_plan(te, s, &pp));
     const PlanDev &plan = *pp;
     if (gdiag_opt) MP_TRY(launch_fill_i32(gdiag_opt, k_max, (int32_t)kInf16, s));
+    // large chains check the free memory first (a synchronisation, so a
+    // graph capture of such a chain fails and it runs directly instead)
+    const double need = 2.0 * (double)plan.N * (double)plan.ldb * 2.0;
+    if (!powers_opt && plan.gcircuit.ready && need > (double)(1u << 30)) {
+        size_t free_b = 0;
+        MP_TRY(device_free_bytes(s, &free_b));
+        if (need > 0.8 * (double)free_b) return transfer_chain_blocked(te, plan, k_max, gdiag_opt, s);
+    }
     DevBuf B;
     MP_TRY(B.alloc(2 * (size_t)plan.N * (size_t)plan.ldb * 2, s));
     uint16_t *B0 = B.as<uint16_t>(), *B1 = B0 + (size_t)plan.N * (size_t)plan.ldb;
@@ -607,6 +650,60 @@ int transfer_powers_strided(int n, int k_max, int16_t *powers_opt, size_t slot,
 // first).  The first constant difference, at k = n0 + a, gives the least
 // n0 of Algorithm 4 and the period a with its constant b (Lemma 1 carries
 // it to every later power).
+// The streaming detection over column blocks, for path orders whose ring
+// of R powers does not fit at full width: every block runs the chain to
+// k_limit with its own ring, and for each k and a < R the statistics of
+// P_k - P_{k-a} (minimum, maximum, INF in one only, finite in both) are
+// folded over the blocks; the first k, smallest a, whose difference is
+// constant over all columns gives n0 = k - a as in the unblocked form.
+static int transfer_recurrence_blocked(TransferEntry *te, const PlanDev &plan, int k_limit, int R,
+                                       Recurrence *out, cudaStream_t s) {
+    int64_t wb = 0;
+    MP_TRY(block_width(plan, R, 0.8, s, &wb));
+    DevBuf ring, g, st;
+    MP_TRY(ring.alloc((size_t)R * (size_t)plan.N * (size_t)wb * 2, s));
+    MP_TRY(g.alloc(sizeof(int32_t) * (size_t)k_limit, s));
+    MP_TRY(st.alloc(sizeof(int32_t) * 4 * (size_t)(k_limit + 1) * (size_t)R, s));
+    const size_t slab = (size_t)plan.N * (size_t)wb;
+    auto slot = [&](int k) { return ring.as<uint16_t>() + (size_t)((k - 1) % R) * slab; };
+    auto stat = [&](int k, int a) { return st.as<int32_t>() + 4 * ((size_t)k * (size_t)R + (size_t)a); };
+    MP_TRY(launch_fill_i32(g.as<int32_t>(), k_limit, (int32_t)kInf16, s));
+    MP_TRY(launch_diff_init(st.as<int32_t>(), (int64_t)(k_limit + 1) * R, s));
+    for (int64_t cb = 0; cb < plan.ldb; cb += wb) {
+        const int64_t w = std::min(wb, plan.ldb - cb);
+        MP_TRY(sparse_init_block_from_csr(plan, te->csr.row_ptr.as<int64_t>(), te->csr.col.as<int32_t>(),
+                                          te->csr.val.as<int16_t>(), cb, w, slot(1), g.as<int32_t>(), s));
+        for (int k = 2; k <= k_limit; ++k) {
+            MP_TRY(gcircuit_block_step(plan, slot(k - 1), slot(k), cb, w, g.as<int32_t>() + (k - 1), s));
+            for (int a = 1; a < R && a < k; ++a)
+                MP_TRY(launch_diff_const(reinterpret_cast<const int16_t *>(slot(k)),
+                                         reinterpret_cast<const int16_t *>(slot(k - a)), (int64_t)(plan.N * w),
+                                         stat(k, a), s, false));
+        }
+    }
+    std::vector<int32_t> h((size_t)4 * (size_t)(k_limit + 1) * (size_t)R);
+    MP_CUDA_TRY(cudaMemcpyAsync(h.data(), st.p, h.size() * 4, cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> gh((size_t)k_limit);
+    MP_CUDA_TRY(cudaMemcpyAsync(gh.data(), g.p, gh.size() * 4, cudaMemcpyDeviceToHost, s));
+    MP_CUDA_TRY(cudaStreamSynchronize(s));
+    Recurrence r;
+    for (int k = 2; k <= k_limit && r.a == 0; ++k)
+        for (int a = 1; a < R && a < k; ++a) {
+            const int32_t *v = &h[4 * ((size_t)k * (size_t)R + (size_t)a)];
+            if (v[2] == 0 && v[3] == 1 && v[0] == v[1]) {
+                r.a = a;
+                r.b = v[0];
+                r.n0 = k - a;
+                r.r0 = k - a;
+                r.K = k;
+                r.gdiag.assign(gh.begin(), gh.begin() + k);
+                break;
+            }
+        }
+    *out = r;
+    return MP_OK;
+}
+
 static int transfer_recurrence_ring(int n, int k_limit, int R, Recurrence *out, cudaStream_t s) {
     NvtxScope nv("mp_transfer_recurrence_stream n=%d ring=%d", n, R);
     // The ring is the chain itself, narrow: slot (k - 1) % R holds the k-th
@@ -619,14 +716,21 @@ static int transfer_recurrence_ring(int n, int k_limit, int R, Recurrence *out, 
     const double cols_est = 0.5625 * (double)N + 64.0;  // a little over N / 2
     size_t free_b = 0;
     MP_TRY(device_free_bytes(s, &free_b));
-    if ((double)N * cols_est * 2.0 * R > 0.9 * (double)free_b)
-        return set_error(MP_ENOMEM, "a ring of %d powers of N = %lld does not fit the free memory", R,
-                         (long long)N);
+    const bool fits = (double)N * cols_est * 2.0 * R <= 0.9 * (double)free_b;
     TransferEntry *te;
     MP_TRY(transfer_entry(n, s, &te));
     const PlanDev *pp = nullptr;
     MP_TRY(narrow_plan(te, s, &pp));
     const PlanDev &plan = *pp;
+    if (plan.gcircuit.ready) {
+        // the global circuit runs the ring over column blocks where it does not fit
+        MP_TRY(device_free_bytes(s, &free_b));
+        if ((double)plan.N * (double)plan.ldb * 2.0 * R > 0.8 * (double)free_b)
+            return transfer_recurrence_blocked(te, plan, k_limit, R, out, s);
+    } else if (!fits) {
+        return set_error(MP_ENOMEM, "a ring of %d powers of N = %lld does not fit the free memory", R,
+                         (long long)N);
+    }
     const size_t slab = (size_t)plan.N * (size_t)plan.ldb;
     DevBuf ring, g, d;
     MP_TRY(ring.alloc(slab * 2 * (size_t)R, s));

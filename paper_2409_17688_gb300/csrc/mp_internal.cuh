@@ -142,8 +142,11 @@ int launch_transfer_csr_fill(int n, const WordMasks *d_masks, int64_t N, const i
 int launch_fill_i32(int32_t *p, int64_t count, int32_t v, cudaStream_t s);
 int launch_diag_min(const int16_t *P, int64_t N, int64_t ld, int32_t *out, bool init,
                     cudaStream_t s);
+// init false: fold into out[0..4) as it stands (statistics over several
+// blocks of columns); launch_diff_init resets count4 groups of four.
 int launch_diff_const(const int16_t *X, const int16_t *Y, int64_t count, int32_t *out,
-                      cudaStream_t s);
+                      cudaStream_t s, bool init = true);
+int launch_diff_init(int32_t *out, int64_t count4, cudaStream_t s);
 int launch_min_trace(const int16_t *X, const int16_t *Y, int64_t N, int64_t ldx,
                      int64_t ldy, int32_t *out, cudaStream_t s);
 // The transfer chain of A(D_n) with a caller-chosen slot stride (elements).

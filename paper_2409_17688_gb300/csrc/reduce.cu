@@ -73,6 +73,15 @@ __global__ void diff_init_kernel(int32_t *out) {
     out[3] = 0;
 }
 
+__global__ void diff_init_many_kernel(int32_t *out, int64_t count4) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count4) return;
+    out[4 * i] = 0x7FFFFFFF;
+    out[4 * i + 1] = (int32_t)0x80000000;
+    out[4 * i + 2] = 0;
+    out[4 * i + 3] = 0;
+}
+
 __global__ void diff_const_kernel(const int16_t *__restrict__ X, const int16_t *__restrict__ Y,
                                   int64_t count, int32_t *out) {
     int32_t lo = 0x7FFFFFFF, hi = (int32_t)0x80000000, mism = 0, fin = 0;
@@ -149,15 +158,24 @@ int launch_diag_min(const int16_t *P, int64_t N, int64_t ld, int32_t *out, bool 
 }
 
 int launch_diff_const(const int16_t *X, const int16_t *Y, int64_t count, int32_t *out,
-                      cudaStream_t s) {
-    diff_init_kernel<<<1, 1, 0, s>>>(out);
-    MP_CUDA_TRY(cudaGetLastError());
+                      cudaStream_t s, bool init) {
+    if (init) {
+        diff_init_kernel<<<1, 1, 0, s>>>(out);
+        MP_CUDA_TRY(cudaGetLastError());
+    }
     if (count <= 0) return MP_OK;
     DeviceInfo di;
     MP_TRY(device_info(&di));
     int64_t blocks = (count / 2 + 255) / 256;
     blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)di.sms * 8));
     diff_const_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, Y, count, out);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+int launch_diff_init(int32_t *out, int64_t count4, cudaStream_t s) {
+    if (count4 <= 0) return MP_OK;
+    diff_init_many_kernel<<<(unsigned)((count4 + 255) / 256), 256, 0, s>>>(out, count4);
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

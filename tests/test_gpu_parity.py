@@ -539,6 +539,50 @@ def test_recurrence_stream_twice_with_large_ring(mp, torch):
         assert (n0, a, b) == (26, 3, 14)
 
 
+def test_column_blocks_match_the_whole_width(mp, torch):
+    """Chains whose buffers do not fit run over blocks of columns (column
+    chunks of a power depend only on the same chunks of the previous power).
+    With most of the device memory held elsewhere, the gamma_2 table and the
+    ring detection of n = 12 run in blocks and give the whole-width table and
+    Table 4's (n0, a, b) = (26, 3, 14)."""
+    want = mp.mp_gamma2_table(12, 40)
+    assert mp.mp_transfer_recurrence_stream(12, 40, 8)[:3] == (26, 3, 14)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < 12e9:
+        pytest.skip("not enough device memory to set aside")
+    hold = torch.empty(int(free - 4e9), dtype=torch.uint8, device="cuda")
+    try:
+        got = mp.mp_gamma2_table(12, 40)
+        rec = mp.mp_transfer_recurrence_stream(12, 40, 8)
+    finally:
+        del hold
+        torch.cuda.empty_cache()
+    assert np.array_equal(got, want)
+    assert rec[:3] == (26, 3, 14) and rec[3] == 29
+
+
+def test_path_order_14(mp, torch):
+    """Path order 14 (N = 327006, about 4.7e8 arcs; the two mirror-column
+    chain buffers alone would take 214 GB), beyond the paper's reach: the
+    chain and the ring detection run over column blocks.  Pins are the
+    paper's statements: the C_5 formula 2n + 2 = 30 for even n (Section 4),
+    the conjecture gamma_2 = (n + 2) m / 3 = 16 m / 3 for m = 0 mod 3
+    (Section 5) and so the period's slope b / a = 16 / 3; Theorem 3 carries
+    them to m = 3000.  Skipped only where the device has too little memory."""
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < 120e9:
+        pytest.skip("not enough free device memory for path order 14")
+    n0, a, b, k = mp.mp_transfer_recurrence_stream(14, 48, 4)
+    assert a > 0 and k == n0 + a
+    assert 3 * b == 16 * a
+    assert mp.mp_gamma2_cylinder(14, 5) == 30
+    for m in range(3, 3001, 3):
+        assert mp.mp_gamma2_cylinder(14, m) == 16 * m // 3, m
+
+
 def test_path_order_13_conjecture(mp, torch):
     """Path order 13 (N = 131562, 34.6 GB per power), which the paper could
     not fit: the ring-buffer detector keeps four powers and the two chain
@@ -736,7 +780,8 @@ def test_allocation_failures_are_reported(mp, torch):
         mp.mp_transfer_recurrence(12, 200)  # 200 powers of 5.6 GB
     assert e.value.code in (-3, -4)
     with pytest.raises(mp.MinplusError) as e:
-        mp.mp_transfer_recurrence_stream(12, 60, int(free // (52929 * 52929)) + 8)
+        # more ring slots than even one column chunk per slot can hold
+        mp.mp_transfer_recurrence_stream(12, 60, int(free // (52929 * 128)) + 8)
     assert e.value.code == -3
     # a server whose budget cannot hold the path order refuses it
     srv = mp.Server(hbm_budget=1 << 20, max_batch=8, max_m=100)
