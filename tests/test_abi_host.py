@@ -151,3 +151,15 @@ def test_powers_checkpoint_header_is_checked_on_the_host(mp, tmp_path):
     with pytest.raises(mp.MinplusError) as e:
         mp.mp_powers_info(str(tmp_path / "missing.mpp"))
     assert e.value.code == -9
+
+
+def test_command_line_lists_its_commands():
+    """The package's command line (python -m paper_2409_17688_gb300) parses
+    without a GPU and names its commands."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-m", "paper_2409_17688_gb300", "--help"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    for cmd in ("gamma2", "table", "recurrence", "circuit", "product", "save", "autotune"):
+        assert cmd in r.stdout

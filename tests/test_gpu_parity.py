@@ -804,6 +804,21 @@ def test_dpx_peak_positive(mp):
         assert mp.mp_dpx_peak(v, 4096) > 1e12
 
 
+def test_command_line(mp, capsys, tmp_path):
+    """The command line answers through the library: gamma_2(P_3 x C_12) = 16
+    (ceil(4m/3)) by the chain and by repeated squaring, and a checkpoint it
+    writes reads back."""
+    import json
+    from paper_2409_17688_gb300.__main__ import main
+    for extra in ([], ["--squaring"]):
+        assert main(["gamma2", "--n", "3", "--m", "12", *extra]) == 0
+        assert json.loads(capsys.readouterr().out)["gamma2"] == 16
+    path = str(tmp_path / "p.mpp")
+    assert main(["save", "--n", "4", "--kmax", "5", "--out", path]) == 0
+    out = json.loads(capsys.readouterr().out)
+    assert (out["n"], out["k0"], out["count"]) == (4, 1, 5)
+
+
 def test_device_status_clean(mp):
     assert mp.mp_device_status() == 0
 
