@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-dense", action="store_true", help="skip the N=8192 dense products")
     ap.add_argument("--no-batched", action="store_true", help="skip the 96-product batch")
     ap.add_argument("--no-serving", action="store_true", help="skip the served query stream")
-    ap.add_argument("--profile", choices=["chain9", "chain8", "gemm8192", "gemm8192u8"],
+    ap.add_argument("--profile", choices=["chain9", "chain8", "gchain11", "gemm8192", "gemm8192u8"],
                     help="run one small case for an ncu capture and exit")
     return ap.parse_args()
 
@@ -770,6 +770,11 @@ def run_profile(what: str):
         n = int(what[5:])
         for _ in range(3):
             mp.mp_transfer_power_sequence(n, 12, keep_powers=False)
+    elif what.startswith("gchain"):
+        # the circuit in global memory (n >= 10): a short mirror-column chain
+        n = int(what[6:])
+        for _ in range(3):
+            mp.mp_transfer_power_sequence(n, 6, keep_powers=False)
     else:
         dt = np.uint8 if what.endswith("u8") else np.int16
         X = torch.from_numpy(synth.block_inf_matrix(8192, 8192, 1, dt, inf_frac=0.4)).cuda()
