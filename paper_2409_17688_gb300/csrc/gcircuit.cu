@@ -20,7 +20,8 @@
 // chain's two global buffers (L2 holds them where they fit), and every step
 // computes the levels in order with a block barrier between them.  A warp
 // task is 32 / L rows of one level, longest lists first; its lanes walk
-// their row's list four entries at a time.  The buffers hold the powers
+// their row's list eight entries at a time, the eight row loads issued
+// before any is folded (the kernel is bound by the latency of L2 and HBM).  The buffers hold the powers
 // themselves, not labelled: an entry of a direct read carries its label and
 // is folded with a fused add-min (__viaddmin_u16x2), a cover entry with a
 // plain minimum.  After the levels the chunk's diagonal entries (at most W
@@ -60,14 +61,21 @@ struct GArgs {
     int32_t *gdiag;
 };
 
-template <int L>
-__device__ __forceinline__ void gfold(uint4 &acc, uint32_t e, const uint16_t *X, const uint16_t *R,
-                                      int64_t ldb, int64_t col) {
-    if (e & kGPad) return;
+// The 16 bytes an entry names (all ones for padding: above every value, so
+// it never lowers a minimum) and the label to add.
+__device__ __forceinline__ void gload(uint32_t e, const uint16_t *X, const uint16_t *R, int64_t ldb,
+                                      int64_t col, uint4 &v, uint32_t &zz) {
+    if (e & kGPad) {
+        v = make_uint4(~0u, ~0u, ~0u, ~0u);
+        zz = 0;
+        return;
+    }
     const bool cov = (e & kGCover) != 0;
     const int64_t row = (int64_t)(e & kGRow);
-    const uint4 v = *reinterpret_cast<const uint4 *>((cov ? R : X) + row * ldb + col);
-    const uint32_t zz = cov ? 0u : ((e >> 24) & 0xFu) * 0x10001u;
+    v = *reinterpret_cast<const uint4 *>((cov ? R : X) + row * ldb + col);
+    zz = cov ? 0u : ((e >> 24) & 0xFu) * 0x10001u;
+}
+__device__ __forceinline__ void gmin(uint4 &acc, const uint4 &v, uint32_t zz) {
     acc.x = __viaddmin_u16x2(v.x, zz, acc.x);
     acc.y = __viaddmin_u16x2(v.y, zz, acc.y);
     acc.z = __viaddmin_u16x2(v.z, zz, acc.z);
@@ -98,14 +106,19 @@ __global__ void __launch_bounds__(kGThreads, 2) gcircuit_kernel(GArgs a) {
             for (int t = (int)a.level_task0[l] + warp; t < t1; t += kGWarps) {
                 const uint4 d = a.tasks[(size_t)t * RPT + slotr];  // row, off4, len4, task max len4
                 uint4 acc = make_uint4(kInf16x2, kInf16x2, kInf16x2, kInf16x2);
-                for (uint32_t e4 = 0; e4 < d.w; ++e4) {
-                    if (e4 < d.z) {
-                        const uint4 e = a.ents[d.y + e4];
-                        gfold<L>(acc, e.x, X, R, ldb, col);
-                        gfold<L>(acc, e.y, X, R, ldb, col);
-                        gfold<L>(acc, e.z, X, R, ldb, col);
-                        gfold<L>(acc, e.w, X, R, ldb, col);
-                    }
+                // eight entries (two loads of four) per pass, so eight row
+                // loads are in flight per lane
+                const uint4 pad4 = make_uint4(kGPad, kGPad, kGPad, kGPad);
+                for (uint32_t e4 = 0; e4 < d.w; e4 += 2) {
+                    const uint4 ea = e4 < d.z ? a.ents[d.y + e4] : pad4;
+                    const uint4 eb = e4 + 1 < d.z ? a.ents[d.y + e4 + 1] : pad4;
+                    const uint32_t e[8] = {ea.x, ea.y, ea.z, ea.w, eb.x, eb.y, eb.z, eb.w};
+                    uint4 v[8];
+                    uint32_t zz[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) gload(e[j], X, R, ldb, col, v[j], zz[j]);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) gmin(acc, v[j], zz[j]);
                 }
                 if (d.x == 0xFFFFFFFFu) continue;
                 *reinterpret_cast<uint4 *>(R + (int64_t)d.x * ldb + col) = acc;
