@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-dense", action="store_true", help="skip the N=8192 dense products")
     ap.add_argument("--no-batched", action="store_true", help="skip the 96-product batch")
     ap.add_argument("--no-serving", action="store_true", help="skip the served query stream")
-    ap.add_argument("--profile", choices=["chain9", "chain8", "gchain11", "gemm8192", "gemm8192u8"],
+    ap.add_argument("--profile", choices=["chains", "chain9", "chain8", "gchain11", "gemm8192", "gemm8192u8"],
                     help="run one small case for an ncu capture and exit")
     return ap.parse_args()
 
@@ -239,7 +239,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step(gamma_host):
-        # the four chains side by side (library streams forked from this one)
+        # the four chains in one launch of the circuit kernel (longest chain first)
         mp._check(lib.mp_transfer_power_sequences(ns_arr, len(PATH_ORDERS), K_MAX,
                                                   ctypes.c_void_p(g_all.data_ptr()), sptr))
         gh = g_all.to("cpu", non_blocking=False)
@@ -312,50 +312,75 @@ def run_ours(args):
             best = t if best is None else min(best, t)
         return best
 
-    # The dominant kernel: the n = 9 chain runs as one launch of the circuit
-    # chain kernel (each CTA keeps its 8-column chunk on chip for every
-    # step); its duration is the chain to k = 201 minus the chain to k = 1
-    # (the same initialisation, no chain launch).
-    circ = mp.mp_transfer_circuit_info(9)
-    t_hi, t_lo = chain_ms(9, 201), chain_ms(9, 1)
+    # The dominant kernel: the four chains run as one launch of the circuit
+    # kernel (circuit_multi_kernel; each CTA keeps its 8-column chunk of its
+    # chain on chip for every step, the n = 9 chain's CTAs first).  Its
+    # duration over 199 steps is the side-by-side call to k = 201 minus the
+    # call to k = 2 (the same initialisation and a one-step launch).
+    circs = {n: mp.mp_transfer_circuit_info(n) for n in PATH_ORDERS}
+    g_hi = torch.empty((len(PATH_ORDERS), K_MAX + 1), dtype=torch.int32, device=dev)
+
+    def chains_ms(kmax, reps=5):
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mp._check(lib.mp_transfer_power_sequences(ns_arr, len(PATH_ORDERS), kmax,
+                                                      ctypes.c_void_p(g_hi.data_ptr()), sptr))
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+        return best
+
+    chains_ms(201), chains_ms(2)
+    t_hi, t_lo = chains_ms(201), chains_ms(2)
+    # the n = 9 chain alone (its own launch of the circuit kernel), per step
+    n9_alone_us = (chain_ms(9, 201) - chain_ms(9, 1)) / K_MAX * 1e3
     launch_ms = t_hi - t_lo
-    steps9 = 200
-    step_ms = launch_ms / steps9
-    achieved = cols[9] * nnz[9] / (step_ms * 1e-3)  # product terms / s (context only)
+    steps = K_MAX - 1
+    reads_cols = sum(circs[n]["reads"] * cols[n] for n in PATH_ORDERS)
+    terms_cols = sum(nnz[n] * cols[n] for n in PATH_ORDERS)
     props = torch.cuda.get_device_properties(dev)
     roofline = None
-    if circ.get("width", 0) > 0:
+    if all(circs[n].get("width", 0) > 0 for n in PATH_ORDERS):
         # algorithmic shared-memory bytes: every circuit row read, 2 bytes per column
-        smem_bytes = circ["reads"] * 2 * cols[9] * steps9
+        smem_bytes = reads_cols * 2 * steps
+        chunks = sum(-(-cols[n] // 64) * 64 // circs[n]["width"] for n in PATH_ORDERS)
         roofline = {"bound": "smem",
-                    "kernel": f"circuit_step_kernel<{circ['width']}, chain> (n=9, N={Ns[9]}, {cols[9]} "
-                              f"columns, {steps9} steps in one launch)",
+                    "kernel": f"circuit_multi_kernel: the chains n = {', '.join(str(n) for n in PATH_ORDERS)} "
+                              f"in one launch ({chunks} chunks of 8 columns, one CTA for each of the n = 9 "
+                              f"chain's, which come first, and a few chunks for each CTA of the others; {steps} "
+                              "steps; more chunks than SMs, so the circuits are read from L2 and two CTAs "
+                              "share an SM)",
                     "achieved": round(smem_bytes / (launch_ms * 1e-3) / 1e9, 1),
                     "unit": "GB/s",
                     "algorithmic_bytes": smem_bytes,
-                    "algorithmic_bytes_rule": f"circuit row reads per column ({circ['reads']}) x 2 bytes x "
-                                              f"{cols[9]} columns x {steps9} steps",
-                    "traffic": profiled_traffic("profiles/k2_circuit_chain_n9.md",
+                    "algorithmic_bytes_rule": "sum over the four chains of circuit row reads per column x "
+                                              f"2 bytes x columns ({reads_cols} per step) x {steps} steps",
+                    "traffic": profiled_traffic("profiles/k2_circuit_chains_bench.md",
                                                 "paper_2409_17688_gb300/csrc/circuit.cu"),
-                    "traffic_unit": "DRAM bytes per launch (ncu read+write; the chain stays on chip, so "
+                    "traffic_unit": "DRAM bytes per launch (ncu read+write; the chains stay on chip, so "
                                     "a launch reads its chunks once whatever its step count)",
-                    "shared_memory": profiled_shared("profiles/k2_circuit_chain_n9.md",
+                    "shared_memory": profiled_shared("profiles/k2_circuit_chains_bench.md",
                                                      "paper_2409_17688_gb300/csrc/circuit.cu"),
                     "launch_us": round(launch_ms * 1e3, 1),
-                    "step_us": round(step_ms * 1e3, 2),
-                    "circuit": circ,
+                    "step_us": round(launch_ms / steps * 1e3, 2),
+                    "n9_chain_alone_step_us": round(n9_alone_us, 2),
+                    "circuits": circs,
                     # what the kernel executes: one 16-bit minimum per circuit row read and column
                     "executed_minima": {
-                        "per_s": round(circ["reads"] * cols[9] * steps9 / (launch_ms * 1e-3) / 1e9, 1),
+                        "per_s": round(reads_cols * steps / (launch_ms * 1e-3) / 1e9, 1),
                         "unit": "G minima/s",
-                        "vs_vimin3_peak": round(circ["reads"] * cols[9] * steps9 / (launch_ms * 1e-3)
-                                                / peak_vimin3, 4),
-                        "rule": f"{circ['reads']} row reads x {cols[9]} columns x {steps9} steps"},
-                    # what the sparse product it replaces would evaluate (nnz(A) terms per column)
-                    "product_equivalent": {"terms_per_s": round(achieved / 1e9, 1), "unit": "G terms/s",
-                                           "vs_vimin3_peak": round(achieved / peak_vimin3, 4),
-                                           "note": "terms of the sparse product A (x) P; the circuit "
-                                                   f"executes {circ['reads']} of every {nnz[9]}"}}
+                        "vs_vimin3_peak": round(reads_cols * steps / (launch_ms * 1e-3) / peak_vimin3, 4),
+                        "rule": f"{reads_cols} row reads x columns per step x {steps} steps"},
+                    # what the sparse products it replaces would evaluate (nnz(A) terms per column)
+                    "product_equivalent": {
+                        "terms_per_s": round(terms_cols * steps / (launch_ms * 1e-3) / 1e9, 1),
+                        "unit": "G terms/s",
+                        "vs_vimin3_peak": round(terms_cols * steps / (launch_ms * 1e-3) / peak_vimin3, 4),
+                        "note": f"terms of the sparse products A (x) P; the circuits execute {reads_cols} "
+                                f"of every {terms_cols}"}}
 
     # ---- e2e through the C ABI with host buffers (synchronous gamma_2 tables)
     out = np.zeros((len(PATH_ORDERS), K_MAX + 1), dtype=np.int64)
@@ -393,10 +418,10 @@ def run_ours(args):
                                    "conflict-free 16-byte loads, 8 CTAs per SM)")
         roofline["nominal_peak"] = {"value": round(nominal / 1e9, 1), "unit": "GB/s",
                                     "rule": f"128 B/clk/SM x {props.multi_processor_count} SMs x {mhz} MHz"}
-    # our launches per chain: the diagonal fill, the initial power and the
-    # chain (one launch with a circuit, one per step without)
-    per_chain = {n: 3 if mp.mp_transfer_circuit_info(n)["width"] > 0 else K_MAX + 1 for n in PATH_ORDERS}
-    launches = sum(per_chain.values()) * args.steps
+    # our launches per step: the chains all run on the shared-memory circuit,
+    # so one diagonal fill, one initial power per chain and one launch of the
+    # circuit kernel for all chains together
+    launches = (2 + len(PATH_ORDERS)) * args.steps
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "Gop/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_per_step, 4),
@@ -766,7 +791,11 @@ def run_profile(what: str):
     __graft_entry__.build()
     import paper_2409_17688_gb300 as mp
     from paper_2409_17688_gb300 import synth
-    if what.startswith("chain"):
+    if what == "chains":
+        # the bench's four chains in one launch of the circuit kernel, 11 steps
+        for _ in range(3):
+            mp.mp_transfer_power_sequences(list(PATH_ORDERS), 12)
+    elif what.startswith("chain"):
         n = int(what[5:])
         for _ in range(3):
             mp.mp_transfer_power_sequence(n, 12, keep_powers=False)

@@ -274,10 +274,12 @@ int mp_gamma2_table(int n, int k_max, int64_t *out);
 /* Several transfer chains at once (Algorithm 2 and Theorem 2 for each path
  * order ns[i], i < count, distinct): gdiag (DEVICE int32, count x k_max,
  * row i for ns[i]) receives min diag A^k for k = 1..k_max as in
- * mp_transfer_power_sequence with powers_opt NULL.  The chains run side by
- * side on library-owned streams forked from and joined back into stream, so
- * the work is asynchronous on stream and the short chains' per-step latency
- * overlaps the long ones.  Errors: MP_EINVAL (count < 0, NULL arrays,
+ * mp_transfer_power_sequence with powers_opt NULL.  Up to 8 chains that all
+ * run on the shared-memory reuse circuit (n <= 9) run in one launch on
+ * stream, the longest chain's CTAs first; otherwise the chains run side by
+ * side on library-owned streams forked from and joined back into stream.
+ * Either way the work is asynchronous on stream and the short chains
+ * overlap the long ones.  Errors: MP_EINVAL (count < 0, NULL arrays,
  * k_max < 1, an n out of range or repeated), MP_ENOMEM, MP_ECUDA. */
 int mp_transfer_power_sequences(const int *ns, int count, int k_max, int32_t *gdiag,
                                 void *stream);

@@ -68,11 +68,20 @@ static int device_state(DeviceState **out) {
         int optin = 0;
         MP_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         st.info.smem_optin = (size_t)optin;
+        int per_sm = 0;
+        MP_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        st.info.smem_sm = (size_t)per_sm;
         MP_CUDA_TRY(cudaMalloc(&st.status, sizeof(int)));
         MP_CUDA_TRY(cudaMemset(st.status, 0, sizeof(int)));
         MP_CUDA_TRY(cudaStreamCreateWithFlags(&st.sync_stream, cudaStreamNonBlocking));
-        for (cudaStream_t &cs : st.chain_streams)
-            MP_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        // Side-by-side chains go to these streams largest first; the first
+        // streams get the highest priorities, so the CTAs of the longest
+        // chain are placed on the SMs before the short chains fill the rest.
+        int lo_prio = 0, hi_prio = 0;
+        MP_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+        for (int i = 0; i < kChainStreams; ++i)
+            MP_CUDA_TRY(cudaStreamCreateWithPriority(&st.chain_streams[i], cudaStreamNonBlocking,
+                                                     std::min(lo_prio, hi_prio + i)));
         it = g_dev.emplace(dev, st).first;
     }
     *out = &it->second;
@@ -1045,6 +1054,42 @@ int mp_transfer_power_sequences(const int *ns, int count, int k_max, int32_t *gd
     std::vector<int> order((size_t)count);
     for (int i = 0; i < count; ++i) order[(size_t)i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ns[a] > ns[b]; });
+    // Chains that all run on the shared-memory circuit go into one launch,
+    // the longest chain's CTAs first (separate launches on several streams
+    // reach the SMs in no fixed order, and a short chain placed first can
+    // push the longest one into a second wave).
+    if (count <= 8 && k_max >= 2) {
+        std::vector<TransferEntry *> tes;
+        std::vector<const PlanDev *> plans;
+        bool all = true;
+        for (int k = 0; k < count && all; ++k) {
+            TransferEntry *te;
+            MP_TRY(transfer_entry(ns[order[(size_t)k]], s, &te));
+            const PlanDev *pp = nullptr;
+            MP_TRY(narrow_plan(te, s, &pp));
+            all = pp->circuit.ready;
+            tes.push_back(te);
+            plans.push_back(pp);
+        }
+        if (all) {
+            NvtxScope nv("mp_transfer_power_sequences %d chains, one launch", count);
+            MP_TRY(launch_fill_i32(gdiag, (int64_t)count * k_max, (int32_t)kInf16, s));
+            std::vector<DevBuf> bufs((size_t)count);
+            std::vector<uint16_t *> b1((size_t)count);
+            std::vector<int32_t *> gd((size_t)count);
+            for (int k = 0; k < count; ++k) {
+                const PlanDev &pl = *plans[(size_t)k];
+                MP_TRY(bufs[(size_t)k].alloc((size_t)pl.N * (size_t)pl.ldb * 2, s));
+                b1[(size_t)k] = bufs[(size_t)k].as<uint16_t>();
+                gd[(size_t)k] = gdiag + (size_t)order[(size_t)k] * (size_t)k_max;
+                MP_TRY(sparse_init_from_csr(pl, tes[(size_t)k]->csr.row_ptr.as<int64_t>(),
+                                            tes[(size_t)k]->csr.col.as<int32_t>(),
+                                            tes[(size_t)k]->csr.val.as<int16_t>(), b1[(size_t)k], nullptr,
+                                            gd[(size_t)k], s));
+            }
+            return circuit_multi_chain(plans.data(), b1.data(), count, k_max, gd.data(), s);
+        }
+    }
     cudaEvent_t fork = nullptr;
     MP_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     int rc = MP_OK;

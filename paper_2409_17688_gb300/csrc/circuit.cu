@@ -166,28 +166,45 @@ constexpr uint32_t kMetaCopy = 32768;  // bytes per bulk copy of the circuit
 // place, is the next step's X, and the two regions swap: with sh = 0 or Nh,
 // image index j (X rows 0..N-1, result rows Nh..Nh+N-1, Nh = N rounded up to
 // 8) lives at (j + sh) mod 2Nh.
-template <bool kChain>
-__global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs a) {
+// kGBlob: the circuit stays in global memory (read through L1/L2, the next
+// slice's lane info and entry block loaded one slice ahead) and only the
+// image takes shared memory, so two CTAs fit on an SM: chosen where the grid
+// is larger than the GPU's SMs, where one CTA's barrier waits then overlap
+// the other's work.  Otherwise the circuit is copied into shared memory.
+// The work of one CTA: column chunk bx of the chain (or step) a.
+template <bool kChain, bool kGBlob>
+__device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
     constexpr int RB = 2 * kCircW;  // bytes per image row
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t sbase = csmem_u32(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t N = a.N;
     const uint32_t Nh = (uint32_t)a.Nh, N2 = 2 * Nh;
-    const int64_t c0 = (int64_t)blockIdx.x * kCircW;
+    const int64_t c0 = (int64_t)bx * kCircW;
     const uint32_t mb = sbase + (uint32_t)circuit_image_bytes(Nh, kCircW);
 
     // The circuit: plan data only, so its bulk copies start before the
     // previous step has finished.  The barrier's initialisation is made
     // visible to the other threads by the block barrier below, before any of
     // them waits on it.
-    const uint32_t bar = mb + a.meta_bytes;
+    const uint32_t copied = kGBlob ? 0u : a.meta_bytes;
+    const uint32_t bar = mb + copied;
+    if (kGBlob && threadIdx.x == 0) {
+        // the circuit is read from L2 at every slice: each CTA brings its share
+        // of it into L2 now (plan data, so before the previous kernel ends), so
+        // that even the first step after an L2 flush finds it there
+        const uint32_t part = 4096u, o = ((uint32_t)bx * part) % ((a.meta_bytes + part - 1) / part * part);
+        if (o < a.meta_bytes)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.meta + o),
+                         "r"(min(part, a.meta_bytes - o))
+                         : "memory");
+    }
     if (threadIdx.x == 0) {
         cmbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        cmbar_arrive_expect_tx(bar, a.meta_bytes + a.extra_tx);
-        for (uint32_t o = 0; o < a.meta_bytes; o += kMetaCopy)
-            cbulk_copy(mb + o, a.meta + o, min(kMetaCopy, a.meta_bytes - o), bar);
+        cmbar_arrive_expect_tx(bar, copied + a.extra_tx);
+        for (uint32_t o = 0; o < copied; o += kMetaCopy)
+            cbulk_copy(mb + o, a.meta + o, min(kMetaCopy, copied - o), bar);
     }
     // row 2Nh of the image: above every value, the padding of short lists
     if (threadIdx.x < RB / 4) reinterpret_cast<uint32_t *>(smem + (size_t)N2 * RB)[threadIdx.x] = 0xFFFFFFFFu;
@@ -213,20 +230,52 @@ __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs 
     }
 
     const uint32_t m_info = mb + a.off_info, m_en = mb + a.off_ents, m_z = mb + a.off_z;
+    const uint32_t *g_lvl = reinterpret_cast<const uint32_t *>(a.meta);
+    const uint32_t *g_info = reinterpret_cast<const uint32_t *>(a.meta + a.off_info);
+    const uint4 *g_ents = reinterpret_cast<const uint4 *>(a.meta + a.off_ents);
+    const uint16_t *g_z = reinterpret_cast<const uint16_t *>(a.meta + a.off_z);
     auto label = [&](uint32_t q) {
+        if (kGBlob) return (uint32_t)__ldg(g_z + q);
         const uint32_t zw = clds_u32(m_z + 4u * (q >> 1));
         return (q & 1) ? zw >> 16 : zw & 0xFFFFu;
+    };
+    auto level_start = [&](int l) { return kGBlob ? (int)__ldg(g_lvl + l) : (int)clds_u32(mb + 4u * (uint32_t)l); };
+    auto slice_info = [&](int sl) {
+        return kGBlob ? __ldg(g_info + (size_t)sl * 32 + lane) : clds_u32(m_info + 4u * ((uint32_t)sl * 32u + (uint32_t)lane));
+    };
+    auto slice_ents = [&](int sl) {
+        return kGBlob ? __ldg(g_ents + (size_t)sl * 32 + lane) : clds_v4(m_en + 16u * ((uint32_t)sl * 32u + (uint32_t)lane));
     };
     const int k_last = kChain ? a.k_max : 2;
     uint32_t sh = 0;
     for (int k = 2; k <= k_last; ++k) {
         for (int l = 0; l < a.levels; ++l) {
-            const int s1 = (int)clds_u32(mb + 4u * (uint32_t)(l + 1));
-            for (int s = (int)clds_u32(mb + 4u * (uint32_t)l) + warp; s < s1; s += kCircWarps) {
-                const uint32_t slot = (uint32_t)s * 32u + (uint32_t)lane;
-                const uint32_t info = clds_u32(m_info + 4u * slot);
+            const int s1 = level_start(l + 1);
+            int s = level_start(l) + warp;
+            // from global memory a slice's lane info and entry block are read
+            // one slice ahead
+            uint32_t info_n = 0;
+            uint4 e_n = make_uint4(0, 0, 0, 0);
+            if (kGBlob && s < s1) {
+                info_n = slice_info(s);
+                e_n = slice_ents(s);
+            }
+            for (; s < s1; s += kCircWarps) {
+                uint32_t info;
+                uint4 e_c;
+                if (kGBlob) {
+                    info = info_n;
+                    e_c = e_n;
+                    if (s + kCircWarps < s1) {
+                        info_n = slice_info(s + kCircWarps);
+                        e_n = slice_ents(s + kCircWarps);
+                    }
+                } else {
+                    info = slice_info(s);
+                    e_c = slice_ents(s);
+                }
                 uint4 acc = make_uint4(kInf16x2, kInf16x2, kInf16x2, kInf16x2);
-                fold8<RB>(acc, clds_v4(m_en + 16u * slot), sbase, N2, sh);
+                fold8<RB>(acc, e_c, sbase, N2, sh);
                 // the lanes of one row (an aligned group of 1 << lg) combine;
                 // the slice's widest row sits in lane 0
                 const uint32_t lg = (info >> 16) & 7u;
@@ -289,6 +338,37 @@ __global__ void __launch_bounds__(kCircThreads, 1) circuit_step_kernel(CircArgs 
         }
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <bool kChain, bool kGBlob>
+__global__ void __launch_bounds__(kCircThreads, kGBlob ? 2 : 1) circuit_step_kernel(CircArgs a) {
+    circuit_body<kChain, kGBlob>(a, (int)blockIdx.x);
+}
+
+// Several chains in one launch: the CTAs of chain i are blocks
+// cta0[i] .. cta0[i + 1] - 1, the chains in the order given (longest first),
+// so the longest chain's CTAs are placed on the SMs first and the short
+// chains fill what is left, whatever the timing of the launches.  A CTA of
+// chain i runs its chunks b, b + ctas_i, ... one after another (chunks[i] in
+// all), so that the short chains fit into the waves the longest needs.
+constexpr int kMultiChains = 8;
+struct MultiCircArgs {
+    CircArgs c[kMultiChains];
+    int cta0[kMultiChains + 1];
+    int chunks[kMultiChains];
+    int count;
+};
+
+template <bool kGBlob>
+__global__ void __launch_bounds__(kCircThreads, kGBlob ? 2 : 1)
+    circuit_multi_kernel(const __grid_constant__ MultiCircArgs m) {
+    int ci = 0;
+    while (ci + 1 < m.count && (int)blockIdx.x >= m.cta0[ci + 1]) ++ci;
+    const int ctas = m.cta0[ci + 1] - m.cta0[ci];
+    for (int bx = (int)blockIdx.x - m.cta0[ci]; bx < m.chunks[ci]; bx += ctas) {
+        circuit_body<true, kGBlob>(m.c[ci], bx);
+        __syncthreads();  // shared memory and the mbarrier are set up again for the next chunk
+    }
 }
 
 }  // namespace
@@ -658,16 +738,12 @@ int circuit_upload(const CircuitHost &h, const std::vector<uint16_t> &z,
     return MP_OK;
 }
 
-// One launch: a step (Bin -> Bout) or a whole chain from Bin = P_1.
-static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uint16_t *Bout, int k_max,
-                          int16_t *user_out, size_t slot, int32_t *gdiag, cudaStream_t s,
-                          uint32_t extra_tx = 0, int out_k0 = 1) {
+static int circuit_args(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int k_max, int16_t *user_out,
+                        size_t slot, int32_t *gdiag, uint32_t extra_tx, int out_k0, CircArgs *out) {
     const CircuitDev &c = p.circuit;
     if (!c.ready) return set_error(MP_EINVAL, "plan has no circuit");
     if (p.narrow && user_out) return set_error(MP_EINVAL, "a narrow chain has no full powers to write");
-    DeviceInfo di;
-    MP_TRY(device_info(&di));
-    CircArgs a;
+    CircArgs &a = *out;
     memset(&a, 0, sizeof(a));
     a.Bin = Bin;
     a.Bout = Bout;
@@ -688,23 +764,27 @@ static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uin
     a.drow = c.drow.as<uint16_t>();
     a.gdiag = gdiag;
     a.extra_tx = extra_tx;
-    MP_TRY(device_status_ptr(&a.status));
-    const size_t smem = circuit_image_bytes(c.Nh, kCircW) + c.meta_bytes + kCircBarBytes;
-    if (smem > di.smem_optin) return set_error(MP_EINVAL, "circuit does not fit shared memory");
-    const unsigned grid = (unsigned)(p.ldb / kCircW);
-    if (grid == 0) return MP_OK;
-    auto *kern = chain ? circuit_step_kernel<true> : circuit_step_kernel<false>;
-    // the dynamic size each kernel may take, raised as larger plans come
+    return device_status_ptr(&a.status);
+}
+
+// The dynamic shared memory a kernel may take, raised as larger plans come.
+template <class Kern>
+static int circuit_attr(Kern kern, int kind, bool gblob, size_t smem, const DeviceInfo &di) {
     static std::mutex attr_mu;
-    static size_t attr_set[2][64] = {};
-    const int kind = chain ? 1 : 0;
-    {
-        std::lock_guard<std::mutex> lk(attr_mu);
-        if (di.device >= 64 || attr_set[kind][di.device] < smem) {
-            MP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            if (di.device < 64) attr_set[kind][di.device] = smem;
-        }
+    static size_t attr_set[8][64] = {};
+    std::lock_guard<std::mutex> lk(attr_mu);
+    if (di.device >= 64 || attr_set[kind][di.device] < smem) {
+        MP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (gblob)
+            MP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared));
+        if (di.device < 64) attr_set[kind][di.device] = smem;
     }
+    return MP_OK;
+}
+
+template <class Kern, class Args>
+static int circuit_kick(Kern kern, const Args &a, unsigned grid, size_t smem, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kCircThreads);
@@ -718,6 +798,78 @@ static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uin
     MP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
+}
+
+// One launch: a step (Bin -> Bout) or a whole chain from Bin = P_1.
+static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uint16_t *Bout, int k_max,
+                          int16_t *user_out, size_t slot, int32_t *gdiag, cudaStream_t s,
+                          uint32_t extra_tx = 0, int out_k0 = 1) {
+    DeviceInfo di;
+    MP_TRY(device_info(&di));
+    CircArgs a;
+    MP_TRY(circuit_args(p, Bin, Bout, k_max, user_out, slot, gdiag, extra_tx, out_k0, &a));
+    const CircuitDev &c = p.circuit;
+    const unsigned grid = (unsigned)(p.ldb / kCircW);
+    if (grid == 0) return MP_OK;
+    // the circuit in global memory where the grid is larger than the SMs and
+    // two images fit an SM (a chain writing full powers keeps one CTA per SM:
+    // its stores, not its barriers, bound it)
+    const size_t image = circuit_image_bytes(c.Nh, kCircW) + kCircBarBytes;
+    const bool gblob = grid > (unsigned)di.sms && !user_out && 2 * (image + 1024) <= di.smem_sm;
+    const size_t smem = image + (gblob ? 0 : c.meta_bytes);
+    if (smem > di.smem_optin) return set_error(MP_EINVAL, "circuit does not fit shared memory");
+    auto *kern = gblob ? (chain ? circuit_step_kernel<true, true> : circuit_step_kernel<false, true>)
+                       : (chain ? circuit_step_kernel<true, false> : circuit_step_kernel<false, false>);
+    MP_TRY(circuit_attr(kern, (chain ? 1 : 0) + (gblob ? 2 : 0), gblob, smem, di));
+    return circuit_kick(kern, a, grid, smem, s);
+}
+
+int circuit_multi_chain(const PlanDev *const *plans, uint16_t *const *B1, int count, int k_max,
+                        int32_t *const *gdiag, cudaStream_t s) {
+    if (count < 1 || count > kMultiChains) return set_error(MP_EINVAL, "%d chains in one launch", count);
+    if (k_max < 2) return MP_OK;
+    DeviceInfo di;
+    MP_TRY(device_info(&di));
+    MultiCircArgs m;
+    memset(&m, 0, sizeof(m));
+    m.count = count;
+    size_t image_max = 0, meta_max = 0;
+    int64_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        const PlanDev &p = *plans[i];
+        MP_TRY(circuit_args(p, B1[i], nullptr, k_max, nullptr, 0, gdiag[i], 0, 1, &m.c[i]));
+        m.chunks[i] = (int)(p.ldb / kCircW);
+        total += m.chunks[i];
+        image_max = std::max(image_max, circuit_image_bytes(p.circuit.Nh, kCircW) + kCircBarBytes);
+        meta_max = std::max(meta_max, (size_t)p.circuit.meta_bytes + circuit_image_bytes(p.circuit.Nh, kCircW) +
+                                          kCircBarBytes);
+    }
+    if (total == 0) return MP_OK;
+    const bool gblob = total > di.sms && 2 * (image_max + 1024) <= di.smem_sm;
+    // The first chain takes one CTA per chunk, in as many waves of resident
+    // CTAs as it needs (and room for one CTA of every other chain); the
+    // others take the fewest chunks per CTA that fit them into those waves.
+    const int64_t slots = (int64_t)di.sms * (gblob ? 2 : 1);
+    const int64_t room = (m.chunks[0] + count - 1 + slots - 1) / slots * slots;
+    int f = 1;
+    for (;;) {
+        int64_t need = m.chunks[0];
+        bool last = true;
+        for (int i = 1; i < count; ++i) {
+            need += (m.chunks[i] + f - 1) / f;
+            last = last && f >= m.chunks[i];
+        }
+        if (need <= room || last) break;
+        ++f;
+    }
+    for (int i = 0; i < count; ++i)
+        m.cta0[i + 1] = m.cta0[i] + (i == 0 ? m.chunks[0] : (m.chunks[i] + f - 1) / f);
+    const unsigned grid = (unsigned)m.cta0[count];
+    const size_t smem = gblob ? image_max : meta_max;
+    if (smem > di.smem_optin) return set_error(MP_EINVAL, "circuit does not fit shared memory");
+    auto *kern = gblob ? circuit_multi_kernel<true> : circuit_multi_kernel<false>;
+    MP_TRY(circuit_attr(kern, 4 + (gblob ? 1 : 0), gblob, smem, di));
+    return circuit_kick(kern, m, grid, smem, s);
 }
 
 int circuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t *user_out,

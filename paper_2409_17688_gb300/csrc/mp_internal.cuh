@@ -66,7 +66,8 @@ int device_status_ptr(int **p);
 struct DeviceInfo {
     int device = -1;
     int sms = 0;
-    size_t smem_optin = 0;
+    size_t smem_optin = 0;  // dynamic shared memory one block may take
+    size_t smem_sm = 0;     // shared memory of one SM
 };
 int device_info(DeviceInfo *out);
 

@@ -293,6 +293,12 @@ int gcircuit_block_chain(const PlanDev &p, uint16_t *B0, uint16_t *B1, int k_max
                          int64_t width, int32_t *gdiag, cudaStream_t s);
 int gcircuit_chunk(const PlanDev &p);  // columns per chunk (0: no global circuit)
 
+// Several chains (at most 8, each plan with a circuit) in one launch, the
+// CTAs of plans[0] first: B1[i] the labelled buffer of chain i's P_1, gdiag[i]
+// its diagonal minima.
+int circuit_multi_chain(const PlanDev *const *plans, uint16_t *const *B1, int count, int k_max,
+                        int32_t *const *gdiag, cudaStream_t s);
+
 // Failure injection: one step whose bounded wait for the circuit's copies
 // runs out (MP_ETIMEOUT latched in the device status word, nothing written).
 int circuit_timeout_probe(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, cudaStream_t s);

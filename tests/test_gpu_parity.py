@@ -891,6 +891,22 @@ def test_gamma2_tables_of_the_timed_workload(mp, torch):
         assert np.array_equal(mp.mp_gamma2_tables(ns, kmax), t)
 
 
+def test_side_by_side_chains_mixing_both_circuits(mp, torch):
+    """Chains on the shared-memory circuit run in one launch; a set that also
+    holds a path order on the global circuit (n = 10) runs on library streams
+    instead.  Both give the one-at-a-time minimum diagonals, and the oracle's
+    for the small orders."""
+    for ns in ([10, 6, 3], [9, 8, 7, 6, 5, 4, 3, 2]):
+        g = mp.mp_transfer_power_sequences(ns, 50)
+        torch.cuda.synchronize()
+        for i, n in enumerate(ns):
+            _, gi = mp.mp_transfer_power_sequence(n, 50, keep_powers=False)
+            torch.cuda.synchronize()
+            assert torch.equal(g[i], gi), (ns, n)
+            if n <= 7:
+                assert np.array_equal(host(g[i]), oracle_gdiag(n, 50)), (ns, n)
+
+
 def test_several_chains_in_a_cuda_graph(mp, torch):
     """The side-by-side chains can be captured into a CUDA graph (the library
     streams join the capture through the fork and join events) and replayed;
