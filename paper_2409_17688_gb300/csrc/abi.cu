@@ -119,6 +119,10 @@ struct TransferEntry {
     int64_t narrow_cols = 0;
     CircuitHost circuit;       // reuse circuit of the rows (empty: none)
     CircuitCover gcover;       // covers of the global circuit (levels = 0: none)
+    // the narrow plan's labelled first power and its diagonal minimum, kept
+    // for the shared-memory circuit chains (which only read their P_1)
+    DevBuf p1_narrow, g1_narrow;
+    bool have_p1_narrow = false;
 };
 
 // Lanes per row of the global circuit for a chain of `ncols` buffer columns:
@@ -362,6 +366,29 @@ static int narrow_plan(TransferEntry *te, cudaStream_t s, const PlanDev **out) {
     return MP_OK;
 }
 
+// The labelled P_1 of the narrow plan (A in the mirror columns) and g[1],
+// built once per plan on its first shared-memory circuit chain: such a chain
+// copies its chunks of P_1 into shared memory and never writes the buffer,
+// so later chains start from the same one.
+static int narrow_first_power(TransferEntry *te, const PlanDev &plan, cudaStream_t s,
+                              const uint16_t **p1, const int32_t **g1) {
+    std::lock_guard<std::mutex> lk(g_narrow_mu);
+    if (!te->have_p1_narrow) {
+        MP_TRY(te->p1_narrow.alloc((size_t)plan.N * (size_t)plan.ldb * 2, s, true));
+        MP_TRY(te->g1_narrow.alloc(sizeof(int32_t), s, true));
+        MP_TRY(launch_fill_i32(te->g1_narrow.as<int32_t>(), 1, (int32_t)kInf16, s));
+        MP_TRY(sparse_init_from_csr(plan, te->csr.row_ptr.as<int64_t>(), te->csr.col.as<int32_t>(),
+                                    te->csr.val.as<int16_t>(), te->p1_narrow.as<uint16_t>(), nullptr,
+                                    te->g1_narrow.as<int32_t>(), s));
+        // other streams may use it as soon as this returns
+        MP_CUDA_TRY(cudaStreamSynchronize(s));
+        te->have_p1_narrow = true;
+    }
+    *p1 = te->p1_narrow.as<uint16_t>();
+    *g1 = te->g1_narrow.as<int32_t>();
+    return MP_OK;
+}
+
 // The chain over a prepared sparse plan; B0 already holds P_1.
 // P_k goes to powers slot k - out_k0 and gdiag[k - out_k0] (out_k0 = 1 when
 // B0 holds A itself).
@@ -532,6 +559,13 @@ static int transfer_chain_direct(TransferEntry *te, int k_max, int16_t *powers_o
     const PlanDev *pp = &te->plan;
     if (!powers_opt) MP_TRY(narrow_plan(te, s, &pp));
     const PlanDev &plan = *pp;
+    if (!powers_opt && plan.circuit.ready) {
+        const uint16_t *p1;
+        const int32_t *g1;
+        MP_TRY(narrow_first_power(te, plan, s, &p1, &g1));
+        if (gdiag_opt) MP_TRY(launch_gdiag_init(&gdiag_opt, &g1, 1, k_max, s));
+        return circuit_chain(plan, p1, k_max, nullptr, 0, gdiag_opt, s);
+    }
     if (gdiag_opt) MP_TRY(launch_fill_i32(gdiag_opt, k_max, (int32_t)kInf16, s));
     // large chains check the free memory first (a synchronisation, so a
     // graph capture of such a chain fails and it runs directly instead)
@@ -1073,21 +1107,15 @@ int mp_transfer_power_sequences(const int *ns, int count, int k_max, int32_t *gd
         }
         if (all) {
             NvtxScope nv("mp_transfer_power_sequences %d chains, one launch", count);
-            MP_TRY(launch_fill_i32(gdiag, (int64_t)count * k_max, (int32_t)kInf16, s));
-            std::vector<DevBuf> bufs((size_t)count);
-            std::vector<uint16_t *> b1((size_t)count);
+            std::vector<const uint16_t *> p1((size_t)count);
+            std::vector<const int32_t *> g1((size_t)count);
             std::vector<int32_t *> gd((size_t)count);
             for (int k = 0; k < count; ++k) {
-                const PlanDev &pl = *plans[(size_t)k];
-                MP_TRY(bufs[(size_t)k].alloc((size_t)pl.N * (size_t)pl.ldb * 2, s));
-                b1[(size_t)k] = bufs[(size_t)k].as<uint16_t>();
+                MP_TRY(narrow_first_power(tes[(size_t)k], *plans[(size_t)k], s, &p1[(size_t)k], &g1[(size_t)k]));
                 gd[(size_t)k] = gdiag + (size_t)order[(size_t)k] * (size_t)k_max;
-                MP_TRY(sparse_init_from_csr(pl, tes[(size_t)k]->csr.row_ptr.as<int64_t>(),
-                                            tes[(size_t)k]->csr.col.as<int32_t>(),
-                                            tes[(size_t)k]->csr.val.as<int16_t>(), b1[(size_t)k], nullptr,
-                                            gd[(size_t)k], s));
             }
-            return circuit_multi_chain(plans.data(), b1.data(), count, k_max, gd.data(), s);
+            MP_TRY(launch_gdiag_init(gd.data(), g1.data(), count, k_max, s));
+            return circuit_multi_chain(plans.data(), p1.data(), count, k_max, gd.data(), s);
         }
     }
     cudaEvent_t fork = nullptr;

@@ -122,10 +122,6 @@ struct CircArgs {
     uint32_t extra_tx;    // bytes expected beyond the circuit's (0; > 0 only to inject a timeout)
 };
 
-__device__ __forceinline__ uint32_t pick_word(const uint4 &v, int k) {
-    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
-}
-
 // acc = min(acc, the image rows an entry block names), 16 bytes per lane;
 // entries naming the INF row (the padding of short lists, index 2Nh) load
 // nothing, the others live at image row (index + sh) mod 2Nh.
@@ -203,8 +199,9 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
         cmbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         cmbar_arrive_expect_tx(bar, copied + a.extra_tx);
-        for (uint32_t o = 0; o < copied; o += kMetaCopy)
-            cbulk_copy(mb + o, a.meta + o, min(kMetaCopy, copied - o), bar);
+        if (!kGBlob)
+            for (uint32_t o = 0; o < a.meta_bytes; o += kMetaCopy)
+                cbulk_copy(mb + o, a.meta + o, min(kMetaCopy, a.meta_bytes - o), bar);
     }
     // row 2Nh of the image: above every value, the padding of short lists
     if (threadIdx.x < RB / 4) reinterpret_cast<uint32_t *>(smem + (size_t)N2 * RB)[threadIdx.x] = 0xFFFFFFFFu;
@@ -246,20 +243,24 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
     auto slice_ents = [&](int sl) {
         return kGBlob ? __ldg(g_ents + (size_t)sl * 32 + lane) : clds_v4(m_en + 16u * ((uint32_t)sl * 32u + (uint32_t)lane));
     };
+    // the label of the row whose diagonal entry lies in this thread's column
+    const uint32_t zdrow = (kChain && drow != 0xFFFFu) ? label(drow) : 0u;
     const int k_last = kChain ? a.k_max : 2;
     uint32_t sh = 0;
+    // From global memory a slice's lane info and entry block are read one
+    // slice ahead, and the first slice of the next level (of the next step's
+    // first level after the last) before the barrier that ends a level: the
+    // circuit is plan data, so nothing orders these reads after the barrier.
+    uint32_t info_n = 0;
+    uint4 e_n = make_uint4(0, 0, 0, 0);
+    if (kGBlob && level_start(0) + warp < level_start(1)) {
+        info_n = slice_info(level_start(0) + warp);
+        e_n = slice_ents(level_start(0) + warp);
+    }
     for (int k = 2; k <= k_last; ++k) {
         for (int l = 0; l < a.levels; ++l) {
             const int s1 = level_start(l + 1);
             int s = level_start(l) + warp;
-            // from global memory a slice's lane info and entry block are read
-            // one slice ahead
-            uint32_t info_n = 0;
-            uint4 e_n = make_uint4(0, 0, 0, 0);
-            if (kGBlob && s < s1) {
-                info_n = slice_info(s);
-                e_n = slice_ents(s);
-            }
             for (; s < s1; s += kCircWarps) {
                 uint32_t info;
                 uint4 e_c;
@@ -305,18 +306,37 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
                                    (int64_t)a.caller[q] * N + c0,
                                acc, N - c0);
             }
+            if (kGBlob) {
+                const int nl = l + 1 < a.levels ? l + 1 : 0;
+                const int ns = level_start(nl) + warp;
+                if (ns < level_start(nl + 1)) {
+                    info_n = slice_info(ns);
+                    e_n = slice_ents(ns);
+                }
+            }
             __syncthreads();  // this level's rows are read by the later levels
         }
         const uint32_t shr = sh;  // where this step's result rows are
         if (kChain) {
-            // the labels, in place: the result becomes the next step's X
-            for (int64_t q = threadIdx.x; q < N; q += kCircThreads) {
-                uint32_t rr = Nh + (uint32_t)q + sh;
-                if (rr >= N2) rr -= N2;
-                const uint32_t addr = sbase + rr * RB;
-                const uint32_t zq = label((uint32_t)q) * 0x10001u;
-                const uint4 v = clds_v4(addr);
-                csts_v4(addr, make_uint4(v.x + zq, v.y + zq, v.z + zq, v.w + zq));
+            // the labels, in place: the result becomes the next step's X (the
+            // labels of four rows per thread loaded before their rows)
+            for (uint32_t q0 = threadIdx.x; q0 < (uint32_t)N; q0 += 4 * kCircThreads) {
+                uint32_t zq[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t q = q0 + (uint32_t)j * kCircThreads;
+                    zq[j] = q < (uint32_t)N ? label(q) * 0x10001u : 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t q = q0 + (uint32_t)j * kCircThreads;
+                    if (q >= (uint32_t)N) break;
+                    uint32_t rr = Nh + q + sh;
+                    if (rr >= N2) rr -= N2;
+                    const uint32_t addr = sbase + rr * RB;
+                    const uint4 v = clds_v4(addr);
+                    csts_v4(addr, make_uint4(v.x + zq[j], v.y + zq[j], v.z + zq[j], v.w + zq[j]));
+                }
             }
             sh = Nh - sh;
             __syncthreads();
@@ -330,7 +350,7 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
                 if (rr >= N2) rr -= N2;
                 const uint32_t w = clds_u32(sbase + rr * RB + 4u * (uint32_t)(lane >> 1));
                 v = (int32_t)((lane & 1) ? w >> 16 : w & 0xFFFFu);
-                if (kChain) v -= (int32_t)label(drow);
+                if (kChain) v -= (int32_t)zdrow;
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
@@ -824,7 +844,7 @@ static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uin
     return circuit_kick(kern, a, grid, smem, s);
 }
 
-int circuit_multi_chain(const PlanDev *const *plans, uint16_t *const *B1, int count, int k_max,
+int circuit_multi_chain(const PlanDev *const *plans, const uint16_t *const *B1, int count, int k_max,
                         int32_t *const *gdiag, cudaStream_t s) {
     if (count < 1 || count > kMultiChains) return set_error(MP_EINVAL, "%d chains in one launch", count);
     if (k_max < 2) return MP_OK;

@@ -141,6 +141,10 @@ int launch_transfer_csr_count(int n, const WordMasks *d_masks, int64_t N, int64_
 int launch_transfer_csr_fill(int n, const WordMasks *d_masks, int64_t N, const int64_t *row_ptr,
                              int32_t *col, cudaStream_t s);
 int launch_fill_i32(int32_t *p, int64_t count, int32_t v, cudaStream_t s);
+// dst[c][0] = *g1[c] and dst[c][1 .. k_max) = INF for count <= kGdiagChains chains, one launch.
+constexpr int kGdiagChains = 8;
+int launch_gdiag_init(int32_t *const *dst, const int32_t *const *g1, int count, int k_max,
+                      cudaStream_t s);
 int launch_diag_min(const int16_t *P, int64_t N, int64_t ld, int32_t *out, bool init,
                     cudaStream_t s);
 // init false: fold into out[0..4) as it stands (statistics over several

@@ -7,6 +7,7 @@
 // in registers, then across the warp with shuffles, then one atomicMin per
 // warp into a 32-bit result that starts at INF.
 #include <algorithm>
+#include <cstring>
 
 #include "mp_internal.cuh"
 
@@ -24,6 +25,19 @@ __global__ void fill_i32_kernel(int32_t *p, int64_t count, int32_t v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
+}
+
+// g[0 .. k_max) of up to kGdiagChains chains: g[0] from the chain's first
+// power (a value kept on the device), INF for the powers still to come.
+struct GdiagInitArgs {
+    int32_t *dst[kGdiagChains];
+    const int32_t *g1[kGdiagChains];
+    int count, k_max;
+};
+__global__ void gdiag_init_kernel(const __grid_constant__ GdiagInitArgs a) {
+    for (int c = 0; c < a.count; ++c)
+        for (int i = (int)threadIdx.x; i < a.k_max; i += (int)blockDim.x)
+            a.dst[c][i] = i == 0 ? *a.g1[c] : (int32_t)kInf16;
 }
 
 __global__ void diag_min_kernel(const int16_t *__restrict__ P, int64_t N, int64_t ld,
@@ -139,6 +153,23 @@ int launch_fill_i32(int32_t *p, int64_t count, int32_t v, cudaStream_t s) {
     int64_t blocks = (count + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     fill_i32_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, count, v);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+int launch_gdiag_init(int32_t *const *dst, const int32_t *const *g1, int count, int k_max,
+                      cudaStream_t s) {
+    if (count < 0 || count > kGdiagChains) return set_error(MP_EINVAL, "%d chains for one g init", count);
+    if (count == 0 || k_max < 1) return MP_OK;
+    GdiagInitArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int c = 0; c < count; ++c) {
+        a.dst[c] = dst[c];
+        a.g1[c] = g1[c];
+    }
+    a.count = count;
+    a.k_max = k_max;
+    gdiag_init_kernel<<<1, 256, 0, s>>>(a);
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

@@ -296,7 +296,7 @@ int gcircuit_chunk(const PlanDev &p);  // columns per chunk (0: no global circui
 // Several chains (at most 8, each plan with a circuit) in one launch, the
 // CTAs of plans[0] first: B1[i] the labelled buffer of chain i's P_1, gdiag[i]
 // its diagonal minima.
-int circuit_multi_chain(const PlanDev *const *plans, uint16_t *const *B1, int count, int k_max,
+int circuit_multi_chain(const PlanDev *const *plans, const uint16_t *const *B1, int count, int k_max,
                         int32_t *const *gdiag, cudaStream_t s);
 
 // Failure injection: one step whose bounded wait for the circuit's copies
