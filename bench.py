@@ -346,13 +346,12 @@ def run_ours(args):
     if all(circs[n].get("width", 0) > 0 for n in PATH_ORDERS):
         # algorithmic shared-memory bytes: every circuit row read, 2 bytes per column
         smem_bytes = reads_cols * 2 * steps
-        chunks = sum(-(-cols[n] // 64) * 64 // circs[n]["width"] for n in PATH_ORDERS)
+        chunks = sum(-(-cols[n] // 64) * 64 // 16 for n in PATH_ORDERS)
         roofline = {"bound": "smem",
                     "kernel": f"circuit_multi_kernel: the chains n = {', '.join(str(n) for n in PATH_ORDERS)} "
-                              f"in one launch ({chunks} chunks of 8 columns, one CTA for each of the n = 9 "
-                              f"chain's, which come first, and a few chunks for each CTA of the others; {steps} "
-                              "steps; more chunks than SMs, so the circuits are read from L2 and two CTAs "
-                              "share an SM)",
+                              f"in one launch ({chunks} chunks of 16 columns: one CTA per SM for each of the "
+                              "n = 9 chain's, which come first, and two chunks for each CTA of the others on "
+                              f"the remaining SMs; {steps} steps; the circuits read from L2)",
                     "achieved": round(smem_bytes / (launch_ms * 1e-3) / 1e9, 1),
                     "unit": "GB/s",
                     "algorithmic_bytes": smem_bytes,

@@ -24,16 +24,18 @@
 // lanes.  Rows are packed widest first into warp slices of 32 lanes, so
 // every lane of a level does the same work.
 //
-// Device (circuit_step_kernel): one CTA per chunk of 8 columns.  The circuit
-// (one blob, the same for every chunk and every step) is copied into shared
-// memory while the previous step finishes; then the chunk of X (N rows of 8
-// columns).  The levels run in order with a block barrier between them,
+// Device (circuit_step_kernel): one CTA per chunk of 8 columns (16 where a
+// chain has more 8-column chunks than the GPU has SMs: one CTA per SM then
+// spreads the columns evenly).  The circuit (one blob, the same for every
+// chunk and every step) is copied into shared memory while the previous step
+// finishes, or read from L2 where only the image fits; then the chunk of X
+// (N rows of 8 or 16 columns).  The levels run in order with a block barrier between them,
 // touching only shared memory: a warp takes every 16th slice of a level,
 // each lane folds its 8 rows (16 bytes of each), the lanes of a row combine
 // by shuffles and the first of them writes the row's result to shared memory
 // for the later levels and, with its label added, straight to the next
-// buffer.  After the levels the (at most 8) rows whose diagonal entries lie
-// in the chunk are read back and min-reduced into g[k].
+// buffer.  After the levels the (at most 8 or 16) rows whose diagonal
+// entries lie in the chunk are read back and min-reduced into g[k].
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -115,6 +117,9 @@ struct CircArgs {
     int out_k0;           // a chain: P_k goes to output slot k - out_k0
     int16_t *user_out;    // the caller's power(s), or null
     size_t slot;          // a chain: entries between the caller's powers
+    int64_t user_ld;      // entries between rows of a power in user_out: N, or a
+                          // multiple of 8 no smaller than ldb (then every piece is
+                          // one aligned store, columns past N into the row's padding)
     const int32_t *caller;   // per internal row, the caller's row (for user_out)
     const uint16_t *drow;    // per buffer column, the row whose diagonal entry it holds
     int32_t *gdiag;       // one step: g[k]; a chain: g[0 .. k_max - 1]
@@ -122,29 +127,48 @@ struct CircArgs {
     uint32_t extra_tx;    // bytes expected beyond the circuit's (0; > 0 only to inject a timeout)
 };
 
-// acc = min(acc, the image rows an entry block names), 16 bytes per lane;
-// entries naming the INF row (the padding of short lists, index 2Nh) load
-// nothing, the others live at image row (index + sh) mod 2Nh.
-template <int RB>
-__device__ __forceinline__ void fold8(uint4 &acc, const uint4 &e, uint32_t rbase, uint32_t N2,
+// Byte offset of 16-byte piece h of image row j.  With 8-column chunks a row
+// is one piece, in bank group j mod 8.  With 16-column chunks a row is two
+// pieces, swapped in rows with bit 2 set, so that piece h of rows with
+// distinct j mod 8 still lies in distinct bank groups (2j + (h ^ bit 2 of j)
+// mod 8): the entry colouring by j mod 8 holds for both.
+template <int kW>
+__device__ __forceinline__ uint32_t img_off(uint32_t j, uint32_t h) {
+    if (kW == 8) return j * 16u;
+    return j * 32u + 16u * (h ^ ((j >> 2) & 1u));
+}
+
+// acc = min(acc, the image rows an entry block names), 16 bytes per lane and
+// piece; entries naming the INF row (the padding of short lists, index 2Nh)
+// load nothing, the others live at image row (index + sh) mod 2Nh.
+template <int kW>
+__device__ __forceinline__ void fold8(uint4 (&acc)[kW / 8], const uint4 &e, uint32_t rbase, uint32_t N2,
                                       uint32_t sh) {
     const uint32_t ix[8] = {e.x & 0xFFFFu, e.x >> 16, e.y & 0xFFFFu, e.y >> 16,
                             e.z & 0xFFFFu, e.z >> 16, e.w & 0xFFFFu, e.w >> 16};
-    uint4 v[8];
+    uint32_t jj[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        uint32_t j = ix[k] + sh;
-        if (j >= N2) j -= N2;
-        v[k] = ix[k] != N2 ? clds_v4(rbase + j * RB) : make_uint4(~0u, ~0u, ~0u, ~0u);
+    for (int h = 0; h < kW / 8; ++h) {
+        uint4 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (h == 0) {
+                uint32_t j = ix[k] + sh;
+                if (j >= N2) j -= N2;
+                jj[k] = j;
+            }
+            v[k] = ix[k] != N2 ? clds_v4(rbase + img_off<kW>(jj[k], (uint32_t)h)) : make_uint4(~0u, ~0u, ~0u, ~0u);
+        }
+        uint4 &c = acc[h];
+        c.x = __vimin3_u16x2(__vimin3_u16x2(c.x, v[0].x, v[1].x), __vimin3_u16x2(v[2].x, v[3].x, v[4].x),
+                             __vimin3_u16x2(v[5].x, v[6].x, v[7].x));
+        c.y = __vimin3_u16x2(__vimin3_u16x2(c.y, v[0].y, v[1].y), __vimin3_u16x2(v[2].y, v[3].y, v[4].y),
+                             __vimin3_u16x2(v[5].y, v[6].y, v[7].y));
+        c.z = __vimin3_u16x2(__vimin3_u16x2(c.z, v[0].z, v[1].z), __vimin3_u16x2(v[2].z, v[3].z, v[4].z),
+                             __vimin3_u16x2(v[5].z, v[6].z, v[7].z));
+        c.w = __vimin3_u16x2(__vimin3_u16x2(c.w, v[0].w, v[1].w), __vimin3_u16x2(v[2].w, v[3].w, v[4].w),
+                             __vimin3_u16x2(v[5].w, v[6].w, v[7].w));
     }
-    acc.x = __vimin3_u16x2(__vimin3_u16x2(acc.x, v[0].x, v[1].x), __vimin3_u16x2(v[2].x, v[3].x, v[4].x),
-                           __vimin3_u16x2(v[5].x, v[6].x, v[7].x));
-    acc.y = __vimin3_u16x2(__vimin3_u16x2(acc.y, v[0].y, v[1].y), __vimin3_u16x2(v[2].y, v[3].y, v[4].y),
-                           __vimin3_u16x2(v[5].y, v[6].y, v[7].y));
-    acc.z = __vimin3_u16x2(__vimin3_u16x2(acc.z, v[0].z, v[1].z), __vimin3_u16x2(v[2].z, v[3].z, v[4].z),
-                           __vimin3_u16x2(v[5].z, v[6].z, v[7].z));
-    acc.w = __vimin3_u16x2(__vimin3_u16x2(acc.w, v[0].w, v[1].w), __vimin3_u16x2(v[2].w, v[3].w, v[4].w),
-                           __vimin3_u16x2(v[5].w, v[6].w, v[7].w));
 }
 
 // Shared memory of a step: the image (X, result, INF row), then the circuit,
@@ -168,16 +192,18 @@ constexpr uint32_t kMetaCopy = 32768;  // bytes per bulk copy of the circuit
 // is larger than the GPU's SMs, where one CTA's barrier waits then overlap
 // the other's work.  Otherwise the circuit is copied into shared memory.
 // The work of one CTA: column chunk bx of the chain (or step) a.
-template <bool kChain, bool kGBlob>
+// kW: columns per chunk, 8 (one 16-byte piece per image row) or 16 (two).
+template <bool kChain, bool kGBlob, int kW>
 __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
-    constexpr int RB = 2 * kCircW;  // bytes per image row
+    constexpr int RB = 2 * kW;  // bytes per image row
+    constexpr int NP = kW / 8;  // 16-byte pieces per image row
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t sbase = csmem_u32(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t N = a.N;
     const uint32_t Nh = (uint32_t)a.Nh, N2 = 2 * Nh;
-    const int64_t c0 = (int64_t)bx * kCircW;
-    const uint32_t mb = sbase + (uint32_t)circuit_image_bytes(Nh, kCircW);
+    const int64_t c0 = (int64_t)bx * kW;
+    const uint32_t mb = sbase + (uint32_t)circuit_image_bytes(Nh, kW);
 
     // The circuit: plan data only, so its bulk copies start before the
     // previous step has finished.  The barrier's initialisation is made
@@ -207,13 +233,15 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
     if (threadIdx.x < RB / 4) reinterpret_cast<uint32_t *>(smem + (size_t)N2 * RB)[threadIdx.x] = 0xFFFFFFFFu;
     // the row whose diagonal entry lies in column c0 + t (threads t < 8)
     uint32_t drow = 0xFFFFu;
-    if (a.gdiag && threadIdx.x < kCircW) drow = a.drow[c0 + threadIdx.x];
+    if (a.gdiag && threadIdx.x < kW) drow = a.drow[c0 + threadIdx.x];
     // Programmatic dependent launch: the previous step's output (our X) is
     // read only after its grid has completed.
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    // X's chunk: N rows of 16 bytes
+    // X's chunk: N rows of RB bytes
     for (int64_t r = threadIdx.x; r < N; r += kCircThreads)
-        ccp_async16(sbase + (uint32_t)r * RB, a.Bin + r * a.ldb + c0);
+#pragma unroll
+        for (int h = 0; h < NP; ++h)
+            ccp_async16(sbase + img_off<kW>((uint32_t)r, (uint32_t)h), a.Bin + r * a.ldb + c0 + 8 * h);
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
@@ -275,36 +303,51 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
                     info = slice_info(s);
                     e_c = slice_ents(s);
                 }
-                uint4 acc = make_uint4(kInf16x2, kInf16x2, kInf16x2, kInf16x2);
-                fold8<RB>(acc, e_c, sbase, N2, sh);
+                uint4 acc[NP];
+#pragma unroll
+                for (int h = 0; h < NP; ++h) acc[h] = make_uint4(kInf16x2, kInf16x2, kInf16x2, kInf16x2);
+                fold8<kW>(acc, e_c, sbase, N2, sh);
                 // the lanes of one row (an aligned group of 1 << lg) combine;
                 // the slice's widest row sits in lane 0
                 const uint32_t lg = (info >> 16) & 7u;
                 const uint32_t lg0 = __shfl_sync(0xFFFFFFFFu, lg, 0);
                 for (uint32_t o = 1; o < (1u << lg0); o <<= 1) {
-                    const uint32_t vx = __shfl_xor_sync(0xFFFFFFFFu, acc.x, o);
-                    const uint32_t vy = __shfl_xor_sync(0xFFFFFFFFu, acc.y, o);
-                    const uint32_t vz = __shfl_xor_sync(0xFFFFFFFFu, acc.z, o);
-                    const uint32_t vw = __shfl_xor_sync(0xFFFFFFFFu, acc.w, o);
-                    if (o < (1u << lg))
-                        acc = make_uint4(__vminu2(acc.x, vx), __vminu2(acc.y, vy), __vminu2(acc.z, vz),
-                                         __vminu2(acc.w, vw));
+#pragma unroll
+                    for (int h = 0; h < NP; ++h) {
+                        const uint32_t vx = __shfl_xor_sync(0xFFFFFFFFu, acc[h].x, o);
+                        const uint32_t vy = __shfl_xor_sync(0xFFFFFFFFu, acc[h].y, o);
+                        const uint32_t vz = __shfl_xor_sync(0xFFFFFFFFu, acc[h].z, o);
+                        const uint32_t vw = __shfl_xor_sync(0xFFFFFFFFu, acc[h].w, o);
+                        if (o < (1u << lg))
+                            acc[h] = make_uint4(__vminu2(acc[h].x, vx), __vminu2(acc[h].y, vy),
+                                                __vminu2(acc[h].z, vz), __vminu2(acc[h].w, vw));
+                    }
                 }
                 const uint32_t q = info & 0xFFFFu;
                 if (q == 0xFFFFu || (lane & ((1u << lg) - 1u)) != 0) continue;
                 // the result row, for the later levels (and the next step)
                 uint32_t rr = Nh + q + sh;
                 if (rr >= N2) rr -= N2;
-                csts_v4(sbase + rr * RB, acc);
+#pragma unroll
+                for (int h = 0; h < NP; ++h) csts_v4(sbase + img_off<kW>(rr, (uint32_t)h), acc[h]);
                 if (!kChain) {
                     const uint32_t zq = label(q) * 0x10001u;
-                    *reinterpret_cast<uint4 *>(a.Bout + (int64_t)q * a.ldb + c0) =
-                        make_uint4(acc.x + zq, acc.y + zq, acc.z + zq, acc.w + zq);
+#pragma unroll
+                    for (int h = 0; h < NP; ++h)
+                        *reinterpret_cast<uint4 *>(a.Bout + (int64_t)q * a.ldb + c0 + 8 * h) =
+                            make_uint4(acc[h].x + zq, acc[h].y + zq, acc[h].z + zq, acc[h].w + zq);
                 }
-                if (a.user_out)
-                    store_row8(a.user_out + (kChain ? (size_t)(k - a.out_k0) * a.slot : 0) +
-                                   (int64_t)a.caller[q] * N + c0,
-                               acc, N - c0);
+                if (a.user_out) {
+                    int16_t *dst = a.user_out + (kChain ? (size_t)(k - a.out_k0) * a.slot : 0) +
+                                   (int64_t)a.caller[q] * a.user_ld + c0;
+#pragma unroll
+                    for (int h = 0; h < NP; ++h) {
+                        if (a.user_ld % 8 == 0 && a.user_ld >= a.ldb)
+                            *reinterpret_cast<uint4 *>(dst + 8 * h) = acc[h];
+                        else
+                            store_row8(dst + 8 * h, acc[h], N - c0 - 8 * h);
+                    }
+                }
             }
             if (kGBlob) {
                 const int nl = l + 1 < a.levels ? l + 1 : 0;
@@ -333,9 +376,12 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
                     if (q >= (uint32_t)N) break;
                     uint32_t rr = Nh + q + sh;
                     if (rr >= N2) rr -= N2;
-                    const uint32_t addr = sbase + rr * RB;
-                    const uint4 v = clds_v4(addr);
-                    csts_v4(addr, make_uint4(v.x + zq[j], v.y + zq[j], v.z + zq[j], v.w + zq[j]));
+#pragma unroll
+                    for (int h = 0; h < NP; ++h) {
+                        const uint32_t addr = sbase + img_off<kW>(rr, (uint32_t)h);
+                        const uint4 v = clds_v4(addr);
+                        csts_v4(addr, make_uint4(v.x + zq[j], v.y + zq[j], v.z + zq[j], v.w + zq[j]));
+                    }
                 }
             }
             sh = Nh - sh;
@@ -345,10 +391,11 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
             // the diagonal entries of this chunk (unlabelled); the next step
             // writes only the other region, so nothing races with these reads
             int32_t v = (int32_t)kInf16;
-            if (lane < kCircW && drow != 0xFFFFu) {
+            if (lane < kW && drow != 0xFFFFu) {
                 uint32_t rr = Nh + drow + shr;
                 if (rr >= N2) rr -= N2;
-                const uint32_t w = clds_u32(sbase + rr * RB + 4u * (uint32_t)(lane >> 1));
+                const uint32_t w =
+                    clds_u32(sbase + img_off<kW>(rr, (uint32_t)lane >> 3) + 4u * (uint32_t)((lane & 7) >> 1));
                 v = (int32_t)((lane & 1) ? w >> 16 : w & 0xFFFFu);
                 if (kChain) v -= (int32_t)zdrow;
             }
@@ -360,9 +407,9 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-template <bool kChain, bool kGBlob>
-__global__ void __launch_bounds__(kCircThreads, kGBlob ? 2 : 1) circuit_step_kernel(CircArgs a) {
-    circuit_body<kChain, kGBlob>(a, (int)blockIdx.x);
+template <bool kChain, bool kGBlob, int kW>
+__global__ void __launch_bounds__(kCircThreads, kGBlob && kW == 8 ? 2 : 1) circuit_step_kernel(CircArgs a) {
+    circuit_body<kChain, kGBlob, kW>(a, (int)blockIdx.x);
 }
 
 // Several chains in one launch: the CTAs of chain i are blocks
@@ -379,14 +426,14 @@ struct MultiCircArgs {
     int count;
 };
 
-template <bool kGBlob>
-__global__ void __launch_bounds__(kCircThreads, kGBlob ? 2 : 1)
+template <bool kGBlob, int kW>
+__global__ void __launch_bounds__(kCircThreads, kGBlob && kW == 8 ? 2 : 1)
     circuit_multi_kernel(const __grid_constant__ MultiCircArgs m) {
     int ci = 0;
     while (ci + 1 < m.count && (int)blockIdx.x >= m.cta0[ci + 1]) ++ci;
     const int ctas = m.cta0[ci + 1] - m.cta0[ci];
     for (int bx = (int)blockIdx.x - m.cta0[ci]; bx < m.chunks[ci]; bx += ctas) {
-        circuit_body<true, kGBlob>(m.c[ci], bx);
+        circuit_body<true, kGBlob, kW>(m.c[ci], bx);
         __syncthreads();  // shared memory and the mbarrier are set up again for the next chunk
     }
 }
@@ -759,7 +806,8 @@ int circuit_upload(const CircuitHost &h, const std::vector<uint16_t> &z,
 }
 
 static int circuit_args(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int k_max, int16_t *user_out,
-                        size_t slot, int32_t *gdiag, uint32_t extra_tx, int out_k0, CircArgs *out) {
+                        size_t slot, int64_t user_ld, int32_t *gdiag, uint32_t extra_tx, int out_k0,
+                        CircArgs *out) {
     const CircuitDev &c = p.circuit;
     if (!c.ready) return set_error(MP_EINVAL, "plan has no circuit");
     if (p.narrow && user_out) return set_error(MP_EINVAL, "a narrow chain has no full powers to write");
@@ -780,6 +828,11 @@ static int circuit_args(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, i
     a.out_k0 = out_k0;
     a.user_out = user_out;
     a.slot = slot;
+    if (user_ld == 0) user_ld = p.N;
+    if (user_out && user_ld != p.N && (user_ld % 8 || user_ld < p.ldb))
+        return set_error(MP_EINVAL, "power rows of %lld entries: need N or a multiple of 8 >= %lld",
+                         (long long)user_ld, (long long)p.ldb);
+    a.user_ld = user_ld;
     a.caller = c.caller.as<int32_t>();
     a.drow = c.drow.as<uint16_t>();
     a.gdiag = gdiag;
@@ -823,23 +876,36 @@ static int circuit_kick(Kern kern, const Args &a, unsigned grid, size_t smem, cu
 // One launch: a step (Bin -> Bout) or a whole chain from Bin = P_1.
 static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uint16_t *Bout, int k_max,
                           int16_t *user_out, size_t slot, int32_t *gdiag, cudaStream_t s,
-                          uint32_t extra_tx = 0, int out_k0 = 1) {
+                          uint32_t extra_tx = 0, int out_k0 = 1, int64_t user_ld = 0) {
     DeviceInfo di;
     MP_TRY(device_info(&di));
     CircArgs a;
-    MP_TRY(circuit_args(p, Bin, Bout, k_max, user_out, slot, gdiag, extra_tx, out_k0, &a));
+    MP_TRY(circuit_args(p, Bin, Bout, k_max, user_out, slot, user_ld, gdiag, extra_tx, out_k0, &a));
     const CircuitDev &c = p.circuit;
     const unsigned grid = (unsigned)(p.ldb / kCircW);
     if (grid == 0) return MP_OK;
+    // A chain of more 8-column chunks than SMs runs on 16-column chunks, one
+    // CTA per SM with the circuit in global memory, where that image fits:
+    // the columns spread over the SMs more evenly than two 8-column CTAs to
+    // some SMs and one to others, and a lane's entry indices serve twice the
+    // columns.
+    const size_t wide = circuit_image_bytes(c.Nh, 16) + kCircBarBytes;
+    if (chain && !user_out && grid > (unsigned)di.sms && p.ldb % 16 == 0 && wide + 1024 <= di.smem_optin) {
+        auto *kern = circuit_step_kernel<true, true, 16>;
+        MP_TRY(circuit_attr(kern, 6, true, wide, di));
+        return circuit_kick(kern, a, (unsigned)(p.ldb / 16), wide, s);
+    }
     // the circuit in global memory where the grid is larger than the SMs and
-    // two images fit an SM (a chain writing full powers keeps one CTA per SM:
-    // its stores, not its barriers, bound it)
+    // two images fit an SM but not two images with their circuits (a chain
+    // writing full powers in rows of N entries keeps the circuit on chip:
+    // its narrow stores, not its barriers, bound it)
     const size_t image = circuit_image_bytes(c.Nh, kCircW) + kCircBarBytes;
-    const bool gblob = grid > (unsigned)di.sms && !user_out && 2 * (image + 1024) <= di.smem_sm;
+    const bool gblob = grid > (unsigned)di.sms && (!user_out || (a.user_ld % 8 == 0 && a.user_ld >= p.ldb)) &&
+                       2 * (image + 1024) <= di.smem_sm && 2 * (image + c.meta_bytes + 1024) > di.smem_sm;
     const size_t smem = image + (gblob ? 0 : c.meta_bytes);
     if (smem > di.smem_optin) return set_error(MP_EINVAL, "circuit does not fit shared memory");
-    auto *kern = gblob ? (chain ? circuit_step_kernel<true, true> : circuit_step_kernel<false, true>)
-                       : (chain ? circuit_step_kernel<true, false> : circuit_step_kernel<false, false>);
+    auto *kern = gblob ? (chain ? circuit_step_kernel<true, true, kCircW> : circuit_step_kernel<false, true, kCircW>)
+                       : (chain ? circuit_step_kernel<true, false, kCircW> : circuit_step_kernel<false, false, kCircW>);
     MP_TRY(circuit_attr(kern, (chain ? 1 : 0) + (gblob ? 2 : 0), gblob, smem, di));
     return circuit_kick(kern, a, grid, smem, s);
 }
@@ -853,23 +919,33 @@ int circuit_multi_chain(const PlanDev *const *plans, const uint16_t *const *B1, 
     MultiCircArgs m;
     memset(&m, 0, sizeof(m));
     m.count = count;
+    // 16-column chunks where the first (longest) chain has more 8-column
+    // chunks than the GPU has SMs and the widest image fits (as for one chain)
+    size_t wide_max = 0;
+    bool wide = plans[0]->ldb / kCircW > di.sms;
+    for (int i = 0; i < count; ++i) {
+        wide = wide && plans[i]->ldb % 16 == 0;
+        wide_max = std::max(wide_max, circuit_image_bytes(plans[i]->circuit.Nh, 16) + kCircBarBytes);
+    }
+    wide = wide && wide_max + 1024 <= di.smem_optin;
+    const int W = wide ? 16 : kCircW;
     size_t image_max = 0, meta_max = 0;
     int64_t total = 0;
     for (int i = 0; i < count; ++i) {
         const PlanDev &p = *plans[i];
-        MP_TRY(circuit_args(p, B1[i], nullptr, k_max, nullptr, 0, gdiag[i], 0, 1, &m.c[i]));
-        m.chunks[i] = (int)(p.ldb / kCircW);
+        MP_TRY(circuit_args(p, B1[i], nullptr, k_max, nullptr, 0, 0, gdiag[i], 0, 1, &m.c[i]));
+        m.chunks[i] = (int)(p.ldb / W);
         total += m.chunks[i];
-        image_max = std::max(image_max, circuit_image_bytes(p.circuit.Nh, kCircW) + kCircBarBytes);
-        meta_max = std::max(meta_max, (size_t)p.circuit.meta_bytes + circuit_image_bytes(p.circuit.Nh, kCircW) +
+        image_max = std::max(image_max, circuit_image_bytes(p.circuit.Nh, W) + kCircBarBytes);
+        meta_max = std::max(meta_max, (size_t)p.circuit.meta_bytes + circuit_image_bytes(p.circuit.Nh, W) +
                                           kCircBarBytes);
     }
     if (total == 0) return MP_OK;
-    const bool gblob = total > di.sms && 2 * (image_max + 1024) <= di.smem_sm;
+    const bool gblob = wide || (total > di.sms && 2 * (image_max + 1024) <= di.smem_sm);
     // The first chain takes one CTA per chunk, in as many waves of resident
     // CTAs as it needs (and room for one CTA of every other chain); the
     // others take the fewest chunks per CTA that fit them into those waves.
-    const int64_t slots = (int64_t)di.sms * (gblob ? 2 : 1);
+    const int64_t slots = (int64_t)di.sms * (gblob && 2 * (image_max + 1024) <= di.smem_sm ? 2 : 1);
     const int64_t room = (m.chunks[0] + count - 1 + slots - 1) / slots * slots;
     int f = 1;
     for (;;) {
@@ -887,7 +963,12 @@ int circuit_multi_chain(const PlanDev *const *plans, const uint16_t *const *B1, 
     const unsigned grid = (unsigned)m.cta0[count];
     const size_t smem = gblob ? image_max : meta_max;
     if (smem > di.smem_optin) return set_error(MP_EINVAL, "circuit does not fit shared memory");
-    auto *kern = gblob ? circuit_multi_kernel<true> : circuit_multi_kernel<false>;
+    if (wide) {
+        auto *kern = circuit_multi_kernel<true, 16>;
+        MP_TRY(circuit_attr(kern, 7, true, smem, di));
+        return circuit_kick(kern, m, grid, smem, s);
+    }
+    auto *kern = gblob ? circuit_multi_kernel<true, kCircW> : circuit_multi_kernel<false, kCircW>;
     MP_TRY(circuit_attr(kern, 4 + (gblob ? 1 : 0), gblob, smem, di));
     return circuit_kick(kern, m, grid, smem, s);
 }
@@ -906,10 +987,11 @@ int circuit_timeout_probe(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout,
 }
 
 int circuit_chain(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *powers, size_t slot,
-                  int32_t *gdiag, cudaStream_t s, int out_k0) {
+                  int32_t *gdiag, cudaStream_t s, int out_k0, int64_t powers_ld) {
     if (k_max < 2) return MP_OK;
-    if (powers && slot < (size_t)p.N * (size_t)p.N) return set_error(MP_EINVAL, "power slots too small");
-    return circuit_launch(p, true, B1, nullptr, k_max, powers, slot, gdiag, s, 0, out_k0);
+    const int64_t ld = powers_ld ? powers_ld : p.N;
+    if (powers && slot < (size_t)p.N * (size_t)ld) return set_error(MP_EINVAL, "power slots too small");
+    return circuit_launch(p, true, B1, nullptr, k_max, powers, slot, gdiag, s, 0, out_k0, ld);
 }
 
 }  // namespace mp

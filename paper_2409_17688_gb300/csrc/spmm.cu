@@ -415,6 +415,59 @@ __global__ void init_from_csr_kernel(const int64_t *__restrict__ row_ptr,
     }
 }
 
+// The 8 entries that start at entry R of the 16 held by x and y.
+template <int R>
+__device__ __forceinline__ uint4 entries_from(const uint4 &x, const uint4 &y) {
+    const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+    uint32_t o[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int e = R + 2 * j;
+        o[j] = (e & 1) ? __byte_perm(w[e >> 1], w[(e >> 1) + 1], 0x5432) : w[e >> 1];
+    }
+    return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
+// Powers staged in rows of src_ld entries (16-byte aligned) to rows of N
+// entries, which start at any 2-byte boundary: per row the entries before
+// the first 16-byte boundary of the destination one by one, then aligned
+// 16-byte stores, each made of two aligned 16-byte loads of the source
+// shifted by the row's offset, then the tail.  One row per block iteration.
+__global__ void repack_powers_kernel(const int16_t *__restrict__ src, int64_t src_ld, size_t src_slot,
+                                     int16_t *__restrict__ dst, size_t dst_slot, int64_t N, int64_t rows) {
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int64_t k = r / N, i = r - k * N;
+        const int16_t *a = src + (size_t)k * src_slot + (size_t)i * (size_t)src_ld;
+        int16_t *b = dst + (size_t)k * dst_slot + (size_t)i * (size_t)N;
+        const int64_t h0 = (int64_t)(((16 - ((uintptr_t)b & 15)) & 15) >> 1);
+        const int head = (int)(h0 < N ? h0 : N);
+        const int64_t nb = (N - head) / 8;
+        if ((int)threadIdx.x < head) b[threadIdx.x] = a[threadIdx.x];
+        for (int64_t t = head + nb * 8 + threadIdx.x; t < N; t += blockDim.x) b[t] = a[t];
+        const uint4 *a4 = reinterpret_cast<const uint4 *>(a);
+        uint4 *b4 = reinterpret_cast<uint4 *>(b + head);
+        // block q of the destination's aligned part takes source entries
+        // head + 8q .. head + 8q + 7: the end of source block q and the start
+        // of block q + 1 (read only where the shift needs it)
+        for (int64_t q = threadIdx.x; q < nb; q += blockDim.x) {
+            const uint4 x = a4[q];
+            const uint4 y = head ? a4[q + 1] : x;
+            uint4 v;
+            switch (head) {
+                case 0: v = x; break;
+                case 1: v = entries_from<1>(x, y); break;
+                case 2: v = entries_from<2>(x, y); break;
+                case 3: v = entries_from<3>(x, y); break;
+                case 4: v = entries_from<4>(x, y); break;
+                case 5: v = entries_from<5>(x, y); break;
+                case 6: v = entries_from<6>(x, y); break;
+                default: v = entries_from<7>(x, y); break;
+            }
+            b4[q] = v;
+        }
+    }
+}
+
 // The labelled buffer of a caller's power: internal row q (caller row
 // canon[q]), buffer column j (caller column colmap[j], or j), INF beyond the
 // kept columns; INF entries stay INF + z like the other initialisations.
@@ -631,6 +684,20 @@ int sparse_init_block_from_csr(const PlanDev &p, const int64_t *row_ptr, const i
                                               p.permuted ? p.canon.as<int32_t>() : nullptr,
                                               p.narrow ? p.colpos.as<int32_t>() : nullptr, B0, nullptr, g0,
                                               col_base);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+int launch_repack_powers(const int16_t *src, int64_t src_ld, size_t src_slot, int16_t *dst, size_t dst_slot,
+                         int64_t N, int count, cudaStream_t s) {
+    if (count < 1 || N < 1) return MP_OK;
+    if (src_ld < N || src_ld % 8 || ((uintptr_t)src & 15) || ((uintptr_t)dst & 1))
+        return set_error(MP_EINVAL, "repack needs 16-byte aligned source rows and a 2-byte aligned destination");
+    const int64_t rows = (int64_t)count * N;
+    DeviceInfo di;
+    MP_TRY(device_info(&di));
+    const unsigned grid = (unsigned)std::min<int64_t>(rows, (int64_t)di.sms * 8);
+    repack_powers_kernel<<<grid, 128, 0, s>>>(src, src_ld, src_slot, dst, dst_slot, N, rows);
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

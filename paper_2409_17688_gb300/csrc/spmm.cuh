@@ -270,9 +270,15 @@ int circuit_step(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int16_t 
 // step.  powers (optional): P_k at powers + (k - 1) * slot in the caller's
 // layout; gdiag (optional): g[k - 1] = min diag P_k, folded by atomicMin.
 // out_k0: P_k goes to powers slot k - out_k0 and gdiag[k - out_k0] (1 for a
-// chain from A itself).
+// chain from A itself).  powers_ld: entries between the rows of a power (0:
+// N; a multiple of 8 no smaller than the buffer's width makes every row piece
+// one aligned 16-byte store, the entries past N left as they come).
 int circuit_chain(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *powers, size_t slot,
-                  int32_t *gdiag, cudaStream_t s, int out_k0 = 1);
+                  int32_t *gdiag, cudaStream_t s, int out_k0 = 1, int64_t powers_ld = 0);
+// count N x N powers from rows of src_ld entries (src_slot between powers) to
+// rows of N entries (dst_slot between powers), one launch.
+int launch_repack_powers(const int16_t *src, int64_t src_ld, size_t src_slot, int16_t *dst, size_t dst_slot,
+                         int64_t N, int count, cudaStream_t s);
 // The global circuit (n >= 10): covers from the arc rule (words: the
 // caller's packed words; canon: internal row -> word), its warp tasks for
 // chunks of 8 L columns (z: labels of the internal rows), and the steps.
