@@ -432,8 +432,11 @@ __global__ void __launch_bounds__(kCircThreads, kGBlob && kW == 8 ? 2 : 1)
     int ci = 0;
     while (ci + 1 < m.count && (int)blockIdx.x >= m.cta0[ci + 1]) ++ci;
     const int ctas = m.cta0[ci + 1] - m.cta0[ci];
+    // this chain's arguments in registers: read through the chain index, every
+    // use in the step loops would be a load from the parameter space
+    const CircArgs a = m.c[ci];
     for (int bx = (int)blockIdx.x - m.cta0[ci]; bx < m.chunks[ci]; bx += ctas) {
-        circuit_body<true, kGBlob, kW>(m.c[ci], bx);
+        circuit_body<true, kGBlob, kW>(a, bx);
         __syncthreads();  // shared memory and the mbarrier are set up again for the next chunk
     }
 }
