@@ -161,9 +161,13 @@ int mp_minplus_power_sequence(const int16_t *A, int64_t N, int k_max,
  * the first call.  powers_opt / gdiag_opt as above with N = |C_n|.
  * Where a column chunk fits shared memory (n <= 9 on GB300) the chain runs
  * on the reuse circuit (mp_transfer_circuit_info) as one launch: each CTA
- * keeps an 8-column chunk of the powers on chip for every step.  Larger n
- * run one gather-plan launch per step.  The results are the same bit for
- * bit.  A repeated call with the same arguments is replayed from a CUDA
+ * keeps an 8- or 16-column chunk of the powers on chip for every step.
+ * Larger n run on the circuit in global memory.  The results are the same
+ * bit for bit.  With powers_opt the chain computes only the
+ * mirror-representative columns (see below) into a temporary staging area
+ * of about k_max * N * N bytes and one copy pass writes every power in full
+ * (P_k[R i][R c] = P_k[i][c] for the reversal R); without room for the
+ * staging area it computes every column and writes them itself.  A repeated call with the same arguments is replayed from a CUDA
  * graph captured on its second call; a capture that fails (for instance
  * because another host thread synchronised the whole device meanwhile) is
  * dropped and the chain runs directly.

@@ -136,6 +136,11 @@ struct TransferEntry {
     // for the shared-memory circuit chains (which only read their P_1)
     DevBuf p1_narrow, g1_narrow;
     bool have_p1_narrow = false;
+    // full powers from the narrow chain: per caller column c the buffer
+    // column holding P[i][c] (bit 31 set: column c's mirror, read in row
+    // R i), and per caller row i its mirror row R i
+    DevBuf mirror_col, mirror_row;
+    bool have_mirror = false;
 };
 
 // Lanes per row of the global circuit for a chain of `ncols` buffer columns:
@@ -370,8 +375,22 @@ static int narrow_plan(TransferEntry *te, cudaStream_t s, const PlanDev **out) {
         ph.colpos = colpos;
         MP_TRY(plan_upload(ph, &te->plan_narrow, s, true));
         MP_CUDA_TRY(cudaStreamSynchronize(s));
-        if (te->circuit.W > 0 && te->plan_narrow.ldb % kCircW == 0)
+        if (te->circuit.W > 0 && te->plan_narrow.ldb % kCircW == 0) {
             MP_TRY(circuit_upload(te->circuit, te->pz, dcol, te->canon, &te->plan_narrow, s));
+            std::vector<int32_t> mcol((size_t)N), mrow((size_t)N);
+            for (int64_t c = 0; c < N; ++c) {
+                const int64_t r = partner[(size_t)c];
+                mcol[(size_t)c] = colpos[(size_t)c] >= 0 ? colpos[(size_t)c]
+                                                          : (int32_t)(0x80000000u | (uint32_t)colpos[(size_t)r]);
+                mrow[(size_t)c] = (int32_t)r;
+            }
+            MP_TRY(te->mirror_col.alloc((size_t)N * 4, s, true));
+            MP_TRY(te->mirror_row.alloc((size_t)N * 4, s, true));
+            MP_CUDA_TRY(cudaMemcpyAsync(te->mirror_col.p, mcol.data(), (size_t)N * 4, cudaMemcpyHostToDevice, s));
+            MP_CUDA_TRY(cudaMemcpyAsync(te->mirror_row.p, mrow.data(), (size_t)N * 4, cudaMemcpyHostToDevice, s));
+            MP_CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors go out of scope
+            te->have_mirror = te->plan_narrow.circuit.ready;
+        }
         te->narrow_cols = ncols;
         te->have_narrow = true;
     }
@@ -592,10 +611,52 @@ static int transfer_chain_blocked(TransferEntry *te, const PlanDev &plan, int k_
     return MP_OK;
 }
 
+// Every power written in the caller's layout from the narrow chain: the
+// chain computes the mirror-representative columns (staged in rows of its
+// buffer's width), and since P_k[R i][R c] = P_k[i][c] one copy pass fills
+// each caller row i from staged rows i and R i.  Half the columns of the full
+// chain; returns MP_ENOMEM, having launched nothing, without room for the
+// staging area.
+static int transfer_chain_mirrored(TransferEntry *te, const PlanDev &np, int k_max, int16_t *powers,
+                                   size_t slot, int32_t *gdiag, cudaStream_t s) {
+    const uint16_t *p1;
+    const int32_t *g1;
+    MP_TRY(narrow_first_power(te, np, s, &p1, &g1));
+    const size_t spow = (size_t)np.N * (size_t)np.ldb;
+    // the staging area also takes, before the chain, the full plan's buffer
+    // that writing P_1 in the caller's layout fills on the way
+    const size_t elems = std::max(spow * (size_t)k_max, (size_t)te->plan.N * (size_t)te->plan.ldb);
+    void *stage = nullptr;
+    if (cudaMallocAsync(&stage, elems * 2, s) != cudaSuccess) {
+        cudaGetLastError();
+        return MP_ENOMEM;
+    }
+    int16_t *st = static_cast<int16_t *>(stage);
+    // P_1 = A in the caller's first slot
+    int rc = sparse_init_from_csr(te->plan, te->csr.row_ptr.as<int64_t>(), te->csr.col.as<int32_t>(),
+                                  te->csr.val.as<int16_t>(), reinterpret_cast<uint16_t *>(st), powers, nullptr, s);
+    if (rc == MP_OK && gdiag) rc = launch_gdiag_init(&gdiag, &g1, 1, k_max, s);
+    // P_k to staging slot k - 1, then to the caller's slot k - 1
+    if (rc == MP_OK) rc = circuit_chain(np, p1, k_max, st, spow, gdiag, s, 1, np.ldb);
+    if (rc == MP_OK)
+        rc = launch_mirror_repack(st + spow, np.ldb, spow, powers + slot, slot, te->mirror_col.as<int32_t>(),
+                                  te->mirror_row.as<int32_t>(), np.N, k_max - 1, s);
+    cudaFreeAsync(stage, s);
+    return rc;
+}
+
 static int transfer_chain_direct(TransferEntry *te, int k_max, int16_t *powers_opt, size_t slot,
                                  int32_t *gdiag_opt, cudaStream_t s) {
     // without powers to write, the narrow chain gives the same diagonals
     const PlanDev *pp = &te->plan;
+    if (powers_opt && k_max >= 2) {
+        const PlanDev *np = nullptr;
+        MP_TRY(narrow_plan(te, s, &np));
+        if (te->have_mirror) {
+            const int rc = transfer_chain_mirrored(te, *np, k_max, powers_opt, slot, gdiag_opt, s);
+            if (rc != MP_ENOMEM) return rc;
+        }
+    }
     if (!powers_opt) MP_TRY(narrow_plan(te, s, &pp));
     const PlanDev &plan = *pp;
     if (!powers_opt && plan.circuit.ready) {

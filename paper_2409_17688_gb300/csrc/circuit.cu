@@ -813,7 +813,8 @@ static int circuit_args(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, i
                         CircArgs *out) {
     const CircuitDev &c = p.circuit;
     if (!c.ready) return set_error(MP_EINVAL, "plan has no circuit");
-    if (p.narrow && user_out) return set_error(MP_EINVAL, "a narrow chain has no full powers to write");
+    if (p.narrow && user_out && (user_ld == 0 || user_ld == p.N))
+        return set_error(MP_EINVAL, "a narrow chain writes its powers in buffer columns only");
     CircArgs &a = *out;
     memset(&a, 0, sizeof(a));
     a.Bin = Bin;
@@ -893,7 +894,9 @@ static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uin
     // some SMs and one to others, and a lane's entry indices serve twice the
     // columns.
     const size_t wide = circuit_image_bytes(c.Nh, 16) + kCircBarBytes;
-    if (chain && !user_out && grid > (unsigned)di.sms && p.ldb % 16 == 0 && wide + 1024 <= di.smem_optin) {
+    const bool aligned_out = a.user_ld % 8 == 0 && a.user_ld >= p.ldb;  // staged rows: one store per piece
+    if (chain && (!user_out || aligned_out) && grid > (unsigned)di.sms && p.ldb % 16 == 0 &&
+        wide + 1024 <= di.smem_optin) {
         auto *kern = circuit_step_kernel<true, true, 16>;
         MP_TRY(circuit_attr(kern, 6, true, wide, di));
         return circuit_kick(kern, a, (unsigned)(p.ldb / 16), wide, s);
@@ -903,7 +906,7 @@ static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uin
     // writing full powers in rows of N entries keeps the circuit on chip:
     // its narrow stores, not its barriers, bound it)
     const size_t image = circuit_image_bytes(c.Nh, kCircW) + kCircBarBytes;
-    const bool gblob = grid > (unsigned)di.sms && (!user_out || (a.user_ld % 8 == 0 && a.user_ld >= p.ldb)) &&
+    const bool gblob = grid > (unsigned)di.sms && (!user_out || aligned_out) &&
                        2 * (image + 1024) <= di.smem_sm && 2 * (image + c.meta_bytes + 1024) > di.smem_sm;
     const size_t smem = image + (gblob ? 0 : c.meta_bytes);
     if (smem > di.smem_optin) return set_error(MP_EINVAL, "circuit does not fit shared memory");

@@ -468,6 +468,33 @@ __global__ void repack_powers_kernel(const int16_t *__restrict__ src, int64_t sr
     }
 }
 
+// Full powers from a narrow chain's staged rows: per output row the staged
+// row and its mirror row in shared memory (aligned 16-byte loads), then the
+// caller's row in column order, each entry from one of the two.
+__global__ void mirror_repack_kernel(const int16_t *__restrict__ src, int64_t src_ld, size_t src_slot,
+                                     int16_t *__restrict__ dst, size_t dst_slot, const int32_t *__restrict__ mcol,
+                                     const int32_t *__restrict__ mrow, int64_t N, int64_t rows) {
+    extern __shared__ __align__(16) int16_t srow[];  // [2 * src_ld]: row i, row R i
+    const int64_t n16 = src_ld / 8;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int64_t k = r / N, i = r - k * N;
+        const uint4 *a = reinterpret_cast<const uint4 *>(src + (size_t)k * src_slot + (size_t)i * (size_t)src_ld);
+        const uint4 *b =
+            reinterpret_cast<const uint4 *>(src + (size_t)k * src_slot + (size_t)mrow[i] * (size_t)src_ld);
+        __syncthreads();  // the previous row's reads are done
+        for (int64_t t = threadIdx.x; t < n16; t += blockDim.x) {
+            reinterpret_cast<uint4 *>(srow)[t] = a[t];
+            reinterpret_cast<uint4 *>(srow + src_ld)[t] = b[t];
+        }
+        __syncthreads();
+        int16_t *o = dst + (size_t)k * dst_slot + (size_t)i * (size_t)N;
+        for (int64_t c = threadIdx.x; c < N; c += blockDim.x) {
+            const int32_t m = mcol[c];
+            o[c] = m < 0 ? srow[src_ld + (m & 0x7FFFFFFF)] : srow[m];
+        }
+    }
+}
+
 // The labelled buffer of a caller's power: internal row q (caller row
 // canon[q]), buffer column j (caller column colmap[j], or j), INF beyond the
 // kept columns; INF entries stay INF + z like the other initialisations.
@@ -698,6 +725,21 @@ int launch_repack_powers(const int16_t *src, int64_t src_ld, size_t src_slot, in
     MP_TRY(device_info(&di));
     const unsigned grid = (unsigned)std::min<int64_t>(rows, (int64_t)di.sms * 8);
     repack_powers_kernel<<<grid, 128, 0, s>>>(src, src_ld, src_slot, dst, dst_slot, N, rows);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+int launch_mirror_repack(const int16_t *src, int64_t src_ld, size_t src_slot, int16_t *dst, size_t dst_slot,
+                         const int32_t *mcol, const int32_t *mrow, int64_t N, int count, cudaStream_t s) {
+    if (count < 1 || N < 1) return MP_OK;
+    const size_t smem = (size_t)src_ld * 4;
+    if (src_ld % 8 || ((uintptr_t)src & 15) || smem > 48 * 1024)
+        return set_error(MP_EINVAL, "mirror repack needs 16-byte aligned source rows of at most 6144 entries");
+    const int64_t rows = (int64_t)count * N;
+    DeviceInfo di;
+    MP_TRY(device_info(&di));
+    const unsigned grid = (unsigned)std::min<int64_t>(rows, (int64_t)di.sms * 8);
+    mirror_repack_kernel<<<grid, 256, smem, s>>>(src, src_ld, src_slot, dst, dst_slot, mcol, mrow, N, rows);
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

@@ -279,6 +279,12 @@ int circuit_chain(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *powe
 // rows of N entries (dst_slot between powers), one launch.
 int launch_repack_powers(const int16_t *src, int64_t src_ld, size_t src_slot, int16_t *dst, size_t dst_slot,
                          int64_t N, int count, cudaStream_t s);
+// count N x N powers from a narrow chain's staged rows (src_ld entries, the
+// buffer columns): row i, column c of power k is staged row i, column
+// mcol[c] of power k, or, where mcol[c] has bit 31 set, staged row mrow[i],
+// column mcol[c] & 0x7FFFFFFF (the reversal symmetry).  One launch.
+int launch_mirror_repack(const int16_t *src, int64_t src_ld, size_t src_slot, int16_t *dst, size_t dst_slot,
+                         const int32_t *mcol, const int32_t *mrow, int64_t N, int count, cudaStream_t s);
 // The global circuit (n >= 10): covers from the arc rule (words: the
 // caller's packed words; canon: internal row -> word), its warp tasks for
 // chunks of 8 L columns (z: labels of the internal rows), and the steps.
