@@ -138,8 +138,10 @@ struct TransferEntry {
     bool have_p1_narrow = false;
     // full powers from the narrow chain: per caller column c the buffer
     // column holding P[i][c] (bit 31 set: column c's mirror, read in row
-    // R i), and per caller row i its mirror row R i
-    DevBuf mirror_col, mirror_row;
+    // R i), per caller row i its mirror row R i and its internal row, and
+    // the rows i <= R i
+    DevBuf mirror_col, mirror_row, mirror_inv, mirror_lead;
+    int64_t mirror_nlead = 0;
     bool have_mirror = false;
 };
 
@@ -377,17 +379,24 @@ static int narrow_plan(TransferEntry *te, cudaStream_t s, const PlanDev **out) {
         MP_CUDA_TRY(cudaStreamSynchronize(s));
         if (te->circuit.W > 0 && te->plan_narrow.ldb % kCircW == 0) {
             MP_TRY(circuit_upload(te->circuit, te->pz, dcol, te->canon, &te->plan_narrow, s));
-            std::vector<int32_t> mcol((size_t)N), mrow((size_t)N);
+            std::vector<int32_t> mcol((size_t)N), mrow((size_t)N), inv((size_t)N), lead;
             for (int64_t c = 0; c < N; ++c) {
                 const int64_t r = partner[(size_t)c];
                 mcol[(size_t)c] = colpos[(size_t)c] >= 0 ? colpos[(size_t)c]
                                                           : (int32_t)(0x80000000u | (uint32_t)colpos[(size_t)r]);
                 mrow[(size_t)c] = (int32_t)r;
+                if (c <= r) lead.push_back((int32_t)c);
             }
+            for (int64_t q = 0; q < N; ++q) inv[(size_t)te->canon[(size_t)q]] = (int32_t)q;
             MP_TRY(te->mirror_col.alloc((size_t)N * 4, s, true));
             MP_TRY(te->mirror_row.alloc((size_t)N * 4, s, true));
+            MP_TRY(te->mirror_inv.alloc((size_t)N * 4, s, true));
+            MP_TRY(te->mirror_lead.alloc(lead.size() * 4, s, true));
             MP_CUDA_TRY(cudaMemcpyAsync(te->mirror_col.p, mcol.data(), (size_t)N * 4, cudaMemcpyHostToDevice, s));
             MP_CUDA_TRY(cudaMemcpyAsync(te->mirror_row.p, mrow.data(), (size_t)N * 4, cudaMemcpyHostToDevice, s));
+            MP_CUDA_TRY(cudaMemcpyAsync(te->mirror_inv.p, inv.data(), (size_t)N * 4, cudaMemcpyHostToDevice, s));
+            MP_CUDA_TRY(cudaMemcpyAsync(te->mirror_lead.p, lead.data(), lead.size() * 4, cudaMemcpyHostToDevice, s));
+            te->mirror_nlead = (int64_t)lead.size();
             MP_CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors go out of scope
             te->have_mirror = te->plan_narrow.circuit.ready;
         }
@@ -612,9 +621,10 @@ static int transfer_chain_blocked(TransferEntry *te, const PlanDev &plan, int k_
 }
 
 // Every power written in the caller's layout from the narrow chain: the
-// chain computes the mirror-representative columns (staged in rows of its
-// buffer's width), and since P_k[R i][R c] = P_k[i][c] one copy pass fills
-// each caller row i from staged rows i and R i.  Half the columns of the full
+// chain computes the mirror-representative columns and stages each power
+// chunk by chunk (its label pass writes consecutive rows, so the stores
+// coalesce), and since P_k[R i][R c] = P_k[i][c] one copy pass fills caller
+// rows i and R i from their two staged rows.  Half the columns of the full
 // chain; returns MP_ENOMEM, having launched nothing, without room for the
 // staging area.
 static int transfer_chain_mirrored(TransferEntry *te, const PlanDev &np, int k_max, int16_t *powers,
@@ -636,11 +646,13 @@ static int transfer_chain_mirrored(TransferEntry *te, const PlanDev &np, int k_m
     int rc = sparse_init_from_csr(te->plan, te->csr.row_ptr.as<int64_t>(), te->csr.col.as<int32_t>(),
                                   te->csr.val.as<int16_t>(), reinterpret_cast<uint16_t *>(st), powers, nullptr, s);
     if (rc == MP_OK && gdiag) rc = launch_gdiag_init(&gdiag, &g1, 1, k_max, s);
-    // P_k to staging slot k - 1, then to the caller's slot k - 1
-    if (rc == MP_OK) rc = circuit_chain(np, p1, k_max, st, spow, gdiag, s, 1, np.ldb);
+    // P_k to staging slot k - 1 (chunk by chunk), then to the caller's slot k - 1
+    int W = 0;
+    if (rc == MP_OK) rc = circuit_chain_staged(np, p1, k_max, st, spow, gdiag, s, &W);
     if (rc == MP_OK)
-        rc = launch_mirror_repack(st + spow, np.ldb, spow, powers + slot, slot, te->mirror_col.as<int32_t>(),
-                                  te->mirror_row.as<int32_t>(), np.N, k_max - 1, s);
+        rc = launch_mirror_repack(st + spow, W, np.ldb, spow, powers + slot, slot, te->mirror_col.as<int32_t>(),
+                                  te->mirror_row.as<int32_t>(), te->mirror_inv.as<int32_t>(),
+                                  te->mirror_lead.as<int32_t>(), te->mirror_nlead, np.N, k_max - 1, s);
     cudaFreeAsync(stage, s);
     return rc;
 }

@@ -120,6 +120,9 @@ struct CircArgs {
     int64_t user_ld;      // entries between rows of a power in user_out: N, or a
                           // multiple of 8 no smaller than ldb (then every piece is
                           // one aligned store, columns past N into the row's padding)
+    int chunk_major;      // a chain: user_out takes each power chunk by chunk, the
+                          // chunk's rows in the internal order, W entries each,
+                          // written by the label pass (consecutive rows: coalesced)
     const int32_t *caller;   // per internal row, the caller's row (for user_out)
     const uint16_t *drow;    // per buffer column, the row whose diagonal entry it holds
     int32_t *gdiag;       // one step: g[k]; a chain: g[0 .. k_max - 1]
@@ -193,7 +196,9 @@ constexpr uint32_t kMetaCopy = 32768;  // bytes per bulk copy of the circuit
 // the other's work.  Otherwise the circuit is copied into shared memory.
 // The work of one CTA: column chunk bx of the chain (or step) a.
 // kW: columns per chunk, 8 (one 16-byte piece per image row) or 16 (two).
-template <bool kChain, bool kGBlob, int kW>
+// kOut: the code that writes powers (to the caller or a staging area) is
+// compiled in (the multi-chain kernel writes none).
+template <bool kChain, bool kGBlob, int kW, bool kOut = true>
 __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
     constexpr int RB = 2 * kW;  // bytes per image row
     constexpr int NP = kW / 8;  // 16-byte pieces per image row
@@ -337,7 +342,7 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
                         *reinterpret_cast<uint4 *>(a.Bout + (int64_t)q * a.ldb + c0 + 8 * h) =
                             make_uint4(acc[h].x + zq, acc[h].y + zq, acc[h].z + zq, acc[h].w + zq);
                 }
-                if (a.user_out) {
+                if (kOut && a.user_out && !(kChain && a.chunk_major)) {
                     int16_t *dst = a.user_out + (kChain ? (size_t)(k - a.out_k0) * a.slot : 0) +
                                    (int64_t)a.caller[q] * a.user_ld + c0;
 #pragma unroll
@@ -362,7 +367,11 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
         const uint32_t shr = sh;  // where this step's result rows are
         if (kChain) {
             // the labels, in place: the result becomes the next step's X (the
-            // labels of four rows per thread loaded before their rows)
+            // labels of four rows per thread loaded before their rows); a
+            // chain staging its powers chunk by chunk writes each row first
+            int16_t *stage = (kOut && a.user_out && a.chunk_major)
+                                 ? a.user_out + (size_t)(k - a.out_k0) * a.slot + (size_t)bx * (size_t)N * kW
+                                 : nullptr;
             for (uint32_t q0 = threadIdx.x; q0 < (uint32_t)N; q0 += 4 * kCircThreads) {
                 uint32_t zq[4];
 #pragma unroll
@@ -380,6 +389,7 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
                     for (int h = 0; h < NP; ++h) {
                         const uint32_t addr = sbase + img_off<kW>(rr, (uint32_t)h);
                         const uint4 v = clds_v4(addr);
+                        if (stage) *reinterpret_cast<uint4 *>(stage + (size_t)q * kW + 8 * h) = v;
                         csts_v4(addr, make_uint4(v.x + zq[j], v.y + zq[j], v.z + zq[j], v.w + zq[j]));
                     }
                 }
@@ -436,7 +446,7 @@ __global__ void __launch_bounds__(kCircThreads, kGBlob && kW == 8 ? 2 : 1)
     // use in the step loops would be a load from the parameter space
     const CircArgs a = m.c[ci];
     for (int bx = (int)blockIdx.x - m.cta0[ci]; bx < m.chunks[ci]; bx += ctas) {
-        circuit_body<true, kGBlob, kW>(a, bx);
+        circuit_body<true, kGBlob, kW, false>(a, bx);
         __syncthreads();  // shared memory and the mbarrier are set up again for the next chunk
     }
 }
@@ -810,7 +820,7 @@ int circuit_upload(const CircuitHost &h, const std::vector<uint16_t> &z,
 
 static int circuit_args(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, int k_max, int16_t *user_out,
                         size_t slot, int64_t user_ld, int32_t *gdiag, uint32_t extra_tx, int out_k0,
-                        CircArgs *out) {
+                        CircArgs *out, bool chunk_major = false) {
     const CircuitDev &c = p.circuit;
     if (!c.ready) return set_error(MP_EINVAL, "plan has no circuit");
     if (p.narrow && user_out && (user_ld == 0 || user_ld == p.N))
@@ -837,6 +847,9 @@ static int circuit_args(const PlanDev &p, const uint16_t *Bin, uint16_t *Bout, i
         return set_error(MP_EINVAL, "power rows of %lld entries: need N or a multiple of 8 >= %lld",
                          (long long)user_ld, (long long)p.ldb);
     a.user_ld = user_ld;
+    a.chunk_major = chunk_major ? 1 : 0;
+    if (chunk_major && (!user_out || slot < (size_t)p.N * (size_t)p.ldb))
+        return set_error(MP_EINVAL, "chunk-major staging needs N x ldb entries per power");
     a.caller = c.caller.as<int32_t>();
     a.drow = c.drow.as<uint16_t>();
     a.gdiag = gdiag;
@@ -880,11 +893,13 @@ static int circuit_kick(Kern kern, const Args &a, unsigned grid, size_t smem, cu
 // One launch: a step (Bin -> Bout) or a whole chain from Bin = P_1.
 static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uint16_t *Bout, int k_max,
                           int16_t *user_out, size_t slot, int32_t *gdiag, cudaStream_t s,
-                          uint32_t extra_tx = 0, int out_k0 = 1, int64_t user_ld = 0) {
+                          uint32_t extra_tx = 0, int out_k0 = 1, int64_t user_ld = 0, int *width = nullptr) {
     DeviceInfo di;
     MP_TRY(device_info(&di));
     CircArgs a;
-    MP_TRY(circuit_args(p, Bin, Bout, k_max, user_out, slot, user_ld, gdiag, extra_tx, out_k0, &a));
+    const bool chunk_major = width != nullptr;
+    MP_TRY(circuit_args(p, Bin, Bout, k_max, user_out, slot, user_ld, gdiag, extra_tx, out_k0, &a, chunk_major));
+    if (chunk_major && !chain) return set_error(MP_EINVAL, "chunk-major staging is for chains");
     const CircuitDev &c = p.circuit;
     const unsigned grid = (unsigned)(p.ldb / kCircW);
     if (grid == 0) return MP_OK;
@@ -899,6 +914,7 @@ static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uin
         wide + 1024 <= di.smem_optin) {
         auto *kern = circuit_step_kernel<true, true, 16>;
         MP_TRY(circuit_attr(kern, 6, true, wide, di));
+        if (width) *width = 16;
         return circuit_kick(kern, a, (unsigned)(p.ldb / 16), wide, s);
     }
     // the circuit in global memory where the grid is larger than the SMs and
@@ -913,6 +929,7 @@ static int circuit_launch(const PlanDev &p, bool chain, const uint16_t *Bin, uin
     auto *kern = gblob ? (chain ? circuit_step_kernel<true, true, kCircW> : circuit_step_kernel<false, true, kCircW>)
                        : (chain ? circuit_step_kernel<true, false, kCircW> : circuit_step_kernel<false, false, kCircW>);
     MP_TRY(circuit_attr(kern, (chain ? 1 : 0) + (gblob ? 2 : 0), gblob, smem, di));
+    if (width) *width = kCircW;
     return circuit_kick(kern, a, grid, smem, s);
 }
 
@@ -998,6 +1015,12 @@ int circuit_chain(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *powe
     const int64_t ld = powers_ld ? powers_ld : p.N;
     if (powers && slot < (size_t)p.N * (size_t)ld) return set_error(MP_EINVAL, "power slots too small");
     return circuit_launch(p, true, B1, nullptr, k_max, powers, slot, gdiag, s, 0, out_k0, ld);
+}
+
+int circuit_chain_staged(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *stage, size_t slot,
+                         int32_t *gdiag, cudaStream_t s, int *width) {
+    if (k_max < 2) return MP_OK;
+    return circuit_launch(p, true, B1, nullptr, k_max, stage, slot, gdiag, s, 0, 1, p.ldb, width);
 }
 
 }  // namespace mp

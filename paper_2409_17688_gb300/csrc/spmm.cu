@@ -468,29 +468,37 @@ __global__ void repack_powers_kernel(const int16_t *__restrict__ src, int64_t sr
     }
 }
 
-// Full powers from a narrow chain's staged rows: per output row the staged
-// row and its mirror row in shared memory (aligned 16-byte loads), then the
-// caller's row in column order, each entry from one of the two.
-__global__ void mirror_repack_kernel(const int16_t *__restrict__ src, int64_t src_ld, size_t src_slot,
+// Full powers from a narrow chain's chunk-major staging: per pair {i, R i}
+// of caller rows the two staged rows gathered into shared memory (16-byte
+// pieces, a row's W entries of one chunk contiguous), then both caller rows
+// in column order, each entry from one of the two.
+__global__ void mirror_repack_kernel(const int16_t *__restrict__ src, int W, int64_t ldb, size_t src_slot,
                                      int16_t *__restrict__ dst, size_t dst_slot, const int32_t *__restrict__ mcol,
-                                     const int32_t *__restrict__ mrow, int64_t N, int64_t rows) {
-    extern __shared__ __align__(16) int16_t srow[];  // [2 * src_ld]: row i, row R i
-    const int64_t n16 = src_ld / 8;
-    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-        const int64_t k = r / N, i = r - k * N;
-        const uint4 *a = reinterpret_cast<const uint4 *>(src + (size_t)k * src_slot + (size_t)i * (size_t)src_ld);
-        const uint4 *b =
-            reinterpret_cast<const uint4 *>(src + (size_t)k * src_slot + (size_t)mrow[i] * (size_t)src_ld);
-        __syncthreads();  // the previous row's reads are done
-        for (int64_t t = threadIdx.x; t < n16; t += blockDim.x) {
-            reinterpret_cast<uint4 *>(srow)[t] = a[t];
-            reinterpret_cast<uint4 *>(srow + src_ld)[t] = b[t];
+                                     const int32_t *__restrict__ mrow, const int32_t *__restrict__ inv,
+                                     const int32_t *__restrict__ lead, int64_t nlead, int64_t N, int64_t units) {
+    extern __shared__ __align__(16) int16_t srow[];  // [2 * ldb]: staged rows of i and of R i
+    const int64_t pieces = ldb / 8, ppc = W / 8;     // 16-byte pieces per row, per chunk row
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int64_t k = u / nlead, i = lead[u - k * nlead], ri = mrow[i];
+        const int16_t *base = src + (size_t)k * src_slot;
+        const int64_t qa = inv[i], qb = inv[ri];
+        __syncthreads();  // the previous pair's reads are done
+        for (int64_t t = threadIdx.x; t < 2 * pieces; t += blockDim.x) {
+            const int64_t pc = t < pieces ? t : t - pieces, q = t < pieces ? qa : qb;
+            const int64_t ch = pc / ppc, h = pc - ch * ppc;
+            reinterpret_cast<uint4 *>(srow)[t] =
+                *reinterpret_cast<const uint4 *>(base + (size_t)ch * (size_t)N * W + (size_t)q * W + 8 * h);
         }
         __syncthreads();
-        int16_t *o = dst + (size_t)k * dst_slot + (size_t)i * (size_t)N;
+        int16_t *oa = dst + (size_t)k * dst_slot + (size_t)i * (size_t)N;
+        int16_t *ob = dst + (size_t)k * dst_slot + (size_t)ri * (size_t)N;
         for (int64_t c = threadIdx.x; c < N; c += blockDim.x) {
             const int32_t m = mcol[c];
-            o[c] = m < 0 ? srow[src_ld + (m & 0x7FFFFFFF)] : srow[m];
+            const int64_t j = m & 0x7FFFFFFF;
+            // row i: a kept column from its own row, a mirrored one from row R i;
+            // row R i the other way round
+            oa[c] = m < 0 ? srow[ldb + j] : srow[j];
+            if (ri != i) ob[c] = m < 0 ? srow[j] : srow[ldb + j];
         }
     }
 }
@@ -729,17 +737,20 @@ int launch_repack_powers(const int16_t *src, int64_t src_ld, size_t src_slot, in
     return MP_OK;
 }
 
-int launch_mirror_repack(const int16_t *src, int64_t src_ld, size_t src_slot, int16_t *dst, size_t dst_slot,
-                         const int32_t *mcol, const int32_t *mrow, int64_t N, int count, cudaStream_t s) {
-    if (count < 1 || N < 1) return MP_OK;
-    const size_t smem = (size_t)src_ld * 4;
-    if (src_ld % 8 || ((uintptr_t)src & 15) || smem > 48 * 1024)
-        return set_error(MP_EINVAL, "mirror repack needs 16-byte aligned source rows of at most 6144 entries");
-    const int64_t rows = (int64_t)count * N;
+int launch_mirror_repack(const int16_t *src, int W, int64_t ldb, size_t src_slot, int16_t *dst, size_t dst_slot,
+                         const int32_t *mcol, const int32_t *mrow, const int32_t *inv, const int32_t *lead,
+                         int64_t nlead, int64_t N, int count, cudaStream_t s) {
+    if (count < 1 || N < 1 || nlead < 1) return MP_OK;
+    const size_t smem = (size_t)ldb * 4;
+    if ((W != 8 && W != 16) || ldb % W || ((uintptr_t)src & 15) || smem > 48 * 1024 ||
+        src_slot < (size_t)N * (size_t)ldb)
+        return set_error(MP_EINVAL, "mirror repack needs aligned chunks of 8 or 16 columns, rows of at most 6144");
+    const int64_t units = (int64_t)count * nlead;
     DeviceInfo di;
     MP_TRY(device_info(&di));
-    const unsigned grid = (unsigned)std::min<int64_t>(rows, (int64_t)di.sms * 8);
-    mirror_repack_kernel<<<grid, 256, smem, s>>>(src, src_ld, src_slot, dst, dst_slot, mcol, mrow, N, rows);
+    const unsigned grid = (unsigned)std::min<int64_t>(units, (int64_t)di.sms * 8);
+    mirror_repack_kernel<<<grid, 256, smem, s>>>(src, W, ldb, src_slot, dst, dst_slot, mcol, mrow, inv, lead, nlead,
+                                                 N, units);
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

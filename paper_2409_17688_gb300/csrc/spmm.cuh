@@ -279,12 +279,21 @@ int circuit_chain(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *powe
 // rows of N entries (dst_slot between powers), one launch.
 int launch_repack_powers(const int16_t *src, int64_t src_ld, size_t src_slot, int16_t *dst, size_t dst_slot,
                          int64_t N, int count, cudaStream_t s);
-// count N x N powers from a narrow chain's staged rows (src_ld entries, the
-// buffer columns): row i, column c of power k is staged row i, column
-// mcol[c] of power k, or, where mcol[c] has bit 31 set, staged row mrow[i],
-// column mcol[c] & 0x7FFFFFFF (the reversal symmetry).  One launch.
-int launch_mirror_repack(const int16_t *src, int64_t src_ld, size_t src_slot, int16_t *dst, size_t dst_slot,
-                         const int32_t *mcol, const int32_t *mrow, int64_t N, int count, cudaStream_t s);
+// A chain staging its powers chunk by chunk (P_k in stage slot k - 1, slot
+// >= N x ldb entries): each power is ldb / W chunks of N rows (internal
+// order) of W entries, written by the label pass; *width receives W.
+int circuit_chain_staged(const PlanDev &p, const uint16_t *B1, int k_max, int16_t *stage, size_t slot,
+                         int32_t *gdiag, cudaStream_t s, int *width);
+// count N x N powers from a narrow chain's chunk-major staging (chunks of W
+// buffer columns, N internal rows each, src_slot between powers): caller row
+// i, column c of power k is internal row inv[i], buffer column mcol[c], or,
+// where mcol[c] has bit 31 set, internal row inv[mrow[i]], buffer column
+// mcol[c] & 0x7FFFFFFF (the reversal symmetry).  lead[0 .. nlead) are the
+// rows i <= mrow[i]: each pair {i, mrow[i]} is written from its two staged
+// rows, read once.  One launch.
+int launch_mirror_repack(const int16_t *src, int W, int64_t ldb, size_t src_slot, int16_t *dst, size_t dst_slot,
+                         const int32_t *mcol, const int32_t *mrow, const int32_t *inv, const int32_t *lead,
+                         int64_t nlead, int64_t N, int count, cudaStream_t s);
 // The global circuit (n >= 10): covers from the arc rule (words: the
 // caller's packed words; canon: internal row -> word), its warp tasks for
 // chunks of 8 L columns (z: labels of the internal rows), and the steps.
