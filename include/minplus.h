@@ -50,6 +50,8 @@ extern "C" {
 #define MP_ENOTREADY -8 /* a polled server ticket has not finished yet          */
 #define MP_EIO -9      /* a file cannot be read or written, or is not a checkpoint
                           of this library's powers                            */
+#define MP_ECHECK -10  /* a bounds-checked build (compiled with -DMP_CHECK)
+                          caught an index outside its buffer                  */
 
 /* ---- element types ----------------------------------------------------- */
 #define MP_I16 0 /* int16 entries in [0, 0x7FFF], INF = 0x7FFF */
@@ -432,7 +434,11 @@ int mp_inject_circuit_timeout(int n, void *stream);
 
 /* ---- device status and errors --------------------------------------------
  * mp_device_status synchronizes the current device, then returns MP_OK or
- * the first latched device-side error (MP_ETIMEOUT) and clears it. */
+ * the first latched device-side error (MP_ETIMEOUT; MP_ECHECK in a build
+ * compiled with -DMP_CHECK, whose circuit kernels check every shared- and
+ * global-memory index they compute, latch MP_ECHECK on one outside its
+ * buffer and use index 0 instead, so the access stays in bounds) and clears
+ * it. */
 int mp_device_status(void);
 const char *mp_last_error(void);
 

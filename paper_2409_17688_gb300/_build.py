@@ -12,6 +12,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libminplus.so")
+# the bounds-checked variant (-DMP_CHECK): every index the circuit kernels
+# compute is checked; a bad one latches MP_ECHECK and is replaced by 0
+OBJ_CHECK = os.path.join(PKG, "_build_check")
+LIB_CHECK = os.path.join(PKG, "libminplus_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
@@ -30,21 +34,24 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build_library(force: bool = False, verbose: bool = False) -> str:
-    """Compile every csrc/*.cu in parallel and link the shared library."""
-    os.makedirs(OBJ, exist_ok=True)
+def build_library(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Compile every csrc/*.cu in parallel and link the shared library (check:
+    the bounds-checked variant, libminplus_check.so)."""
+    obj_dir, lib = (OBJ_CHECK, LIB_CHECK) if check else (OBJ, LIB)
+    flags = FLAGS + (["-DMP_CHECK"] if check else [])
+    os.makedirs(obj_dir, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "minplus.h")]
     nvcc = _nvcc()
     jobs = []
     for src in sources:
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + headers):
             jobs.append((src, obj))
 
     def compile_one(job):
         src, obj = job
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj + ".tmp"]
+        cmd = [nvcc, *ARCH, *flags, "-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
@@ -56,15 +63,15 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
             for out in ex.map(compile_one, jobs):
                 if verbose and out:
                     print(out)
-    objs = [os.path.join(OBJ, os.path.basename(s)[:-3] + ".o") for s in sources]
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    objs = [os.path.join(obj_dir, os.path.basename(s)[:-3] + ".o") for s in sources]
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -1552,7 +1552,8 @@ int mp_device_status(void) {
     MP_CUDA_TRY(cudaMemcpy(&v, st->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (v != 0) {
         MP_CUDA_TRY(cudaMemset(st->status, 0, sizeof(int)));
-        return set_error(v, "a device-side bounded wait ran out");
+        return set_error(v, v == MP_ECHECK ? "a bounds check caught an index outside its buffer"
+                                           : "a device-side bounded wait ran out");
     }
     return MP_OK;
 }

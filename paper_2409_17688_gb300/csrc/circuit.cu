@@ -146,7 +146,7 @@ __device__ __forceinline__ uint32_t img_off(uint32_t j, uint32_t h) {
 // load nothing, the others live at image row (index + sh) mod 2Nh.
 template <int kW>
 __device__ __forceinline__ void fold8(uint4 (&acc)[kW / 8], const uint4 &e, uint32_t rbase, uint32_t N2,
-                                      uint32_t sh) {
+                                      uint32_t sh, int *status) {
     const uint32_t ix[8] = {e.x & 0xFFFFu, e.x >> 16, e.y & 0xFFFFu, e.y >> 16,
                             e.z & 0xFFFFu, e.z >> 16, e.w & 0xFFFFu, e.w >> 16};
     uint32_t jj[8];
@@ -158,7 +158,7 @@ __device__ __forceinline__ void fold8(uint4 (&acc)[kW / 8], const uint4 &e, uint
             if (h == 0) {
                 uint32_t j = ix[k] + sh;
                 if (j >= N2) j -= N2;
-                jj[k] = j;
+                jj[k] = ix[k] != N2 ? mp_ix(j, N2, status) : 0u;
             }
             v[k] = ix[k] != N2 ? clds_v4(rbase + img_off<kW>(jj[k], (uint32_t)h)) : make_uint4(~0u, ~0u, ~0u, ~0u);
         }
@@ -238,7 +238,7 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
     if (threadIdx.x < RB / 4) reinterpret_cast<uint32_t *>(smem + (size_t)N2 * RB)[threadIdx.x] = 0xFFFFFFFFu;
     // the row whose diagonal entry lies in column c0 + t (threads t < 8)
     uint32_t drow = 0xFFFFu;
-    if (a.gdiag && threadIdx.x < kW) drow = a.drow[c0 + threadIdx.x];
+    if (a.gdiag && threadIdx.x < kW) drow = a.drow[mp_ix(c0 + (int64_t)threadIdx.x, a.ldb, a.status)];
     // Programmatic dependent launch: the previous step's output (our X) is
     // read only after its grid has completed.
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -246,7 +246,8 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
     for (int64_t r = threadIdx.x; r < N; r += kCircThreads)
 #pragma unroll
         for (int h = 0; h < NP; ++h)
-            ccp_async16(sbase + img_off<kW>((uint32_t)r, (uint32_t)h), a.Bin + r * a.ldb + c0 + 8 * h);
+            ccp_async16(sbase + img_off<kW>((uint32_t)r, (uint32_t)h),
+                        a.Bin + r * a.ldb + mp_ix(c0 + 8 * h, a.ldb - 7, a.status));
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
@@ -265,15 +266,19 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
     const uint4 *g_ents = reinterpret_cast<const uint4 *>(a.meta + a.off_ents);
     const uint16_t *g_z = reinterpret_cast<const uint16_t *>(a.meta + a.off_z);
     auto label = [&](uint32_t q) {
+        q = mp_ix(q, (uint32_t)N, a.status);
         if (kGBlob) return (uint32_t)__ldg(g_z + q);
         const uint32_t zw = clds_u32(m_z + 4u * (q >> 1));
         return (q & 1) ? zw >> 16 : zw & 0xFFFFu;
     };
     auto level_start = [&](int l) { return kGBlob ? (int)__ldg(g_lvl + l) : (int)clds_u32(mb + 4u * (uint32_t)l); };
+    const int nsl = level_start(a.levels);  // warp slices of the circuit
     auto slice_info = [&](int sl) {
+        sl = mp_ix(sl, nsl, a.status);
         return kGBlob ? __ldg(g_info + (size_t)sl * 32 + lane) : clds_u32(m_info + 4u * ((uint32_t)sl * 32u + (uint32_t)lane));
     };
     auto slice_ents = [&](int sl) {
+        sl = mp_ix(sl, nsl, a.status);
         return kGBlob ? __ldg(g_ents + (size_t)sl * 32 + lane) : clds_v4(m_en + 16u * ((uint32_t)sl * 32u + (uint32_t)lane));
     };
     // the label of the row whose diagonal entry lies in this thread's column
@@ -311,7 +316,7 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
                 uint4 acc[NP];
 #pragma unroll
                 for (int h = 0; h < NP; ++h) acc[h] = make_uint4(kInf16x2, kInf16x2, kInf16x2, kInf16x2);
-                fold8<kW>(acc, e_c, sbase, N2, sh);
+                fold8<kW>(acc, e_c, sbase, N2, sh, a.status);
                 // the lanes of one row (an aligned group of 1 << lg) combine;
                 // the slice's widest row sits in lane 0
                 const uint32_t lg = (info >> 16) & 7u;
@@ -333,6 +338,7 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
                 // the result row, for the later levels (and the next step)
                 uint32_t rr = Nh + q + sh;
                 if (rr >= N2) rr -= N2;
+                rr = mp_ix(rr, N2, a.status);
 #pragma unroll
                 for (int h = 0; h < NP; ++h) csts_v4(sbase + img_off<kW>(rr, (uint32_t)h), acc[h]);
                 if (!kChain) {
@@ -344,7 +350,7 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
                 }
                 if (kOut && a.user_out && !(kChain && a.chunk_major)) {
                     int16_t *dst = a.user_out + (kChain ? (size_t)(k - a.out_k0) * a.slot : 0) +
-                                   (int64_t)a.caller[q] * a.user_ld + c0;
+                                   (int64_t)mp_ix((int64_t)a.caller[q], N, a.status) * a.user_ld + c0;
 #pragma unroll
                     for (int h = 0; h < NP; ++h) {
                         if (a.user_ld % 8 == 0 && a.user_ld >= a.ldb)
@@ -385,6 +391,7 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
                     if (q >= (uint32_t)N) break;
                     uint32_t rr = Nh + q + sh;
                     if (rr >= N2) rr -= N2;
+                    rr = mp_ix(rr, N2, a.status);
 #pragma unroll
                     for (int h = 0; h < NP; ++h) {
                         const uint32_t addr = sbase + img_off<kW>(rr, (uint32_t)h);
@@ -404,6 +411,7 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
             if (lane < kW && drow != 0xFFFFu) {
                 uint32_t rr = Nh + drow + shr;
                 if (rr >= N2) rr -= N2;
+                rr = mp_ix(rr, N2, a.status);
                 const uint32_t w =
                     clds_u32(sbase + img_off<kW>(rr, (uint32_t)lane >> 3) + 4u * (uint32_t)((lane & 7) >> 1));
                 v = (int32_t)((lane & 1) ? w >> 16 : w & 0xFFFFu);

@@ -59,19 +59,21 @@ struct GArgs {
     int16_t *user_out;
     size_t slot;
     int32_t *gdiag;
+    uint32_t nents4;      // blocks of four entries (bounds-checked builds)
+    int *status;
 };
 
 // The 16 bytes an entry names (all ones for padding: above every value, so
 // it never lowers a minimum) and the label to add.
 __device__ __forceinline__ void gload(uint32_t e, const uint16_t *X, const uint16_t *R, int64_t ldb,
-                                      int64_t col, uint4 &v, uint32_t &zz) {
+                                      int64_t col, uint4 &v, uint32_t &zz, int64_t N, int *status) {
     if (e & kGPad) {
         v = make_uint4(~0u, ~0u, ~0u, ~0u);
         zz = 0;
         return;
     }
     const bool cov = (e & kGCover) != 0;
-    const int64_t row = (int64_t)(e & kGRow);
+    const int64_t row = mp_ix((int64_t)(e & kGRow), N, status);
     v = *reinterpret_cast<const uint4 *>((cov ? R : X) + row * ldb + col);
     zz = cov ? 0u : ((e >> 24) & 0xFu) * 0x10001u;
 }
@@ -96,6 +98,7 @@ __global__ void __launch_bounds__(kGThreads, 2) gcircuit_kernel(GArgs a) {
     // the row whose diagonal entry lies in column cb + t (threads t < W)
     uint32_t drow = 0xFFFFFFFFu;
     if (a.gdiag && threadIdx.x < W) drow = a.drow[a.col_base + cb + threadIdx.x];
+    if (drow != 0xFFFFFFFFu) drow = mp_ix(drow, (uint32_t)N, a.status);
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint16_t *X = a.B0;
     uint16_t *R = a.B1;
@@ -110,21 +113,22 @@ __global__ void __launch_bounds__(kGThreads, 2) gcircuit_kernel(GArgs a) {
                 // loads are in flight per lane
                 const uint4 pad4 = make_uint4(kGPad, kGPad, kGPad, kGPad);
                 for (uint32_t e4 = 0; e4 < d.w; e4 += 2) {
-                    const uint4 ea = e4 < d.z ? a.ents[d.y + e4] : pad4;
-                    const uint4 eb = e4 + 1 < d.z ? a.ents[d.y + e4 + 1] : pad4;
+                    const uint4 ea = e4 < d.z ? a.ents[mp_ix(d.y + e4, a.nents4, a.status)] : pad4;
+                    const uint4 eb = e4 + 1 < d.z ? a.ents[mp_ix(d.y + e4 + 1, a.nents4, a.status)] : pad4;
                     const uint32_t e[8] = {ea.x, ea.y, ea.z, ea.w, eb.x, eb.y, eb.z, eb.w};
                     uint4 v[8];
                     uint32_t zz[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) gload(e[j], X, R, ldb, col, v[j], zz[j]);
+                    for (int j = 0; j < 8; ++j) gload(e[j], X, R, ldb, col, v[j], zz[j], N, a.status);
 #pragma unroll
                     for (int j = 0; j < 8; ++j) gmin(acc, v[j], zz[j]);
                 }
                 if (d.x == 0xFFFFFFFFu) continue;
-                *reinterpret_cast<uint4 *>(R + (int64_t)d.x * ldb + col) = acc;
+                const int64_t qr = mp_ix((int64_t)d.x, N, a.status);
+                *reinterpret_cast<uint4 *>(R + qr * ldb + col) = acc;
                 if (a.user_out)
                     store_row8(a.user_out + (kChain ? (size_t)(k - a.out_k0) * a.slot : 0) +
-                                   (int64_t)a.caller[d.x] * N + a.col_base + col,
+                                   (int64_t)mp_ix((int64_t)a.caller[qr], N, a.status) * N + a.col_base + col,
                                acc, N - a.col_base - col);
             }
             __syncthreads();  // this level's rows are read by the later levels
@@ -371,6 +375,8 @@ static int gcircuit_launch(const PlanDev &p, bool chain, const uint16_t *B0, uin
     a.user_out = user_out;
     a.slot = slot;
     a.gdiag = gdiag;
+    a.nents4 = (uint32_t)(g.ents.bytes / sizeof(uint4));
+    MP_TRY(device_status_ptr(&a.status));
     const unsigned grid = (unsigned)(width / W);
     if (grid == 0) return MP_OK;
     cudaLaunchConfig_t cfg = {};

@@ -54,6 +54,24 @@ constexpr uint32_t kInf16 = 0x7FFFu;
 constexpr uint32_t kInf16x2 = 0x7FFF7FFFu;
 constexpr uint32_t kInf8 = 0xFFu;
 
+// Bounds-checked builds (-DMP_CHECK): mp_ix(i, n, status) is i where i < n;
+// otherwise it latches MP_ECHECK in the device status word (the first error
+// wins) and gives 0, so that the access it feeds stays inside its buffer and
+// the kernel runs to its end.  Without MP_CHECK it is i itself.
+template <class T>
+__device__ __forceinline__ T mp_ix(T i, T n, int *status) {
+#ifdef MP_CHECK
+    if (!(i < n)) {
+        if (status) atomicCAS(status, 0, MP_ECHECK);
+        return T(0);
+    }
+#else
+    (void)n;
+    (void)status;
+#endif
+    return i;
+}
+
 // Bound on spin iterations of any device-side wait (mbarrier phases).  A
 // wait that runs out latches MP_ETIMEOUT into the device status word and
 // the kernel returns without touching the stalled buffer.

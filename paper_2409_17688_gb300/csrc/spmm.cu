@@ -475,13 +475,15 @@ __global__ void repack_powers_kernel(const int16_t *__restrict__ src, int64_t sr
 __global__ void mirror_repack_kernel(const int16_t *__restrict__ src, int W, int64_t ldb, size_t src_slot,
                                      int16_t *__restrict__ dst, size_t dst_slot, const int32_t *__restrict__ mcol,
                                      const int32_t *__restrict__ mrow, const int32_t *__restrict__ inv,
-                                     const int32_t *__restrict__ lead, int64_t nlead, int64_t N, int64_t units) {
+                                     const int32_t *__restrict__ lead, int64_t nlead, int64_t N, int64_t units,
+                                     int *status) {
     extern __shared__ __align__(16) int16_t srow[];  // [2 * ldb]: staged rows of i and of R i
     const int64_t pieces = ldb / 8, ppc = W / 8;     // 16-byte pieces per row, per chunk row
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-        const int64_t k = u / nlead, i = lead[u - k * nlead], ri = mrow[i];
+        const int64_t k = u / nlead, i = mp_ix((int64_t)lead[u - k * nlead], N, status);
+        const int64_t ri = mp_ix((int64_t)mrow[i], N, status);
         const int16_t *base = src + (size_t)k * src_slot;
-        const int64_t qa = inv[i], qb = inv[ri];
+        const int64_t qa = mp_ix((int64_t)inv[i], N, status), qb = mp_ix((int64_t)inv[ri], N, status);
         __syncthreads();  // the previous pair's reads are done
         for (int64_t t = threadIdx.x; t < 2 * pieces; t += blockDim.x) {
             const int64_t pc = t < pieces ? t : t - pieces, q = t < pieces ? qa : qb;
@@ -494,7 +496,7 @@ __global__ void mirror_repack_kernel(const int16_t *__restrict__ src, int W, int
         int16_t *ob = dst + (size_t)k * dst_slot + (size_t)ri * (size_t)N;
         for (int64_t c = threadIdx.x; c < N; c += blockDim.x) {
             const int32_t m = mcol[c];
-            const int64_t j = m & 0x7FFFFFFF;
+            const int64_t j = mp_ix((int64_t)(m & 0x7FFFFFFF), ldb, status);
             // row i: a kept column from its own row, a mirrored one from row R i;
             // row R i the other way round
             oa[c] = m < 0 ? srow[ldb + j] : srow[j];
@@ -749,8 +751,10 @@ int launch_mirror_repack(const int16_t *src, int W, int64_t ldb, size_t src_slot
     DeviceInfo di;
     MP_TRY(device_info(&di));
     const unsigned grid = (unsigned)std::min<int64_t>(units, (int64_t)di.sms * 8);
+    int *status = nullptr;
+    MP_TRY(device_status_ptr(&status));
     mirror_repack_kernel<<<grid, 256, smem, s>>>(src, W, ldb, src_slot, dst, dst_slot, mcol, mrow, inv, lead, nlead,
-                                                 N, units);
+                                                 N, units, status);
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
