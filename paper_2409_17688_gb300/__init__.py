@@ -23,7 +23,8 @@ MP_I16 = 0
 MP_U8 = 1
 
 STATUS = {0: "MP_OK", -1: "MP_EINVAL", -2: "MP_EALIAS", -3: "MP_ENOMEM", -4: "MP_ERANGE",
-          -5: "MP_ECUDA", -6: "MP_ETIMEOUT", -7: "MP_EBUSY", -8: "MP_ENOTREADY", -9: "MP_EIO"}
+          -5: "MP_ECUDA", -6: "MP_ETIMEOUT", -7: "MP_EBUSY", -8: "MP_ENOTREADY", -9: "MP_EIO",
+          -10: "MP_ECHECK"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libminplus.so")
