@@ -9,8 +9,8 @@
 // X[p]) for any subsets Out(q'_i) whose union with L(q) is Out(q).  The
 // words' arc rule makes such subsets plentiful (a letter 2 forces a 0 below
 // it, so turning a 1 into a 2 shrinks the successor set), and a greedy cover
-// reads at n = 9 about 6.7 rows per output row instead of the 88 arcs of a
-// row: 23271 row reads per column against nnz(A) = 303097.  The result is
+// reads at n = 9 about 6.9 rows per output row instead of the 88 arcs of a
+// row: 23923 row reads per column against nnz(A) = 303097.  The result is
 // the same minimum, bit for bit.
 //
 // Host: successor sets as bitsets; for each row, in order of set size, the
@@ -19,22 +19,24 @@
 // level it would add to the row, is largest, while that score is at least
 // two.  A row's level is one more than the deepest row of its cover; the
 // level penalty trades a few more reads for fewer, fuller levels.  Each
-// level's rows become lane tasks of at most 8 list entries (16 bytes, one
-// load per lane): a longer list takes an aligned group of 2, 4, .. 32
-// lanes.  Rows are packed widest first into warp slices of 32 lanes, so
-// every lane of a level does the same work.
+// level's rows become lane tasks of at most 8 list entries (one 16-byte
+// piece of each row per load): a longer list takes an aligned group of 2,
+// 4, .. 32 lanes.  Rows are packed widest first into warp slices of 32
+// lanes, so every lane of a level does the same work.
 //
 // Device (circuit_step_kernel): one CTA per chunk of 8 columns (16 where a
 // chain has more 8-column chunks than the GPU has SMs: one CTA per SM then
 // spreads the columns evenly).  The circuit (one blob, the same for every
-// chunk and every step) is copied into shared memory while the previous step
-// finishes, or read from L2 where only the image fits; then the chunk of X
-// (N rows of 8 or 16 columns).  The levels run in order with a block barrier between them,
-// touching only shared memory: a warp takes every 16th slice of a level,
-// each lane folds its 8 rows (16 bytes of each), the lanes of a row combine
-// by shuffles and the first of them writes the row's result to shared memory
-// for the later levels and, with its label added, straight to the next
-// buffer.  After the levels the (at most 8 or 16) rows whose diagonal
+// chunk and every step) is copied into shared memory while the previous
+// step finishes, or read from L2 where only the image fits; then the chunk
+// of X (N rows of 8 or 16 columns).  The levels run in order with a block
+// barrier between them, touching only shared memory: a warp takes every
+// 16th slice of a level, each lane folds its 8 rows (the chunk's 16 or 32
+// bytes of each), the lanes of a row combine by shuffles and the first of
+// them writes the row's result to shared memory for the later levels (a
+// single step also writes it, labelled, to the next buffer; a chain adds
+// the labels in place after the last level, and the result becomes the next
+// step's X).  After the levels the (at most 8 or 16) rows whose diagonal
 // entries lie in the chunk are read back and min-reduced into g[k].
 #include <algorithm>
 #include <cstring>
@@ -191,9 +193,10 @@ constexpr uint32_t kMetaCopy = 32768;  // bytes per bulk copy of the circuit
 // 8) lives at (j + sh) mod 2Nh.
 // kGBlob: the circuit stays in global memory (read through L1/L2, the next
 // slice's lane info and entry block loaded one slice ahead) and only the
-// image takes shared memory, so two CTAs fit on an SM: chosen where the grid
-// is larger than the GPU's SMs, where one CTA's barrier waits then overlap
-// the other's work.  Otherwise the circuit is copied into shared memory.
+// image takes shared memory: chosen where the grid is larger than the GPU's
+// SMs, so that two 8-column CTAs fit on an SM (one CTA's barrier waits then
+// overlap the other's work) or a 16-column image fits at all.  Otherwise the
+// circuit is copied into shared memory.
 // The work of one CTA: column chunk bx of the chain (or step) a.
 // kW: columns per chunk, 8 (one 16-byte piece per image row) or 16 (two).
 // kOut: the code that writes powers (to the caller or a staging area) is
@@ -236,7 +239,7 @@ __device__ __forceinline__ void circuit_body(const CircArgs &a, int bx) {
     }
     // row 2Nh of the image: above every value, the padding of short lists
     if (threadIdx.x < RB / 4) reinterpret_cast<uint32_t *>(smem + (size_t)N2 * RB)[threadIdx.x] = 0xFFFFFFFFu;
-    // the row whose diagonal entry lies in column c0 + t (threads t < 8)
+    // the row whose diagonal entry lies in column c0 + t (threads t < kW)
     uint32_t drow = 0xFFFFu;
     if (a.gdiag && threadIdx.x < kW) drow = a.drow[mp_ix(c0 + (int64_t)threadIdx.x, a.ldb, a.status)];
     // Programmatic dependent launch: the previous step's output (our X) is
