@@ -210,6 +210,19 @@ def test_transfer_chain_graph_replay(mp, torch):
         assert np.array_equal(host(g), go), rep
 
 
+@pytest.mark.parametrize("n,kmax", [(1, 2), (2, 3), (4, 2), (6, 1), (7, 3), (8, 2)])
+def test_full_powers_short_chains(mp, torch, n, kmax):
+    """Full powers for the shortest chains, where the mirrored form stages a
+    single power or none (k_max = 1 takes A itself): every entry against the
+    oracle, on odd and even N."""
+    P, g = mp.mp_transfer_power_sequence(n, kmax)
+    torch.cuda.synchronize()
+    Po, go = oracle.power_sequence(oracle.build_transfer(n), kmax, threads=THREADS)
+    assert np.array_equal(host(P), Po)
+    assert np.array_equal(host(g), go)
+    assert mp.mp_device_status() == 0
+
+
 @pytest.mark.parametrize("n", [8, 9])
 def test_transfer_chain_sampled_rows(mp, torch, n):
     """n = 8, 9 with k_max = 200: every power on sampled rows (the oracle's own
