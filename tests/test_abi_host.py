@@ -163,3 +163,13 @@ def test_command_line_lists_its_commands():
     assert r.returncode == 0, r.stderr
     for cmd in ("gamma2", "table", "recurrence", "circuit", "product", "save", "autotune"):
         assert cmd in r.stdout
+
+
+def test_bounds_checked_build_compiles_and_exports_everything():
+    """The -DMP_CHECK variant of the library builds (nvcc cross-compiles it
+    without a GPU) and exports every entry point the header declares."""
+    from paper_2409_17688_gb300 import _build
+    lib = _build.build_library(check=True)
+    L = ctypes.CDLL(lib)
+    for name in declared_symbols():
+        assert hasattr(L, name), name
